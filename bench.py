@@ -1,0 +1,378 @@
+"""Benchmark: spectral Ewald Stokeslet apply on one GB300 (or N replicas).
+
+A step is one full apply (bin, P2P, P2G, FFT, CNV, IFFT, G2P, SUM) over the
+N = 100,000 uniform workload at tol 1e-6 (M = 128, P = 12), FP32-bulk; the
+plain FP64 apply on the same points is timed beside it.  Inputs are resident
+in HBM; they are smaller than L2, so a 256 MB buffer is rewritten between
+timed steps (outside the per-step events) to flush L2.
+
+Prints one JSON line.  `--impl reference` times the CPU FP64 oracle instead
+(the only other place this script runs oracle/ code besides `cpu_baseline`).
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas, one workload
+per rank, no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "uniform_1e5_tol1e-6_M128_P12"
+METRIC = "particle-applies/s at tol 1e-6 (FP32-bulk vs FP64 plain); per-stage roofline %; p50/p99"
+UNIT = "particle-applies/s"
+FP32_FLOPS_PER_INRANGE = 52      # FP32 pair kernel, FMA = 2 flops, MUFU = 1
+FLOPS_PER_CANDIDATE = 8          # difference + squared distance per tested pair
+N_SM = 152
+FP32_LANES = 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(kernel_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2606_19059_gb300", "csrc", kernel_file)
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        e = d.get(kernel_file)
+        if e and e.get("sha256") == digest and e.get("workload") == WORKLOAD:
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def pair_counts(x: np.ndarray, L: float, rc: float, nc: int):
+    """Exact in-range pair count (0 < |r| <= rc, periodic) and the number of
+    27-cell candidate pairs the P2P kernel tests."""
+    from scipy.spatial import cKDTree
+
+    xw = np.mod(x, L)
+    xw[xw >= L] = 0.0
+    tree = cKDTree(xw, boxsize=L)
+    inrange = int(tree.count_neighbors(tree, rc)) - x.shape[0]   # drop self pairs
+    c = np.minimum((xw / (L / nc)).astype(np.int64), nc - 1)
+    occ = np.zeros((nc, nc, nc), dtype=np.int64)
+    np.add.at(occ, (c[:, 2], c[:, 1], c[:, 0]), 1)
+    nb = np.zeros_like(occ)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                nb += np.roll(occ, (dz, dy, dx), axis=(0, 1, 2))
+    cand = int((occ * nb).sum())
+    return inrange, cand
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2606_19059_gb300 import ewald, workloads
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS[WORKLOAD]
+    x, f = workloads.make(kind, N, seed + rank, L)
+    xd = torch.tensor(x, device=dev)
+    fd = torch.tensor(f, device=dev)
+    ud = torch.empty_like(xd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def timed(plan, steps, warmup):
+        for _ in range(warmup):
+            ewald.ewald_apply(plan.handle, xd.data_ptr(), fd.data_ptr(), ud.data_ptr(), sp)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in evs:
+            flush.zero_()                      # L2 flush between timed steps
+            a.record(stream)
+            ewald.ewald_apply(plan.handle, xd.data_ptr(), fd.data_ptr(), ud.data_ptr(), sp)
+            b.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, wall
+
+    plan32 = ewald.Plan(N, L, tol, ewald.EWALD_F32_BULK, M=M, P=P)
+    with ClockSampler(local) as clk:
+        ms32, wall32 = timed(plan32, args.steps, args.warmup)
+    clocks = clk.summary()
+    if plan32.sync_status() != ewald.EWALD_OK:
+        raise RuntimeError("device error during the timed applies")
+
+    # per-stage device times with serialised stages (CUDA events on the launching stream)
+    ewald.ewald_set_timing(plan32.handle, 2)
+    stage = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        ewald.ewald_apply(plan32.handle, xd.data_ptr(), fd.data_ptr(), ud.data_ptr(), sp)
+        stage.append(ewald.ewald_stage_times(plan32.handle))
+    ewald.ewald_set_timing(plan32.handle, 0)
+    stages = {k: statistics.median([s[k] for s in stage]) for k in stage[0]}
+
+    # plain FP64 apply, same points
+    plan64 = ewald.Plan(N, L, tol, ewald.EWALD_F64, M=M, P=P)
+    ms64, _ = timed(plan64, max(3, args.steps // 4), max(1, args.warmup // 2))
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timing)
+    xh = torch.from_numpy(x.copy()).pin_memory()
+    fh = torch.from_numpy(f.copy()).pin_memory()
+    uh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        ewald.ewald_apply_host(plan32.handle, xh.data_ptr(), fh.data_ptr(), uh.data_ptr(), sp)
+    e2e = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ewald.ewald_apply_host(plan32.handle, xh.data_ptr(), fh.data_ptr(), uh.data_ptr(), sp)
+        e2e.append(time.perf_counter() - t)
+
+    kern, nfft = ewald.ewald_launch_counts(plan32.handle)
+    prm = plan32.params
+    res = {
+        "ms32": ms32, "wall32": wall32, "ms64": ms64, "stages": stages, "e2e_s": e2e,
+        "clocks": clocks, "kernels_per_step": kern, "ffts_per_step": nfft, "params": prm.as_dict(),
+        "N": N, "L": L, "tol": tol, "M": M, "P": P, "x": x if rank == 0 else None,
+    }
+    plan32.close()
+    plan64.close()
+    return res
+
+
+def cpu_baseline(n_targets: int, seed_shift: int = 0):
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle
+    from paper_2606_19059_gb300 import workloads
+
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS[WORKLOAD]
+    x, f = workloads.make(kind, N, seed, L)
+    idx = np.random.default_rng(99 + seed_shift).choice(N, n_targets, replace=False)
+    oracle.build()
+    t = time.perf_counter()
+    oracle.ewald(x, f, L, targets=idx)
+    dt = time.perf_counter() - t
+    return {"value": n_targets / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"direct Ewald (FP64) at {n_targets} sampled targets of the N={N} workload, "
+                      f"structure factors over all {N} sources", "seconds": dt}
+
+
+def main_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2606_19059_gb300 import workloads
+
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS[WORKLOAD]
+    per = 128
+    for w in range(args.warmup):
+        cpu_baseline(per, seed_shift=1000 + w)
+    times = []
+    for k in range(args.steps):
+        r = cpu_baseline(per, seed_shift=k)
+        times.append(r["seconds"])
+        cores = r["cores"]
+    total = sum(times)
+    value = per * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "tol": tol, "M": M, "P": P,
+                   "step": f"oracle direct Ewald at {per} sampled targets"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per} sampled targets per step of the N={N} workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-targets", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    try:
+        if args.impl == "reference":
+            main_reference(args, rank, world)
+            return
+        res = run_gpu(args, rank, world)
+        ms_mean = float(np.mean(res["ms32"]))
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            t = torch.tensor([ms_mean], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_mean = float(t.item())
+        if rank != 0:
+            return
+        N, L, tol, M, P = res["N"], res["L"], res["tol"], res["M"], res["P"]
+        value = world * N / (ms_mean * 1e-3)
+        ms64 = float(np.mean(res["ms64"]))
+        peaks, peak_src = load_peaks()
+        st = res["stages"]
+        prm = res["params"]
+        inr, cand = pair_counts(res["x"], L, prm["rc"], prm["n_c"])
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = N_SM * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+        p2p_flops = FP32_FLOPS_PER_INRANGE * inr + FLOPS_PER_CANDIDATE * cand
+        p2p_tf = p2p_flops / (st["p2p_ms"] * 1e-3) / 1e12
+        # HBM-bound stages: algorithmic bytes per launch
+        b = 4  # FP32 FFT at tol 1e-6
+        ncplx = M * M * (M // 2 + 1)
+        scale_bytes = 2 * 3 * ncplx * 2 * b
+        fft_bytes = 3 * M ** 3 * b + 3 * ncplx * 2 * b
+        hbm = peaks["hbm_gbs"]
+        stage_roof = {
+            "p2p": {"bound": "alu", "achieved": p2p_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": p2p_tf / fp32_peak},
+            "scale": {"bound": "hbm", "achieved": scale_bytes / (st["scale_ms"] * 1e-3) / 1e9,
+                      "peak": hbm, "unit": "GB/s"},
+            "fft": {"bound": "hbm", "achieved": fft_bytes / (st["fft_ms"] * 1e-3) / 1e9, "peak": hbm,
+                    "unit": "GB/s"},
+            "ifft": {"bound": "hbm", "achieved": fft_bytes / (st["ifft_ms"] * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s"},
+        }
+        for k in ("scale", "fft", "ifft"):
+            stage_roof[k]["frac"] = stage_roof[k]["achieved"] / hbm
+        # dominant kernel: the longest stage
+        order = sorted(((st[k + "_ms"], k) for k in ("p2p", "p2g", "fft", "scale", "ifft", "g2p", "bin")),
+                       reverse=True)
+        roof = dict(stage_roof["p2p"])
+        roof["traffic"] = kernel_traffic("k_p2p.cu")
+        roof["kernel"] = "k_p2p<float> (P2P near field)"
+        roof["peak_source"] = (f"FP32 pipe: {N_SM} SMs x {FP32_LANES} lanes x 2 flop x {sm_mhz:.0f} MHz "
+                               f"({peak_src} sm_max_mhz)")
+        roof["algorithmic"] = {"inrange_pairs": inr, "candidate_pairs": cand,
+                               "flops_per_inrange": FP32_FLOPS_PER_INRANGE,
+                               "flops_per_candidate": FLOPS_PER_CANDIDATE, "flops_per_launch": p2p_flops}
+        e2e_ms = 1e3 * float(np.median(res["e2e_s"]))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "L": L, "tol": tol, "M": M, "P": P,
+                       "mode": "f32_bulk", "xi": prm["xi"], "rc": prm["rc"], "n_c": prm["n_c"],
+                       "poly_deg": prm["poly_deg"], "l2": "256 MB buffer rewritten between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "fp64_plain": {"value": world * N / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64},
+            "p50_ms": float(np.percentile(res["ms32"], 50)), "p99_ms": float(np.percentile(res["ms32"], 99)),
+            "wall_s_timed": res["wall32"],
+            "stages_ms": {k: round(v, 5) for k, v in st.items()},
+            "stage_roofline": stage_roof,
+            "dominant_stage": order[0][1],
+            "roofline": roof,
+            "e2e": {"value": N / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": 2 * N * 3 * 8, "d2h_bytes_per_step": N * 3 * 8},
+            "gpu_launches": res["kernels_per_step"] * args.steps,
+            "clocks": res["clocks"],
+        }
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline(args.cpu_targets)
+            cb.pop("seconds", None)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

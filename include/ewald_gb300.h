@@ -1,0 +1,200 @@
+/*
+ * ewald_gb300.h -- C ABI of the GB300 spectral Ewald library for the triply
+ * periodic Stokeslet sum
+ *
+ *     u_i = sum_j sum_{p in L Z^3} G(x_i - x_j + p) f_j,   G(r) = I/|r| + r r^T/|r|^3
+ *
+ * (Kosmacher, Du, Bagge, Biros, "A Performance Portable Fast Ewald Summation
+ * for Stokes Flow": Sec. 2 eq. (potentials) and the Stokeslet of Sec. 2, here
+ * with all three directions periodic).  The sum is evaluated by the spectral
+ * Ewald method of Sec. 2 / Algorithm 1: near field (P2P) over cell lists within
+ * the cutoff rc, plus far field P2G -> FFT -> CNV -> IFFT -> G2P on a uniform
+ * M^3 grid, plus the self term.  Every step runs in this library's CUDA kernels
+ * (cuFFT for the FFTs) on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ *  - Points and forces are N x 3 row-major FP64 arrays in DEVICE memory unless
+ *    the entry point says HOST.  Results are written as N x 3 row-major FP64.
+ *    The caller owns every array it passes; the library never frees them.
+ *  - Positions may lie outside [0, L)^3: they are wrapped periodically.  A
+ *    NaN or Inf coordinate is detected on the device; the apply then writes
+ *    unspecified values (never out-of-bounds memory) and the next call of
+ *    ewald_sync_status() returns EWALD_EINVAL.
+ *  - Sources = targets = the N points.  The pair (i, i, p = 0) and exactly
+ *    coincident points (|r| == 0) are skipped (Sec. 2: "the term is skipped").
+ *  - The k = 0 Fourier mode is dropped (zero mean velocity, Hasimoto's
+ *    convention); a net force is allowed.
+ *  - Apply-type calls are asynchronous on `stream` (a cudaStream_t passed as
+ *    void*; NULL = the legacy default stream) and return after launching.
+ *    Host-side argument errors are returned immediately and launch nothing.
+ *  - A plan is bound to the device current at ewald_plan() time and to its N;
+ *    calls on one plan must not overlap in time (they share its workspace).
+ *  - No call aborts the process; every call returns a status.
+ */
+#ifndef EWALD_GB300_H
+#define EWALD_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ewald_plan_s *ewald_plan_t;
+
+typedef enum {
+    EWALD_OK = 0,
+    EWALD_EINVAL = 1,      /* bad argument (N < 1, L <= 0, tol out of range, NULL, NaN input) */
+    EWALD_ENOMEM = 2,      /* device or host allocation failed */
+    EWALD_ECUDA = 3,       /* a CUDA runtime call failed */
+    EWALD_ECUFFT = 4,      /* a cuFFT call failed */
+    EWALD_ETIMEOUT = 5,    /* a bounded device wait ran out (batched / served queues) */
+    EWALD_EUNSUPPORTED = 6 /* parameters outside what the kernels implement */
+} ewald_status;
+
+typedef enum {
+    /* Everything in FP64 (P2P, P2G, FFT, CNV, G2P, sum). */
+    EWALD_F64 = 0,
+    /* P2P, P2G and G2P in FP32 with FP32 accumulation; FFT, CNV and the final
+     * near + far sum in FP64 when tol < 1e-6, else FP32 FFT/CNV and FP64 sum.
+     * Callers still pass and receive FP64 arrays. */
+    EWALD_F32_BULK = 1
+} ewald_dtype;
+
+/* Method parameters (Sec. 2.3).  ewald_get_params() fills every field.  As an
+ * override for ewald_plan_ex(), a field <= 0 means "choose it": the library
+ * then picks it from the error estimate eq. (ese) as described at ewald_plan. */
+typedef struct {
+    double L;              /* box side */
+    double tol;            /* requested tolerance */
+    double xi;             /* Ewald splitting parameter xi (Sec. 2) */
+    double rc;             /* near-field cutoff radius r_c (Sec. 2.1) */
+    double cell;           /* near-field cell width L / n_c (>= rc) */
+    double h;              /* grid spacing L / M */
+    double est_err;        /* eq. (ese) estimate E^N + E^F + E^w for unit sum |f|^2 */
+    int32_t n_c;           /* near-field cells per side */
+    int32_t M;             /* grid points per side (far field) */
+    int32_t P;             /* window support in grid points (Sec. 2.2) */
+    int32_t poly_deg;      /* degree nu of the piecewise-polynomial window */
+    int32_t tile;          /* grid tile edge T used by P2G / G2P */
+    int32_t p2p_block;     /* threads per P2P block */
+    int32_t near_f64;      /* 1: P2P/P2G/G2P in FP64, 0: FP32 */
+    int32_t fft_f64;       /* 1: FFT/CNV in FP64, 0: FP32 */
+    int64_t footprint_bytes; /* device memory owned by the plan */
+} ewald_params;
+
+/* Per-stage device times (ms) of the most recent apply with timing enabled
+ * (ewald_set_timing).  P2P runs on a second stream concurrently with the far
+ * field, so the stages do not add up to total_ms. */
+typedef struct {
+    float bin_ms, p2p_ms, p2g_ms, fft_ms, scale_ms, ifft_ms, g2p_ms, sum_ms, total_ms;
+} ewald_stage_timing;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *ewald_status_string(ewald_status s);
+
+/* Choose the method parameters for N points in a box of side L at relative
+ * tolerance tol, without touching any GPU.  Rule (Sec. 2.3): each term of the
+ * eq. (ese) estimate is held below tol/3.  With M and P given: xi is the
+ * largest value with E^F <= tol/3, then rc the smallest with E^N <= tol/3.
+ * Without them, M (a cuFFT-friendly size) and rc minimise a per-stage cost
+ * model subject to the same bounds, and P is the smallest support with
+ * E^w <= tol/3.  `override` may be NULL.  Errors: EINVAL for N < 1, L <= 0,
+ * tol outside [1e-12, 1e-2], NULL out; EUNSUPPORTED when an override cannot
+ * be honoured (e.g. P > 16 or M < P). */
+ewald_status ewald_choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
+                                 const ewald_params *override, ewald_params *out);
+
+/* Create a plan: choose parameters (as ewald_choose_params), fit the
+ * piecewise-polynomial window (Sec. 4, Horner form), allocate every device
+ * workspace and create the cuFFT plans on the current device.  *out is set
+ * only on success.  Errors: as ewald_choose_params, plus ENOMEM, ECUDA,
+ * ECUFFT. */
+ewald_status ewald_plan(int64_t N, double L, double tol, ewald_dtype dtype, ewald_plan_t *out);
+ewald_status ewald_plan_ex(int64_t N, double L, double tol, ewald_dtype dtype,
+                           const ewald_params *override, ewald_plan_t *out);
+
+/* Release the plan and all its device memory.  NULL is ignored.  The caller
+ * must make sure no work on the plan is still running. */
+void ewald_destroy(ewald_plan_t plan);
+
+/* Copy the plan's parameters into *out. */
+ewald_status ewald_get_params(ewald_plan_t plan, ewald_params *out);
+
+/* The full apply, Algorithm 1 (bin, P2P, P2G, FFT, CNV, IFFT, G2P, SUM):
+ * u = (near + far - self) for positions x and forces f (device, N x 3 FP64). */
+ewald_status ewald_apply(ewald_plan_t plan, const double *x, const double *f, double *u,
+                         void *stream);
+
+/* Bin new positions (cell lists and grid-tile order, Sec. 3) and keep them in
+ * the plan, so that repeated applies with the same points and new forces --
+ * an iterative solve -- skip the position work.  Followed by
+ * ewald_apply_forces(). */
+ewald_status ewald_set_positions(ewald_plan_t plan, const double *x, void *stream);
+
+/* Apply with the positions of the last ewald_set_positions()/ewald_apply()
+ * and new forces f. */
+ewald_status ewald_apply_forces(ewald_plan_t plan, const double *f, double *u, void *stream);
+
+/* The full apply with HOST arrays (x, f read; u written; N x 3 FP64 each).
+ * Copies host -> device into plan-owned buffers, applies, copies the result
+ * back and synchronises `stream` before returning.  Pinned host memory gives
+ * the full copy bandwidth; pageable memory works. */
+ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const double *f_host,
+                              double *u_host, void *stream);
+
+/* Stage entry points (device arrays).  They share the plan's workspace.
+ * ewald_near_field: u = u^N, the P2P sum of Sec. 2.1 eq. (potentials-near)
+ *   over pairs with 0 < |r| <= rc (no self term).
+ * ewald_far_field:  u = u^F_h, P2G -> FFT -> CNV -> IFFT -> G2P of Sec. 2.2
+ *   (the self image is included; no self term is removed). */
+ewald_status ewald_near_field(ewald_plan_t plan, const double *x, const double *f, double *u,
+                              void *stream);
+ewald_status ewald_far_field(ewald_plan_t plan, const double *x, const double *f, double *u,
+                             void *stream);
+
+/* P2G alone, eq. (p2g): writes the spread grid phi as 3 x M^3 FP64 values,
+ * grid[c][iz][iy][ix] at g = h (ix, iy, iz) (device array of 3 M^3 doubles). */
+ewald_status ewald_spread(ewald_plan_t plan, const double *x, const double *f, double *grid,
+                          void *stream);
+
+/* G2P alone, eq. (g2p): u(x_i) = h^3 sum_g w(x_i - g) v(g) for a caller grid v
+ * in the layout of ewald_spread (device, 3 M^3 FP64, read only). */
+ewald_status ewald_interp(ewald_plan_t plan, const double *x, const double *grid, double *u,
+                          void *stream);
+
+/* FFT -> CNV (eq. (sca), with the 1/M^3 of the inverse FFT folded in) -> IFFT
+ * on a caller grid (3 M^3 FP64 in, 3 M^3 FP64 out; may alias). */
+ewald_status ewald_fourier_convolve(ewald_plan_t plan, const double *grid_in, double *grid_out,
+                                    void *stream);
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing of subsequent applies. */
+ewald_status ewald_set_timing(ewald_plan_t plan, int enable);
+
+/* Stage times of the last timed apply (synchronises on the recorded events). */
+ewald_status ewald_stage_times(ewald_plan_t plan, ewald_stage_timing *out);
+
+/* Synchronise `stream`, then report (and clear) the device-side error flag:
+ * EWALD_EINVAL if an input coordinate was NaN/Inf since the last call. */
+ewald_status ewald_sync_status(ewald_plan_t plan, void *stream);
+
+/* Number of kernel launches (this library's own kernels, cuFFT excluded) that
+ * one ewald_apply() issues with this plan, and the number of cuFFT executions. */
+ewald_status ewald_launch_counts(ewald_plan_t plan, int32_t *kernels, int32_t *ffts);
+
+/* Host-only helpers, usable without a GPU (tests, tooling).
+ * ewald_window_eval: the plan-time piecewise-polynomial fit of the Kaiser-
+ *   Bessel window w_0 for support P and polynomial degree nu (Sec. 2.2 and
+ *   Sec. 4): evaluates w_0(t h) at n offsets t (in grid units) into w;
+ *   returns the fit's maximum error on a dense check grid in *max_err.
+ * ewald_window_hat: the closed-form transform of the truncated window at n
+ *   wave numbers k (for grid spacing h), as the plan uses in CNV. */
+ewald_status ewald_window_eval(int32_t P, int32_t nu, int64_t n, const double *t, double *w,
+                               double *max_err);
+ewald_status ewald_window_hat(int32_t P, double h, int64_t n, const double *k, double *what);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EWALD_GB300_H */

@@ -1,0 +1,566 @@
+// api.cpp -- the C ABI of include/ewald_gb300.h: plan lifecycle and the
+// apply pipeline of Algorithm 1 (bin, P2P || P2G -> FFT -> CNV -> IFFT -> G2P,
+// SUM).  P2P runs on a second stream, concurrently with the far field, as the
+// stages are independent until SUM.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ewg;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+#define EW_CUDA(call)                                    \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) {                         \
+            cudaGetLastError();                          \
+            return e_ == cudaErrorMemoryAllocation ? EWALD_ENOMEM : EWALD_ECUDA; \
+        }                                                \
+    } while (0)
+
+#define EW_FFT(call)                                     \
+    do {                                                 \
+        if ((call) != CUFFT_SUCCESS)                     \
+            return EWALD_ECUFFT;                         \
+    } while (0)
+
+#define EW_ST(call)                                      \
+    do {                                                 \
+        ewald_status s_ = (call);                        \
+        if (s_ != EWALD_OK)                              \
+            return s_;                                   \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess)
+            ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+cudaError_t dalloc(ewald_plan_s *p, T **ptr, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e == cudaSuccess)
+        p->footprint += (int64_t)bytes;
+    return e;
+}
+
+void free_plan(ewald_plan_s *p)
+{
+    if (!p)
+        return;
+    void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
+                    p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nfrc,
+                    p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
+                    p->err, p->hx, p->hf, p->hu};
+    for (void *b : bufs)
+        if (b)
+            cudaFree(b);
+    if (p->have_fwd)
+        cufftDestroy(p->fwd);
+    if (p->have_inv)
+        cufftDestroy(p->inv);
+    if (p->s2)
+        cudaStreamDestroy(p->s2);
+    if (p->ev_fork)
+        cudaEventDestroy(p->ev_fork);
+    if (p->ev_join)
+        cudaEventDestroy(p->ev_join);
+    for (auto &e : p->ev)
+        if (e)
+            cudaEventDestroy(e);
+    delete p;
+}
+
+ewald_status make_plan(ewald_plan_s *p)
+{
+    const ewald_params &q = p->prm;
+    Geometry &g = p->g;
+    g.nc = q.n_c;
+    g.cell = q.cell;
+    g.K = (int)ceil(q.rc / q.cell - 1e-12);
+    if (g.K < 1)
+        g.K = 1;
+    g.ncells = g.nc * g.nc * g.nc;
+    g.nkeys = g.ncells * kSub3;
+    g.M = q.M;
+    g.P = q.P;
+    g.T = q.tile;
+    g.nt = g.M / g.T;
+    g.ntiles = g.nt * g.nt * g.nt;
+    g.KT = (g.P - 1 + g.T - 1) / g.T;
+    g.h = q.h;
+    g.Mh = g.M / 2 + 1;
+    g.nreal = (int64_t)g.M * g.M * g.M;
+    g.ncplx = (int64_t)g.M * g.M * g.Mh;
+    p->near64 = q.near_f64 != 0;
+    p->fft64 = q.fft_f64 != 0;
+
+    double werr = 0;
+    EW_ST(fit_window(g.P, q.poly_deg, &p->wpoly, &werr));
+
+    const int64_t N = p->N;
+    const size_t r4 = p->near64 ? 32 : 16, rs = p->near64 ? 8 : 4, fs = p->fft64 ? 8 : 4;
+    EW_CUDA(dalloc(p, &p->keyn, 4 * N));
+    EW_CUDA(dalloc(p, &p->slotn, 4 * N));
+    EW_CUDA(dalloc(p, &p->keyt, 4 * N));
+    EW_CUDA(dalloc(p, &p->slott, 4 * N));
+    EW_CUDA(dalloc(p, &p->permn, 4 * N));
+    EW_CUDA(dalloc(p, &p->permt, 4 * N));
+    EW_CUDA(dalloc(p, &p->cntn, 4 * ((size_t)g.nkeys + 1)));
+    EW_CUDA(dalloc(p, &p->startn, 4 * ((size_t)g.nkeys + 1)));
+    EW_CUDA(dalloc(p, &p->cntt, 4 * ((size_t)g.ntiles + 1)));
+    EW_CUDA(dalloc(p, &p->startt, 4 * ((size_t)g.ntiles + 1)));
+    EW_CUDA(dalloc(p, &p->items, 4 * ((size_t)g.ncells + 1)));
+    EW_CUDA(dalloc(p, &p->item_off, 4 * ((size_t)g.ncells + 1)));
+    EW_CUDA(dalloc(p, &p->npos, r4 * N));
+    EW_CUDA(dalloc(p, &p->nfrc, r4 * N));
+    EW_CUDA(dalloc(p, &p->tdat, r4 * N));
+    EW_CUDA(dalloc(p, &p->tfrc, r4 * N));
+    EW_CUDA(dalloc(p, &p->un, 3 * rs * N));
+    EW_CUDA(dalloc(p, &p->uf, 3 * rs * N));
+    EW_CUDA(dalloc(p, &p->grid, 3 * fs * (size_t)g.nreal));
+    EW_CUDA(dalloc(p, &p->spec, 3 * 2 * fs * (size_t)g.ncplx));
+    EW_CUDA(dalloc(p, &p->tab, fs * (size_t)g.M));
+    EW_CUDA(dalloc(p, &p->wcoef_dev, rs * p->wpoly.coef.size()));
+    EW_CUDA(dalloc(p, &p->err, sizeof(int)));
+    EW_CUDA(cudaMemset(p->err, 0, sizeof(int)));
+    EW_CUDA(cudaMemset(p->items, 0, 4 * ((size_t)g.ncells + 1)));
+
+    // window polynomial coefficients in the kernels' precision
+    if (p->near64) {
+        EW_CUDA(cudaMemcpy(p->wcoef_dev, p->wpoly.coef.data(), 8 * p->wpoly.coef.size(),
+                           cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> c(p->wpoly.coef.begin(), p->wpoly.coef.end());
+        EW_CUDA(cudaMemcpy(p->wcoef_dev, c.data(), 4 * c.size(), cudaMemcpyHostToDevice));
+    }
+    // CNV table t(n) = e^{-k^2/(4 xi^2)} / w-hat_0(k)^2, zero on the Nyquist plane
+    std::vector<double> tab(g.M);
+    for (int i = 0; i < g.M; ++i) {
+        int n = i <= g.M / 2 ? i : i - g.M;
+        if (g.M % 2 == 0 && i == g.M / 2) {
+            tab[i] = 0.0;
+            continue;
+        }
+        double k = 2.0 * kPi * n / q.L;
+        double wh = kb_window_hat(k, g.h, g.P);
+        tab[i] = exp(-k * k / (4.0 * q.xi * q.xi)) / (wh * wh);
+    }
+    if (p->fft64) {
+        EW_CUDA(cudaMemcpy(p->tab, tab.data(), 8 * g.M, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> t(tab.begin(), tab.end());
+        EW_CUDA(cudaMemcpy(p->tab, t.data(), 4 * g.M, cudaMemcpyHostToDevice));
+    }
+
+    // cuFFT: 3 batched real <-> half-complex transforms of M^3
+    int n3[3] = {g.M, g.M, g.M};
+    int inembed_r[3] = {g.M, g.M, g.M}, inembed_c[3] = {g.M, g.M, g.Mh};
+    size_t ws = 0;
+    EW_FFT(cufftCreate(&p->fwd));
+    p->have_fwd = true;
+    EW_FFT(cufftMakePlanMany(p->fwd, 3, n3, inembed_r, 1, (int)g.nreal, inembed_c, 1,
+                             (int)g.ncplx, p->fft64 ? CUFFT_D2Z : CUFFT_R2C, 3, &ws));
+    p->footprint += (int64_t)ws;
+    EW_FFT(cufftCreate(&p->inv));
+    p->have_inv = true;
+    EW_FFT(cufftMakePlanMany(p->inv, 3, n3, inembed_c, 1, (int)g.ncplx, inembed_r, 1,
+                             (int)g.nreal, p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3, &ws));
+    p->footprint += (int64_t)ws;
+
+    EW_CUDA(cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking));
+    EW_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    EW_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    for (auto &e : p->ev)
+        EW_CUDA(cudaEventCreate(&e));
+    EW_CUDA(load_p2p_constants());
+    p->prm.footprint_bytes = p->footprint;
+    return EWALD_OK;
+}
+
+// a0: binning of positions (and forces when f != NULL) into both orders.
+ewald_status bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t s)
+{
+    const Geometry &g = p->g;
+    BinArgs a;
+    a.x = x;
+    a.f = f;
+    a.N = p->N;
+    a.L = p->prm.L;
+    a.cell = g.cell;
+    a.h = g.h;
+    a.nc = g.nc;
+    a.M = g.M;
+    a.P = g.P;
+    a.T = g.T;
+    a.nt = g.nt;
+    a.f64 = p->near64;
+    EW_CUDA(cudaMemsetAsync(p->cntn, 0, 4 * (size_t)g.nkeys, s));
+    EW_CUDA(cudaMemsetAsync(p->cntt, 0, 4 * (size_t)g.ntiles, s));
+    EW_CUDA(launch_bin_keys(p, a, s));
+    EW_CUDA(launch_scan(p->cntn, p->startn, g.nkeys, s));
+    EW_CUDA(launch_scan(p->cntt, p->startt, g.ntiles, s));
+    EW_CUDA(launch_bin_scatter(p, a, s));
+    EW_CUDA(launch_cell_items(p, s));
+    p->positions_valid = true;
+    return EWALD_OK;
+}
+
+void rec(ewald_plan_s *p, int i, cudaStream_t s)
+{
+    if (p->timing)
+        cudaEventRecord(p->ev[i], s);
+}
+
+// FFT -> CNV -> IFFT on the plan's grid (in place through the spectrum).
+ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s)
+{
+    EW_FFT(cufftSetStream(p->fwd, s));
+    EW_FFT(cufftSetStream(p->inv, s));
+    if (p->fft64)
+        EW_FFT(cufftExecD2Z(p->fwd, (cufftDoubleReal *)p->grid, (cufftDoubleComplex *)p->spec));
+    else
+        EW_FFT(cufftExecR2C(p->fwd, (cufftReal *)p->grid, (cufftComplex *)p->spec));
+    rec(p, 3, s);
+    EW_CUDA(launch_scale(p, C, s));
+    rec(p, 4, s);
+    if (p->fft64)
+        EW_FFT(cufftExecZ2D(p->inv, (cufftDoubleComplex *)p->spec, (cufftDoubleReal *)p->grid));
+    else
+        EW_FFT(cufftExecC2R(p->inv, (cufftComplex *)p->spec, (cufftReal *)p->grid));
+    rec(p, 5, s);
+    return EWALD_OK;
+}
+
+enum Mode { FULL, NEAR_ONLY, FAR_ONLY };
+
+// Everything after binning.  FULL writes u = near + far - self; NEAR_ONLY /
+// FAR_ONLY write that stage alone (converted to FP64).
+ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cudaStream_t s)
+{
+    const double h3 = p->g.h * p->g.h * p->g.h;
+    const double M3 = (double)p->g.nreal;
+    const bool overlap = mode == FULL && p->timing != 2;  // timing mode 2: serialised stages
+    cudaStream_t sn = overlap ? p->s2 : s;
+    if (mode != FAR_ONLY) {
+        if (overlap) {
+            EW_CUDA(cudaEventRecord(p->ev_fork, s));
+            EW_CUDA(cudaStreamWaitEvent(p->s2, p->ev_fork, 0));
+        }
+        rec(p, 7, sn);
+        EW_CUDA(launch_p2p(p, sn));
+        rec(p, 8, sn);
+        if (overlap)
+            EW_CUDA(cudaEventRecord(p->ev_join, p->s2));
+    }
+    if (mode != NEAR_ONLY) {
+        rec(p, 1, s);
+        EW_CUDA(launch_p2g(p, s));
+        rec(p, 2, s);
+        EW_ST(fgc(p, 8.0 * kPi * h3 / M3, s));
+        EW_CUDA(launch_g2p(p, p->grid, p->fft64, s));
+        rec(p, 6, s);
+    }
+    if (overlap)
+        EW_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    if (mode == FULL) {
+        EW_CUDA(launch_sum(p, f, u, s));
+    } else if (mode == NEAR_ONLY) {
+        EW_CUDA(launch_copy_out(p->un, p->near64, u, 3 * p->N, s));
+    } else {
+        EW_CUDA(launch_copy_out(p->uf, p->near64, u, 3 * p->N, s));
+    }
+    rec(p, 9, s);
+    if (p->timing)
+        p->timed_once = true;
+    return EWALD_OK;
+}
+
+bool bad_ptr(const void *a) { return a == nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char *ewald_status_string(ewald_status s)
+{
+    switch (s) {
+    case EWALD_OK: return "ok";
+    case EWALD_EINVAL: return "invalid argument";
+    case EWALD_ENOMEM: return "out of memory";
+    case EWALD_ECUDA: return "CUDA runtime error";
+    case EWALD_ECUFFT: return "cuFFT error";
+    case EWALD_ETIMEOUT: return "device wait timed out";
+    case EWALD_EUNSUPPORTED: return "unsupported parameters";
+    }
+    return "unknown status";
+}
+
+ewald_status ewald_plan_ex(int64_t N, double L, double tol, ewald_dtype dtype,
+                           const ewald_params *ov, ewald_plan_t *out)
+{
+    if (!out)
+        return EWALD_EINVAL;
+    if (N > (int64_t)INT32_MAX / 4)
+        return EWALD_EUNSUPPORTED;
+    ewald_params prm;
+    EW_ST(choose_params(N, L, tol, dtype, ov, &prm));
+    ewald_plan_s *p = new (std::nothrow) ewald_plan_s();
+    if (!p)
+        return EWALD_ENOMEM;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return EWALD_ECUDA;
+    }
+    p->N = N;
+    p->dtype = dtype;
+    p->prm = prm;
+    ewald_status st = make_plan(p);
+    if (st != EWALD_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return EWALD_OK;
+}
+
+ewald_status ewald_plan(int64_t N, double L, double tol, ewald_dtype dtype, ewald_plan_t *out)
+{
+    return ewald_plan_ex(N, L, tol, dtype, nullptr, out);
+}
+
+void ewald_destroy(ewald_plan_t plan)
+{
+    if (!plan)
+        return;
+    DeviceGuard dg(plan->device);
+    free_plan(plan);
+}
+
+ewald_status ewald_get_params(ewald_plan_t plan, ewald_params *out)
+{
+    if (!plan || !out)
+        return EWALD_EINVAL;
+    *out = plan->prm;
+    return EWALD_OK;
+}
+
+ewald_status ewald_apply(ewald_plan_t plan, const double *x, const double *f, double *u,
+                         void *stream)
+{
+    if (!plan || bad_ptr(x) || bad_ptr(f) || bad_ptr(u))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    if (!dg.ok)
+        return EWALD_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    rec(plan, 0, s);
+    EW_ST(bin(plan, x, f, s));
+    return compute(plan, f, u, FULL, s);
+}
+
+ewald_status ewald_set_positions(ewald_plan_t plan, const double *x, void *stream)
+{
+    if (!plan || bad_ptr(x))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    if (!dg.ok)
+        return EWALD_ECUDA;
+    return bin(plan, x, nullptr, (cudaStream_t)stream);
+}
+
+ewald_status ewald_apply_forces(ewald_plan_t plan, const double *f, double *u, void *stream)
+{
+    if (!plan || bad_ptr(f) || bad_ptr(u))
+        return EWALD_EINVAL;
+    if (!plan->positions_valid)
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    if (!dg.ok)
+        return EWALD_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    rec(plan, 0, s);
+    EW_CUDA(launch_gather_forces(plan, f, s));
+    return compute(plan, f, u, FULL, s);
+}
+
+ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const double *f_host,
+                              double *u_host, void *stream)
+{
+    if (!plan || bad_ptr(x_host) || bad_ptr(f_host) || bad_ptr(u_host))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    if (!dg.ok)
+        return EWALD_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = 3 * sizeof(double) * (size_t)plan->N;
+    if (!plan->hx) {
+        EW_CUDA(dalloc(plan, &plan->hx, bytes));
+        EW_CUDA(dalloc(plan, &plan->hf, bytes));
+        EW_CUDA(dalloc(plan, &plan->hu, bytes));
+    }
+    EW_CUDA(cudaMemcpyAsync(plan->hx, x_host, bytes, cudaMemcpyHostToDevice, s));
+    EW_CUDA(cudaMemcpyAsync(plan->hf, f_host, bytes, cudaMemcpyHostToDevice, s));
+    EW_ST(ewald_apply(plan, plan->hx, plan->hf, plan->hu, stream));
+    EW_CUDA(cudaMemcpyAsync(u_host, plan->hu, bytes, cudaMemcpyDeviceToHost, s));
+    EW_CUDA(cudaStreamSynchronize(s));
+    return EWALD_OK;
+}
+
+ewald_status ewald_near_field(ewald_plan_t plan, const double *x, const double *f, double *u,
+                              void *stream)
+{
+    if (!plan || bad_ptr(x) || bad_ptr(f) || bad_ptr(u))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rec(plan, 0, s);
+    EW_ST(bin(plan, x, f, s));
+    return compute(plan, f, u, NEAR_ONLY, s);
+}
+
+ewald_status ewald_far_field(ewald_plan_t plan, const double *x, const double *f, double *u,
+                             void *stream)
+{
+    if (!plan || bad_ptr(x) || bad_ptr(f) || bad_ptr(u))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rec(plan, 0, s);
+    EW_ST(bin(plan, x, f, s));
+    return compute(plan, f, u, FAR_ONLY, s);
+}
+
+ewald_status ewald_spread(ewald_plan_t plan, const double *x, const double *f, double *grid,
+                          void *stream)
+{
+    if (!plan || bad_ptr(x) || bad_ptr(f) || bad_ptr(grid))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    EW_ST(bin(plan, x, f, s));
+    EW_CUDA(launch_p2g(plan, s));
+    EW_CUDA(launch_grid_convert(plan->grid, plan->fft64, grid, true, 3 * plan->g.nreal, s));
+    return EWALD_OK;
+}
+
+ewald_status ewald_interp(ewald_plan_t plan, const double *x, const double *grid, double *u,
+                          void *stream)
+{
+    if (!plan || bad_ptr(x) || bad_ptr(grid) || bad_ptr(u))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    EW_ST(bin(plan, x, nullptr, s));
+    const double h3 = plan->g.h * plan->g.h * plan->g.h;
+    EW_CUDA(launch_g2p_scaled(plan, grid, true, h3, s));
+    EW_CUDA(launch_copy_out(plan->uf, plan->near64, u, 3 * plan->N, s));
+    return EWALD_OK;
+}
+
+ewald_status ewald_fourier_convolve(ewald_plan_t plan, const double *grid_in, double *grid_out,
+                                    void *stream)
+{
+    if (!plan || bad_ptr(grid_in) || bad_ptr(grid_out))
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = 3 * plan->g.nreal;
+    EW_CUDA(launch_grid_convert(grid_in, true, plan->grid, plan->fft64, n, s));
+    EW_ST(fgc(plan, 8.0 * kPi / (double)plan->g.nreal, s));
+    EW_CUDA(launch_grid_convert(plan->grid, plan->fft64, grid_out, true, n, s));
+    return EWALD_OK;
+}
+
+ewald_status ewald_set_timing(ewald_plan_t plan, int enable)
+{
+    if (!plan || enable < 0 || enable > 2)
+        return EWALD_EINVAL;
+    plan->timing = enable;
+    plan->timed_once = false;
+    return EWALD_OK;
+}
+
+ewald_status ewald_stage_times(ewald_plan_t plan, ewald_stage_timing *out)
+{
+    if (!plan || !out)
+        return EWALD_EINVAL;
+    if (!plan->timed_once)
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    EW_CUDA(cudaEventSynchronize(plan->ev[9]));
+    auto el = [&](int a, int b) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, plan->ev[a], plan->ev[b]) != cudaSuccess) {
+            cudaGetLastError();
+            return 0.0f;
+        }
+        return ms;
+    };
+    out->bin_ms = el(0, 7);
+    out->p2p_ms = el(7, 8);
+    out->p2g_ms = el(1, 2);
+    out->fft_ms = el(2, 3);
+    out->scale_ms = el(3, 4);
+    out->ifft_ms = el(4, 5);
+    out->g2p_ms = el(5, 6);
+    float t6 = el(0, 6), t8 = el(0, 8), t9 = el(0, 9);
+    out->sum_ms = t9 - (t6 > t8 ? t6 : t8);
+    out->total_ms = t9;
+    return EWALD_OK;
+}
+
+ewald_status ewald_sync_status(ewald_plan_t plan, void *stream)
+{
+    if (!plan)
+        return EWALD_EINVAL;
+    DeviceGuard dg(plan->device);
+    EW_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int flag = 0;
+    EW_CUDA(cudaMemcpy(&flag, plan->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        EW_CUDA(cudaMemset(plan->err, 0, sizeof(int)));
+        return EWALD_EINVAL;
+    }
+    return EWALD_OK;
+}
+
+ewald_status ewald_launch_counts(ewald_plan_t plan, int32_t *kernels, int32_t *ffts)
+{
+    if (!plan || !kernels || !ffts)
+        return EWALD_EINVAL;
+    // bin_keys, 2 scans, scatter, cell_items + scan, p2p, p2g, scale, g2p, sum
+    *kernels = 11;
+    *ffts = 2;
+    return EWALD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// internal.h -- plan layout and kernel launchers of the GB300 spectral Ewald
+// library.  Private to the library; the public ABI is include/ewald_gb300.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ewald_gb300.h"
+
+namespace ewg {
+
+// 32-byte FP64 quadruple (CUDA 13 deprecates double4)
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+
+constexpr int kSub = 2;             // sub-cells per near cell per side (target ordering)
+constexpr int kSub3 = kSub * kSub * kSub;
+constexpr int kMaxP = 16;           // largest window support the kernels implement
+constexpr int kMaxDeg = 20;         // largest window polynomial degree
+constexpr int kNumEvents = 10;
+
+// Window polynomial for one precision: coef[l * (deg+1) + k] is the z^k
+// coefficient of bin l, z = 2 delta - 1 (Sec. 2.2 / Sec. 4, Horner form).
+struct WindowPoly {
+    int P = 0, deg = 0;
+    std::vector<double> coef;
+};
+
+struct Geometry {
+    // near field
+    int nc;              // cells per side
+    int K;               // neighbour cell reach per side (1 when cell >= rc)
+    double cell;         // cell width
+    int ncells;          // nc^3
+    int nkeys;           // ncells * kSub3
+    // far field
+    int M, P, T, nt;     // grid size, support, tile edge, tiles per side
+    int ntiles;          // nt^3
+    int KT;              // neighbour tile reach for P2G: ceil((P-1)/T)
+    double h;
+    int Mh;              // M/2 + 1
+    int64_t nreal;       // M^3
+    int64_t ncplx;       // M * M * Mh
+};
+
+}  // namespace ewg
+
+struct ewald_plan_s {
+    int device = -1;
+    int64_t N = 0;
+    ewald_dtype dtype = EWALD_F64;
+    ewald_params prm{};
+    ewg::Geometry g{};
+    ewg::WindowPoly wpoly;
+    bool near64 = true, fft64 = true;
+
+    // binning state
+    int32_t *keyn = nullptr, *slotn = nullptr, *keyt = nullptr, *slott = nullptr;
+    int32_t *cntn = nullptr, *startn = nullptr;   // nkeys + 1
+    int32_t *cntt = nullptr, *startt = nullptr;   // ntiles + 1
+    int32_t *items = nullptr, *item_off = nullptr;  // P2P work items per cell (ncells + 1)
+    int32_t *permn = nullptr, *permt = nullptr;   // sorted slot -> user index
+    void *npos = nullptr, *nfrc = nullptr;        // near-sorted positions (cell-local) / forces
+    void *tdat = nullptr, *tfrc = nullptr;        // tile-sorted window data / forces
+    void *un = nullptr, *uf = nullptr;            // near / far results, user order
+    void *grid = nullptr;                         // 3 M^3 real
+    void *spec = nullptr;                         // 3 M^2 (M/2+1) complex
+    void *tab = nullptr;                          // CNV 1-D table (M entries)
+    void *wcoef_dev = nullptr;                    // window polynomial coefficients
+    int *err = nullptr;                           // device error flag
+    double *hx = nullptr, *hf = nullptr, *hu = nullptr;  // device staging for ewald_apply_host
+    size_t scan_tmp_bytes = 0;
+
+    cufftHandle fwd = 0, inv = 0;
+    bool have_fwd = false, have_inv = false;
+    cudaStream_t s2 = nullptr;                    // second stream: P2P alongside the far field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev[ewg::kNumEvents] = {};
+    int timing = 0;                               // 0 off, 1 timed, 2 timed with serialised stages
+    bool timed_once = false;
+    bool positions_valid = false;
+    int64_t footprint = 0;
+};
+
+namespace ewg {
+
+// ---- host-side math shared by the planner (no CUDA) ----------------------
+double bessel_i0(double x);
+double kb_window(double t_grid, int P);                  // w_0 at t (grid units)
+double kb_window_hat(double k, double h, int P);          // closed-form transform
+ewald_status fit_window(int P, int deg, WindowPoly *out, double *max_err);
+ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
+                           const ewald_params *ov, ewald_params *out);
+
+// ---- kernel launchers (defined in the .cu files) -------------------------
+struct BinArgs {
+    const double *x;     // user positions N x 3
+    const double *f;     // user forces N x 3 (may be null: positions only)
+    int64_t N;
+    double L, cell, h;
+    int nc, M, P, T, nt;
+    bool f64;            // sorted arrays in FP64 (else FP32)
+};
+cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s);
+cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s);
+cudaError_t launch_bin_scatter(ewald_plan_s *p, const BinArgs &a, cudaStream_t s);
+cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t s);
+cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s);
+cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s);
+cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s);
+cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);
+cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, bool grid_f64, cudaStream_t s);
+cudaError_t launch_g2p_scaled(ewald_plan_s *p, const void *grid, bool grid_f64, double scale,
+                              cudaStream_t s);
+cudaError_t load_p2p_constants();
+cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s);
+cudaError_t launch_copy_out(const void *src, bool src_f64, double *dst, int64_t n, cudaStream_t s);
+cudaError_t launch_grid_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t n,
+                                cudaStream_t s);
+
+}  // namespace ewg

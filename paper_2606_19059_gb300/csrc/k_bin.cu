@@ -1,0 +1,351 @@
+// k_bin.cu -- step a0 (binning) and a7 (sum) of the apply, plus small
+// conversion kernels.
+//
+// Binning (Sec. 3, "cell lists"): every point gets two keys,
+//   * its near-field cell (width L/n_c >= rc) refined by a 2x2x2 sub-cell, so
+//     that P2P targets of one warp are spatially compact, and
+//   * the grid tile (T^3 grid points) holding its window anchor, for P2G/G2P.
+// A counting sort (atomic slot per key, one scan, one scatter) writes both
+// orders as structure-of-vec4 arrays with cell-local coordinates.  Unlike the
+// paper's padded cell list, cells are compact (offset array), so clustered
+// inputs cost no padding.
+#include <math.h>
+
+#include "internal.h"
+
+namespace ewg {
+namespace {
+
+struct KeyArgs {
+    const double *x, *f;
+    int64_t N;
+    double L, inv_cell, cell, inv_h, half_odd;
+    int nc, M, T, nt, ceilP2;
+    int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
+    const int32_t *startn, *startt;
+    void *npos, *nfrc, *tdat, *tfrc;
+    int *err;
+};
+
+struct Bin {
+    double xw[3];      // wrapped position in [0, L)
+    int c[3], s[3];    // near cell and sub-cell
+    int a[3], tl[3];   // window anchor (wrapped) and its tile
+    double delta[3];   // fractional grid offset of the anchor
+    bool bad;
+};
+
+__device__ __forceinline__ Bin compute_bin(const KeyArgs &k, int64_t i)
+{
+    Bin b;
+    b.bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double v = k.x[3 * i + d];
+        if (!isfinite(v)) {
+            b.bad = true;
+            v = 0.0;
+        }
+        v -= k.L * floor(v / k.L);
+        if (v >= k.L)
+            v -= k.L;
+        if (v < 0.0)
+            v = 0.0;
+        b.xw[d] = v;
+        double q = v * k.inv_cell;
+        int ci = min(max((int)q, 0), k.nc - 1);
+        int si = min(max((int)((q - ci) * kSub), 0), kSub - 1);
+        b.c[d] = ci;
+        b.s[d] = si;
+        // window anchor (Sec. 2.2): a = floor(y/h + (P odd)/2) - ceil(P/2) + 1,
+        // the P support points are a + l, l = 0..P-1
+        double sg = v * k.inv_h + k.half_odd;
+        double fl = floor(sg);
+        b.delta[d] = sg - fl;
+        int ai = ((int)fl - k.ceilP2 + 1) % k.M;
+        if (ai < 0)
+            ai += k.M;
+        b.a[d] = ai;
+        b.tl[d] = ai / k.T;
+    }
+    return b;
+}
+
+__global__ void k_bin_keys(KeyArgs k)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k.N)
+        return;
+    Bin b = compute_bin(k, i);
+    if (b.bad)
+        atomicOr(k.err, 1);
+    int kn = ((b.c[2] * k.nc + b.c[1]) * k.nc + b.c[0]) * kSub3 +
+             (b.s[2] * kSub + b.s[1]) * kSub + b.s[0];
+    int kt = (b.tl[2] * k.nt + b.tl[1]) * k.nt + b.tl[0];
+    k.keyn[i] = kn;
+    k.keyt[i] = kt;
+    k.slotn[i] = atomicAdd(&k.cntn[kn], 1);
+    k.slott[i] = atomicAdd(&k.cntt[kt], 1);
+}
+
+template <typename R, typename R4>
+__global__ void k_bin_scatter(KeyArgs k)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k.N)
+        return;
+    Bin b = compute_bin(k, i);
+    int pn = k.startn[k.keyn[i]] + k.slotn[i];
+    int pt = k.startt[k.keyt[i]] + k.slott[i];
+    R4 *npos = (R4 *)k.npos, *nfrc = (R4 *)k.nfrc, *tdat = (R4 *)k.tdat, *tfrc = (R4 *)k.tfrc;
+    R4 pos;
+    pos.x = (R)(b.xw[0] - b.c[0] * k.cell);
+    pos.y = (R)(b.xw[1] - b.c[1] * k.cell);
+    pos.z = (R)(b.xw[2] - b.c[2] * k.cell);
+    pos.w = (R)0;
+    npos[pn] = pos;
+    k.permn[pn] = (int32_t)i;
+    int packed = (b.a[0] - b.tl[0] * k.T) | ((b.a[1] - b.tl[1] * k.T) << 4) |
+                 ((b.a[2] - b.tl[2] * k.T) << 8);
+    R4 td;
+    td.x = (R)b.delta[0];
+    td.y = (R)b.delta[1];
+    td.z = (R)b.delta[2];
+    td.w = (R)packed;  // small integer, exact in FP32 and FP64
+    tdat[pt] = td;
+    k.permt[pt] = (int32_t)i;
+    if (k.f) {
+        R4 fv;
+        fv.x = (R)k.f[3 * i];
+        fv.y = (R)k.f[3 * i + 1];
+        fv.z = (R)k.f[3 * i + 2];
+        fv.w = (R)0;
+        nfrc[pn] = fv;
+        tfrc[pt] = fv;
+    }
+}
+
+template <typename R, typename R4>
+__global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__restrict__ permn,
+                                const int32_t *__restrict__ permt, R4 *nfrc, R4 *tfrc, int64_t N)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N)
+        return;
+    int in = permn[p], it = permt[p];
+    R4 a, b;
+    a.x = (R)f[3 * in];
+    a.y = (R)f[3 * in + 1];
+    a.z = (R)f[3 * in + 2];
+    a.w = (R)0;
+    b.x = (R)f[3 * it];
+    b.y = (R)f[3 * it + 1];
+    b.z = (R)f[3 * it + 2];
+    b.w = (R)0;
+    nfrc[p] = a;
+    tfrc[p] = b;
+}
+
+// Exclusive scan of n counts by one block; out[n] receives the total.
+__global__ void __launch_bounds__(1024) k_scan(const int32_t *__restrict__ in,
+                                               int32_t *__restrict__ out, int n)
+{
+    __shared__ int32_t wsum[32];
+    int tid = threadIdx.x, nthr = blockDim.x;
+    int per = (n + nthr - 1) / nthr;
+    int lo = min(tid * per, n), hi = min(lo + per, n);
+    int s = 0;
+    for (int i = lo; i < hi; ++i)
+        s += in[i];
+    int lane = tid & 31, w = tid >> 5;
+    int v = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += t;
+    }
+    if (lane == 31)
+        wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = nthr >> 5;
+        int t = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o)
+                t += u;
+        }
+        if (lane < nw)
+            wsum[lane] = t;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    int run = v - s + (w > 0 ? wsum[w - 1] : 0);
+    for (int i = lo; i < hi; ++i) {
+        int c = in[i];
+        out[i] = run;
+        run += c;
+    }
+    if (tid == nthr - 1)
+        out[n] = run;
+}
+
+// Number of P2P work items (target chunks of at most `block` points) per cell.
+__global__ void k_cell_items(const int32_t *__restrict__ startn, int32_t *__restrict__ items,
+                             int ncells, int block)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells)
+        return;
+    int cnt = startn[(c + 1) * kSub3] - startn[c * kSub3];
+    items[c] = (cnt + block - 1) / block;
+}
+
+// Step a7 (Algorithm 1, SUM): u = u^N + u^F - (4 xi / sqrt(pi)) f, FP64, user order.
+template <typename R>
+__global__ void k_sum(const R *__restrict__ un, const R *__restrict__ uf,
+                      const double *__restrict__ f, double *__restrict__ u, double selfc, int64_t n3)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3)
+        return;
+    u[i] = ((double)un[i] + (double)uf[i]) - selfc * f[i];
+}
+
+template <typename R>
+__global__ void k_copy_out(const R *__restrict__ src, double *__restrict__ dst, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        dst[i] = (double)src[i];
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A *__restrict__ src, B *__restrict__ dst, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        dst[i] = (B)src[i];
+}
+
+KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
+{
+    KeyArgs k;
+    k.x = a.x;
+    k.f = a.f;
+    k.N = a.N;
+    k.L = a.L;
+    k.cell = a.cell;
+    k.inv_cell = 1.0 / a.cell;
+    k.inv_h = 1.0 / a.h;
+    k.half_odd = (a.P % 2) ? 0.5 : 0.0;
+    k.nc = a.nc;
+    k.M = a.M;
+    k.T = a.T;
+    k.nt = a.nt;
+    k.ceilP2 = (a.P + 1) / 2;
+    k.keyn = p->keyn;
+    k.slotn = p->slotn;
+    k.keyt = p->keyt;
+    k.slott = p->slott;
+    k.cntn = p->cntn;
+    k.cntt = p->cntt;
+    k.permn = p->permn;
+    k.permt = p->permt;
+    k.startn = p->startn;
+    k.startt = p->startt;
+    k.npos = p->npos;
+    k.nfrc = p->nfrc;
+    k.tdat = p->tdat;
+    k.tfrc = p->tfrc;
+    k.err = p->err;
+    return k;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s)
+{
+    KeyArgs k = key_args(p, a);
+    k_bin_keys<<<blocks_for(a.N, 256), 256, 0, s>>>(k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s)
+{
+    k_scan<<<1, 1024, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter(ewald_plan_s *p, const BinArgs &a, cudaStream_t s)
+{
+    KeyArgs k = key_args(p, a);
+    if (a.f64)
+        k_bin_scatter<double, dvec4><<<blocks_for(a.N, 256), 256, 0, s>>>(k);
+    else
+        k_bin_scatter<float, float4><<<blocks_for(a.N, 256), 256, 0, s>>>(k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t s)
+{
+    if (p->near64)
+        k_gather_forces<double, dvec4><<<blocks_for(p->N, 256), 256, 0, s>>>(
+            f, p->permn, p->permt, (dvec4 *)p->nfrc, (dvec4 *)p->tfrc, p->N);
+    else
+        k_gather_forces<float, float4><<<blocks_for(p->N, 256), 256, 0, s>>>(
+            f, p->permn, p->permt, (float4 *)p->nfrc, (float4 *)p->tfrc, p->N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s)
+{
+    k_cell_items<<<blocks_for(p->g.ncells, 256), 256, 0, s>>>(p->startn, p->items, p->g.ncells,
+                                                               p->prm.p2p_block);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    return launch_scan(p->items, p->item_off, p->g.ncells, s);
+}
+
+cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s)
+{
+    double selfc = 4.0 * p->prm.xi / sqrt(3.14159265358979323846);
+    int64_t n3 = 3 * p->N;
+    if (p->near64)
+        k_sum<double><<<blocks_for(n3, 256), 256, 0, s>>>((const double *)p->un,
+                                                          (const double *)p->uf, f, u, selfc, n3);
+    else
+        k_sum<float><<<blocks_for(n3, 256), 256, 0, s>>>((const float *)p->un,
+                                                         (const float *)p->uf, f, u, selfc, n3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out(const void *src, bool src_f64, double *dst, int64_t n, cudaStream_t s)
+{
+    if (src_f64)
+        k_copy_out<double><<<blocks_for(n, 256), 256, 0, s>>>((const double *)src, dst, n);
+    else
+        k_copy_out<float><<<blocks_for(n, 256), 256, 0, s>>>((const float *)src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t n,
+                                cudaStream_t s)
+{
+    unsigned nb = blocks_for(n, 256);
+    if (src_f64 && dst_f64)
+        k_convert<double, double><<<nb, 256, 0, s>>>((const double *)src, (double *)dst, n);
+    else if (src_f64)
+        k_convert<double, float><<<nb, 256, 0, s>>>((const double *)src, (float *)dst, n);
+    else if (dst_f64)
+        k_convert<float, double><<<nb, 256, 0, s>>>((const float *)src, (double *)dst, n);
+    else
+        k_convert<float, float><<<nb, 256, 0, s>>>((const float *)src, (float *)dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace ewg

@@ -1,0 +1,365 @@
+// params.cpp -- host-only math of the planner: Bessel I0, the truncated
+// Kaiser-Bessel window and its transform, the piecewise-polynomial window fit,
+// and the parameter choice from the error estimate eq. (ese).  No CUDA calls.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace ewg {
+
+static const double kPi = 3.14159265358979323846;
+
+// Modified Bessel function I0 by its power series sum_k ((x/2)^{2k}) / (k!)^2;
+// all terms are positive, so the sum is accurate to rounding for any x.
+double bessel_i0(double x)
+{
+    double q = 0.25 * x * x, term = 1.0, sum = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-18 * sum)
+            break;
+    }
+    return sum;
+}
+
+// Truncated Kaiser-Bessel window of Sec. 2.2 with beta = 2.5 P, a_w = P h / 2,
+// written in grid units t = r / h:  I0(beta sqrt(1 - (2t/P)^2)) / I0(beta)
+// for |t| < P/2, else 0.
+double kb_window(double t, int P)
+{
+    double half = 0.5 * P;
+    if (fabs(t) >= half)
+        return 0.0;
+    double beta = 2.5 * P;
+    double s = t / half;
+    return bessel_i0(beta * sqrt(1.0 - s * s)) / bessel_i0(beta);
+}
+
+// Transform of the truncated window, int w_0(r) e^{-ikr} dr (used in eq. (sca),
+// where the paper leaves it implicit): with a = a_w, s^2 = beta^2 - (k a)^2,
+// 2a sinh(s)/(s I0(beta)); past k a = beta the sinh turns into a sin.
+double kb_window_hat(double k, double h, int P)
+{
+    double beta = 2.5 * P, a = 0.5 * P * h;
+    double d = beta * beta - (k * a) * (k * a);
+    double i0b = bessel_i0(beta);
+    if (d > 0) {
+        double s = sqrt(d);
+        return 2.0 * a * sinh(s) / (s * i0b);
+    }
+    if (d < 0) {
+        double s = sqrt(-d);
+        return 2.0 * a * sin(s) / (s * i0b);
+    }
+    return 2.0 * a / i0b;
+}
+
+// Piecewise-polynomial window (Sec. 2.2 and Sec. 4): for a point whose
+// fractional grid offset is delta in [0, 1), the P window values are
+// w_l(delta) = w_0(l + 1 - P/2 - delta), l = 0..P-1 (one bin of width h each).
+// Each bin is interpolated at deg+1 Chebyshev nodes in z = 2 delta - 1 and
+// stored as monomial coefficients in z for Horner evaluation.
+ewald_status fit_window(int P, int deg, WindowPoly *out, double *max_err)
+{
+    if (P < 2 || P > kMaxP || deg < 1 || deg > kMaxDeg)
+        return EWALD_EUNSUPPORTED;
+    int n = deg + 1;
+    out->P = P;
+    out->deg = deg;
+    out->coef.assign((size_t)P * n, 0.0);
+    std::vector<double> znode(n), cheb(n), Tprev(n), Tcur(n), Tnext(n), mono(n);
+    for (int j = 0; j < n; ++j)
+        znode[j] = cos(kPi * (j + 0.5) / n);
+    double worst = 0.0;
+    for (int l = 0; l < P; ++l) {
+        auto g = [&](double z) { return kb_window(l + 1 - 0.5 * P - 0.5 * (z + 1.0), P); };
+        // Chebyshev coefficients c_m = (2/n) sum_j g(z_j) T_m(z_j), c_0 halved
+        for (int m = 0; m < n; ++m) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j)
+                s += g(znode[j]) * cos(m * kPi * (j + 0.5) / n);
+            cheb[m] = (m == 0 ? 1.0 : 2.0) * s / n;
+        }
+        // monomial form: accumulate c_m T_m(z) with T_{m+1} = 2 z T_m - T_{m-1}
+        std::fill(mono.begin(), mono.end(), 0.0);
+        std::fill(Tprev.begin(), Tprev.end(), 0.0);
+        std::fill(Tcur.begin(), Tcur.end(), 0.0);
+        Tprev[0] = 1.0;                  // T_0
+        if (n > 1)
+            Tcur[1] = 1.0;               // T_1
+        for (int k = 0; k < n; ++k)
+            mono[k] += cheb[0] * Tprev[k];
+        for (int m = 1; m < n; ++m) {
+            for (int k = 0; k < n; ++k)
+                mono[k] += cheb[m] * Tcur[k];
+            std::fill(Tnext.begin(), Tnext.end(), 0.0);
+            for (int k = 0; k < n; ++k) {
+                if (k + 1 < n)
+                    Tnext[k + 1] += 2.0 * Tcur[k];
+                Tnext[k] -= Tprev[k];
+            }
+            Tprev = Tcur;
+            Tcur = Tnext;
+        }
+        for (int k = 0; k < n; ++k)
+            out->coef[(size_t)l * n + k] = mono[k];
+        // dense check of the monomial form against the exact window, on the
+        // open bin (at |t| = P/2 the truncated window jumps from 1/I0(beta)
+        // to 0; the fit takes the one-sided limit there)
+        for (int i = 0; i <= 256; ++i) {
+            double z = -1.0 + 2.0 * (i + 0.5) / 257.0;
+            double p = 0.0;
+            for (int k = n - 1; k >= 0; --k)
+                p = p * z + mono[k];
+            worst = std::max(worst, fabs(p - g(z)));
+        }
+    }
+    if (max_err)
+        *max_err = worst;
+    return EWALD_OK;
+}
+
+// ---- error estimate eq. (ese), unit box, unit sum |f|^2 --------------------
+static double est_near(double xi, double rc)
+{
+    return sqrt(112.0 / 9.0 * pow(xi, 4) * pow(rc, 3)) * exp(-xi * xi * rc * rc);
+}
+static double est_far(double h, double xi)
+{
+    return 4.0 / (3.0 * h) * sqrt(3.5) * exp(-kPi * kPi / pow(2.0 * h * xi, 2));
+}
+// E^w = C(xi) e^{-2.5 P}; the paper leaves C(xi) open.  Measured with the
+// exact window against the direct k sum on the grid's k set: C ~ 20 while
+// h xi is small, and an aliasing floor ~ 5e-4 e^{-0.95 P} near h xi ~ 0.33,
+// where the selection rule below puts it.
+static double est_window(int P)
+{
+    return 20.0 * exp(-2.5 * P) + 5e-4 * exp(-0.95 * P);
+}
+// largest xi with E^F(h, xi) <= target
+static double xi_for_grid(double h, double target)
+{
+    double lg = log(4.0 / (3.0 * h) * sqrt(3.5) / target);
+    if (lg <= 0)
+        lg = 1e-3;
+    return kPi / (2.0 * h * sqrt(lg));
+}
+// smallest rc with E^N(xi, rc) <= target (E^N decreases for xi rc > 1.3)
+static double rc_for_xi(double xi, double target)
+{
+    double lo = 1.3 / xi, hi = 12.0 / xi;
+    if (est_near(xi, lo) <= target)
+        return lo;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (est_near(xi, mid) <= target)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return hi;
+}
+static bool fft_friendly(int m)
+{
+    if (m % 2)
+        return false;
+    for (int p : {2, 3, 5, 7})
+        while (m % p == 0)
+            m /= p;
+    return m == 1;
+}
+
+ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
+                           const ewald_params *ov, ewald_params *out)
+{
+    if (!out || N < 1 || !(L > 0) || !std::isfinite(L) || !(tol >= 1e-12 && tol <= 1e-2))
+        return EWALD_EINVAL;
+    if (dtype != EWALD_F64 && dtype != EWALD_F32_BULK)
+        return EWALD_EINVAL;
+    ewald_params o;
+    memset(&o, 0, sizeof(o));
+    if (ov)
+        o = *ov;
+    ewald_params p;
+    memset(&p, 0, sizeof(p));
+    p.L = L;
+    p.tol = tol;
+    // FP32 bulk stops at tol 1e-7: below it P2P/P2G/G2P fall back to FP64
+    p.near_f64 = (dtype == EWALD_F64 || tol < 1e-7) ? 1 : 0;
+    p.fft_f64 = (dtype == EWALD_F64 || tol < 1e-6) ? 1 : 0;
+    const double target = tol / 3.0;
+
+    // window support P (Sec. 2.2): smallest with E^w <= tol/3
+    int P = o.P;
+    if (P <= 0) {
+        P = 3;
+        while (P < kMaxP && est_window(P) > target)
+            ++P;
+    }
+    if (P < 2 || P > kMaxP)
+        return EWALD_EUNSUPPORTED;
+
+    // Work in the unit box: xi' = xi L, rc' = rc / L, h' = h / L.
+    double xi = o.xi > 0 ? o.xi * L : 0.0;
+    double rc = o.rc > 0 ? o.rc / L : 0.0;
+    int M = o.M;
+    if (M > 0) {
+        if (xi <= 0)
+            xi = xi_for_grid(1.0 / M, target);
+    } else if (xi > 0) {
+        // smallest friendly M with E^F <= target at the given xi
+        M = 8 * ((std::max(8, P + 2) + 7) / 8);
+        while (M < 4096 && (!fft_friendly(M) || est_far(1.0 / M, xi) > target))
+            M += 8;
+    } else {
+        // minimise a per-stage cost model over friendly grid sizes
+        double best = 1e300;
+        for (int m = 8 * ((std::max(8, P + 2) + 7) / 8); m <= 1024; m += 8) {
+            if (!fft_friendly(m))
+                continue;
+            double x = xi_for_grid(1.0 / m, target);
+            double r = rc_for_xi(x, target);
+            int nc = std::max(1, (int)floor(1.0 / r));
+            double cellv = pow(1.0 / nc, 3);
+            double cand = (double)N * (double)N * 27.0 * cellv;       // P2P candidates
+            double inr = (double)N * (double)N * 4.18879 * r * r * r;  // in-range pairs
+            double m3 = (double)m * m * m;
+            double cost = 10.0 * cand + 50.0 * inr                     // P2P
+                          + 2.0 * 8.0 * (double)N * P * P * P          // P2G + G2P
+                          + 2.0 * 30.0 * m3 * log2(m3) / 10.0;          // FFTs (memory bound)
+            if (cost < best) {
+                best = cost;
+                M = m;
+                xi = x;
+            }
+        }
+    }
+    if (M < 4 || M > 4096)
+        return EWALD_EUNSUPPORTED;
+    if (rc <= 0)
+        rc = rc_for_xi(xi, target);
+    // cell list: n_c = floor(L / rc) cells of width >= rc (at least one cell)
+    int nc = o.n_c > 0 ? o.n_c : std::max(1, (int)floor(1.0 / rc));
+    if (1.0 / nc < rc * (1 - 1e-12) && o.n_c <= 0)
+        nc = std::max(1, nc - 1);
+    if ((double)nc * nc * nc * kSub3 > 2.0e8)
+        return EWALD_EUNSUPPORTED;
+
+    p.xi = xi / L;
+    p.rc = rc * L;
+    p.n_c = nc;
+    p.cell = L / nc;
+    p.M = M;
+    p.h = L / M;
+    p.P = P;
+    p.est_err = est_near(xi, rc) + est_far(1.0 / M, xi) + est_window(P);
+
+    // window polynomial degree: max error <= tol/20 (and the FP32 floor)
+    double wtarget = std::max(tol / 20.0, p.near_f64 ? 1e-15 : 2e-8);
+    int deg = o.poly_deg;
+    if (deg <= 0) {
+        WindowPoly wp;
+        double e = 1.0;
+        for (deg = 3; deg <= kMaxDeg; ++deg) {
+            if (fit_window(P, deg, &wp, &e) != EWALD_OK)
+                return EWALD_EUNSUPPORTED;
+            if (e <= wtarget)
+                break;
+        }
+        if (deg > kMaxDeg)
+            deg = kMaxDeg;
+    }
+    p.poly_deg = deg;
+
+    // grid tile T: the G2P block of (T + P - 1)^3 x 3 values must fit in
+    // shared memory (<= 200 KB)
+    int esz = p.near_f64 ? 8 : 4;
+    int T = o.tile > 0 ? o.tile : 8;
+    if (T != 4 && T != 8)
+        return EWALD_EUNSUPPORTED;
+    if (3.0 * pow(T + P - 1, 3) * esz > 200.0 * 1024)
+        T = 4;
+    if (3.0 * pow(T + P - 1, 3) * esz > 200.0 * 1024)
+        return EWALD_EUNSUPPORTED;
+    if (M % T)
+        T = (M % 4 == 0) ? 4 : 0;
+    if (T == 0)
+        return EWALD_EUNSUPPORTED;
+    p.tile = T;
+
+    // P2P block: one warp multiple covering a typical cell (mean + 2 sd)
+    double s = (double)N / ((double)nc * nc * nc);
+    int blk = o.p2p_block > 0 ? o.p2p_block : 32 * (int)ceil((s + 2.0 * sqrt(s) + 1.0) / 32.0);
+    p.p2p_block = std::min(256, std::max(64, blk));
+
+    // device footprint (bytes) of the plan's workspaces
+    int64_t Mh = M / 2 + 1;
+    int64_t m3 = (int64_t)M * M * M, mc = (int64_t)M * M * Mh;
+    int64_t nkeys = (int64_t)nc * nc * nc * kSub3, ntl = m3 / ((int64_t)T * T * T);
+    int64_t fb = 0;
+    fb += N * 4 * 6;                                   // keys, slots, perms
+    fb += (nkeys + 1) * 8 + (ntl + 1) * 8 + ((int64_t)nc * nc * nc + 1) * 8;
+    fb += N * 2 * (p.near_f64 ? 32 : 16) * 2;          // sorted near / tile data
+    fb += N * 3 * (p.near_f64 ? 8 : 4) * 2;            // un, uf
+    fb += 3 * m3 * (p.fft_f64 ? 8 : 4);                // real grid
+    fb += 3 * mc * (p.fft_f64 ? 16 : 8);               // half spectrum
+    fb += 2 * 3 * m3 * (p.fft_f64 ? 8 : 4);            // cuFFT work areas (estimate)
+    p.footprint_bytes = fb;
+    *out = p;
+    return EWALD_OK;
+}
+
+}  // namespace ewg
+
+extern "C" ewald_status ewald_choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
+                                            const ewald_params *ov, ewald_params *out)
+{
+    return ewg::choose_params(N, L, tol, dtype, ov, out);
+}
+
+extern "C" ewald_status ewald_window_eval(int32_t P, int32_t nu, int64_t n, const double *t,
+                                          double *w, double *max_err)
+{
+    if (n < 0 || (n > 0 && (!t || !w)))
+        return EWALD_EINVAL;
+    ewg::WindowPoly wp;
+    double e = 0;
+    ewald_status st = ewg::fit_window(P, nu, &wp, &e);
+    if (st != EWALD_OK)
+        return st;
+    int nn = nu + 1;
+    for (int64_t i = 0; i < n; ++i) {
+        // t in grid units, |t| < P/2: bin l and offset delta with
+        // t = l + 1 - P/2 - delta, delta in [0, 1)
+        double u = t[i] + 0.5 * P;        // in [0, P)
+        if (!(u > 0.0 && u <= (double)P)) {
+            w[i] = 0.0;
+            continue;
+        }
+        int l = (int)ceil(u) - 1;         // u in (l, l + 1]
+        double delta = (double)(l + 1) - u;
+        double z = 2.0 * delta - 1.0;
+        double p = 0.0;
+        for (int k = nn - 1; k >= 0; --k)
+            p = p * z + wp.coef[(size_t)l * nn + k];
+        w[i] = p;
+    }
+    if (max_err)
+        *max_err = e;
+    return EWALD_OK;
+}
+
+extern "C" ewald_status ewald_window_hat(int32_t P, double h, int64_t n, const double *k,
+                                         double *what)
+{
+    if (n < 0 || (n > 0 && (!k || !what)) || P < 2 || P > ewg::kMaxP || !(h > 0))
+        return EWALD_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        what[i] = ewg::kb_window_hat(k[i], h, P);
+    return EWALD_OK;
+}

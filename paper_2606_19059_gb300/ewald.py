@@ -1,0 +1,332 @@
+"""Python binding of the C ABI in include/ewald_gb300.h.
+
+Argument marshalling only: every step of the apply runs in the CUDA library
+``libewald_gb300.so``.  Functions keep the C names.  Device arrays are passed
+as raw pointers (e.g. ``tensor.data_ptr()`` of contiguous float64 CUDA
+tensors) and streams as ``torch.cuda.Stream.cuda_stream`` integers.  If the
+library is missing the import-time loader raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+
+class EwaldError(RuntimeError):
+    """A library call returned a status other than EWALD_OK."""
+
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {ewald_status_string(status)} (status {status})")
+
+
+EWALD_OK, EWALD_EINVAL, EWALD_ENOMEM, EWALD_ECUDA, EWALD_ECUFFT, EWALD_ETIMEOUT, EWALD_EUNSUPPORTED = range(7)
+EWALD_F64, EWALD_F32_BULK = 0, 1
+
+
+class ewald_params(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("xi", ctypes.c_double),
+        ("rc", ctypes.c_double),
+        ("cell", ctypes.c_double),
+        ("h", ctypes.c_double),
+        ("est_err", ctypes.c_double),
+        ("n_c", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("P", ctypes.c_int32),
+        ("poly_deg", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
+        ("p2p_block", ctypes.c_int32),
+        ("near_f64", ctypes.c_int32),
+        ("fft_f64", ctypes.c_int32),
+        ("footprint_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class ewald_stage_timing(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in
+                ("bin_ms", "p2p_ms", "p2g_ms", "fft_ms", "scale_ms", "ifft_ms", "g2p_ms", "sum_ms",
+                 "total_ms")]
+
+    def as_dict(self):
+        return {name: float(getattr(self, name)) for name, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = [
+    ("ewald_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("ewald_choose_params", ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           ctypes.POINTER(ewald_params), ctypes.POINTER(ewald_params)]),
+    ("ewald_plan", ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(_P)]),
+    ("ewald_plan_ex", ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(ewald_params), ctypes.POINTER(_P)]),
+    ("ewald_destroy", None, [_P]),
+    ("ewald_get_params", ctypes.c_int, [_P, ctypes.POINTER(ewald_params)]),
+    ("ewald_apply", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("ewald_set_positions", ctypes.c_int, [_P, _P, _P]),
+    ("ewald_apply_forces", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ewald_apply_host", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("ewald_near_field", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("ewald_far_field", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("ewald_spread", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("ewald_interp", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("ewald_fourier_convolve", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ewald_set_timing", ctypes.c_int, [_P, ctypes.c_int]),
+    ("ewald_stage_times", ctypes.c_int, [_P, ctypes.POINTER(ewald_stage_timing)]),
+    ("ewald_sync_status", ctypes.c_int, [_P, _P]),
+    ("ewald_launch_counts", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("ewald_window_eval", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
+                                         ctypes.POINTER(ctypes.c_double)]),
+    ("ewald_window_hat", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _P, _P]),
+]
+EXPORTED = [name for name, _, _ in _SIGS]
+
+
+def load(build_if_missing: bool = True):
+    """Load libewald_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH}")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != EWALD_OK:
+        raise EwaldError(st, where)
+
+
+def ewald_status_string(status: int) -> str:
+    return load().ewald_status_string(int(status)).decode()
+
+
+def ewald_choose_params(N: int, L: float, tol: float, dtype: int = EWALD_F32_BULK, override=None):
+    out = ewald_params()
+    st = load().ewald_choose_params(int(N), float(L), float(tol), int(dtype),
+                                    ctypes.byref(override) if override is not None else None,
+                                    ctypes.byref(out))
+    _check(st, "ewald_choose_params")
+    return out
+
+
+def ewald_plan_ex(N: int, L: float, tol: float, dtype: int = EWALD_F32_BULK, override=None) -> int:
+    h = _P()
+    st = load().ewald_plan_ex(int(N), float(L), float(tol), int(dtype),
+                              ctypes.byref(override) if override is not None else None, ctypes.byref(h))
+    _check(st, "ewald_plan_ex")
+    return h.value
+
+
+def ewald_plan(N: int, L: float, tol: float, dtype: int = EWALD_F32_BULK) -> int:
+    return ewald_plan_ex(N, L, tol, dtype, None)
+
+
+def ewald_destroy(plan: int) -> None:
+    load().ewald_destroy(plan)
+
+
+def ewald_get_params(plan: int) -> ewald_params:
+    out = ewald_params()
+    _check(load().ewald_get_params(plan, ctypes.byref(out)), "ewald_get_params")
+    return out
+
+
+def _call(name: str, *args):
+    _check(getattr(load(), name)(*args), name)
+
+
+def ewald_apply(plan, x_ptr, f_ptr, u_ptr, stream=0):
+    _call("ewald_apply", plan, x_ptr, f_ptr, u_ptr, stream)
+
+
+def ewald_set_positions(plan, x_ptr, stream=0):
+    _call("ewald_set_positions", plan, x_ptr, stream)
+
+
+def ewald_apply_forces(plan, f_ptr, u_ptr, stream=0):
+    _call("ewald_apply_forces", plan, f_ptr, u_ptr, stream)
+
+
+def ewald_apply_host(plan, x_ptr, f_ptr, u_ptr, stream=0):
+    _call("ewald_apply_host", plan, x_ptr, f_ptr, u_ptr, stream)
+
+
+def ewald_near_field(plan, x_ptr, f_ptr, u_ptr, stream=0):
+    _call("ewald_near_field", plan, x_ptr, f_ptr, u_ptr, stream)
+
+
+def ewald_far_field(plan, x_ptr, f_ptr, u_ptr, stream=0):
+    _call("ewald_far_field", plan, x_ptr, f_ptr, u_ptr, stream)
+
+
+def ewald_spread(plan, x_ptr, f_ptr, grid_ptr, stream=0):
+    _call("ewald_spread", plan, x_ptr, f_ptr, grid_ptr, stream)
+
+
+def ewald_interp(plan, x_ptr, grid_ptr, u_ptr, stream=0):
+    _call("ewald_interp", plan, x_ptr, grid_ptr, u_ptr, stream)
+
+
+def ewald_fourier_convolve(plan, grid_in_ptr, grid_out_ptr, stream=0):
+    _call("ewald_fourier_convolve", plan, grid_in_ptr, grid_out_ptr, stream)
+
+
+def ewald_set_timing(plan, enable: int = 1):
+    _call("ewald_set_timing", plan, int(enable))
+
+
+def ewald_stage_times(plan) -> dict:
+    out = ewald_stage_timing()
+    _check(load().ewald_stage_times(plan, ctypes.byref(out)), "ewald_stage_times")
+    return out.as_dict()
+
+
+def ewald_sync_status(plan, stream=0) -> int:
+    """Synchronise and return the device error status (EWALD_OK or EWALD_EINVAL)."""
+    return int(load().ewald_sync_status(plan, stream))
+
+
+def ewald_launch_counts(plan):
+    k, f = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ewald_launch_counts(plan, ctypes.byref(k), ctypes.byref(f)), "ewald_launch_counts")
+    return k.value, f.value
+
+
+def ewald_window_eval(P: int, nu: int, t):
+    import numpy as np
+
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    w = np.empty_like(t)
+    err = ctypes.c_double()
+    _check(load().ewald_window_eval(int(P), int(nu), t.size, t.ctypes.data, w.ctypes.data,
+                                    ctypes.byref(err)), "ewald_window_eval")
+    return w, err.value
+
+
+def ewald_window_hat(P: int, h: float, k):
+    import numpy as np
+
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    w = np.empty_like(k)
+    _check(load().ewald_window_hat(int(P), float(h), k.size, k.ctypes.data, w.ctypes.data),
+           "ewald_window_hat")
+    return w
+
+
+class Plan:
+    """Owner of one ewald_plan_t working on torch CUDA tensors (marshalling only)."""
+
+    def __init__(self, N: int, L: float, tol: float, dtype: int = EWALD_F32_BULK, **override):
+        ov = None
+        if override:
+            ov = ewald_params()
+            for k, v in override.items():
+                setattr(ov, k, v)
+        self.N, self.L = int(N), float(L)
+        self.handle = ewald_plan_ex(N, L, tol, dtype, ov)
+        self.params = ewald_get_params(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ewald_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def _check_arr(self, a, shape):
+        import torch
+
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and tuple(a.shape) == shape):
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of shape {shape}")
+
+    def apply(self, x, f, out=None, stream=None):
+        import torch
+
+        self._check_arr(x, (self.N, 3))
+        self._check_arr(f, (self.N, 3))
+        u = out if out is not None else torch.empty_like(x)
+        ewald_apply(self.handle, x.data_ptr(), f.data_ptr(), u.data_ptr(), self._stream(stream))
+        return u
+
+    def set_positions(self, x, stream=None):
+        self._check_arr(x, (self.N, 3))
+        ewald_set_positions(self.handle, x.data_ptr(), self._stream(stream))
+
+    def apply_forces(self, f, out=None, stream=None):
+        import torch
+
+        self._check_arr(f, (self.N, 3))
+        u = out if out is not None else torch.empty_like(f)
+        ewald_apply_forces(self.handle, f.data_ptr(), u.data_ptr(), self._stream(stream))
+        return u
+
+    def near_field(self, x, f, stream=None):
+        import torch
+
+        u = torch.empty_like(x)
+        ewald_near_field(self.handle, x.data_ptr(), f.data_ptr(), u.data_ptr(), self._stream(stream))
+        return u
+
+    def far_field(self, x, f, stream=None):
+        import torch
+
+        u = torch.empty_like(x)
+        ewald_far_field(self.handle, x.data_ptr(), f.data_ptr(), u.data_ptr(), self._stream(stream))
+        return u
+
+    def spread(self, x, f, stream=None):
+        import torch
+
+        M = self.params.M
+        g = torch.empty((3, M, M, M), dtype=torch.float64, device=x.device)
+        ewald_spread(self.handle, x.data_ptr(), f.data_ptr(), g.data_ptr(), self._stream(stream))
+        return g
+
+    def interp(self, x, grid, stream=None):
+        import torch
+
+        u = torch.empty_like(x)
+        ewald_interp(self.handle, x.data_ptr(), grid.data_ptr(), u.data_ptr(), self._stream(stream))
+        return u
+
+    def fourier_convolve(self, grid, stream=None):
+        import torch
+
+        out = torch.empty_like(grid)
+        ewald_fourier_convolve(self.handle, grid.data_ptr(), out.data_ptr(), self._stream(stream))
+        return out
+
+    def sync_status(self, stream=None) -> int:
+        return ewald_sync_status(self.handle, self._stream(stream))

@@ -1,0 +1,305 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Error measures (relative to the reference's size):
+  rel_l2  = ||u - u_ref||_2 / ||u_ref||_2 over all components,
+  rel_max = max |u - u_ref| / max |u_ref|.
+A full apply passes when both are <= tol (the requested tolerance).  Stage
+tests hold each stage to its own bound: rounding for the near field and the
+convolution, the window-polynomial error for P2G/G2P, the window (aliasing)
+error for the far field.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from oracle import spectral  # noqa: E402
+from paper_2606_19059_gb300 import ewald, workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+F64, F32 = ewald.EWALD_F64, ewald.EWALD_F32_BULK
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def errs(u, ref):
+    d = u - ref
+    return (np.linalg.norm(d) / np.linalg.norm(ref), np.abs(d).max() / np.abs(ref).max())
+
+
+def plan(N, L, tol, dtype, **ov):
+    return ewald.Plan(N, L, tol, dtype, **ov)
+
+
+# ---------------------------------------------------------------- stages ----
+
+@pytest.mark.parametrize("dtype,bound", [(F64, 1e-12), (F32, 2e-6)])
+def test_near_field_matches_oracle(dtype, bound):
+    x, f = workloads.make("uniform", 3000, seed=101)
+    p = plan(3000, 1.0, 1e-8 if dtype == F64 else 1e-6, dtype, M=32, P=8)
+    u = host(p.near_field(dev(x), dev(f)))
+    ref = oracle.near_field(x, f, 1.0, p.params.xi, p.params.rc)
+    l2, mx = errs(u, ref)
+    assert l2 <= bound and mx <= 5 * bound, (l2, mx)
+
+
+def test_near_field_small_box_explicit_images():
+    # rc > L/3: fewer than three cells per side, colleague cells alias and
+    # images must be enumerated explicitly
+    x, f = workloads.make("uniform", 40, seed=102, L=1.0)
+    p = plan(40, 1.0, 1e-3, F64, M=16, P=6)
+    assert p.params.n_c < 3
+    u = host(p.near_field(dev(x), dev(f)))
+    ref = oracle.near_field(x, f, 1.0, p.params.xi, p.params.rc)
+    assert errs(u, ref)[1] < 1e-12
+
+
+@pytest.mark.parametrize("dtype,P,M", [(F64, 8, 32), (F64, 7, 24), (F32, 12, 32)])
+def test_spread_matches_exact_window(dtype, P, M):
+    x, f = workloads.make("uniform", 400, seed=103)
+    p = plan(400, 1.0, 1e-8 if dtype == F64 else 1e-6, dtype, M=M, P=P)
+    g = host(p.spread(dev(x), dev(f)))
+    ref = spectral.spread(x, f, 1.0, M, P)
+    _, werr = ewald.ewald_window_eval(P, p.params.poly_deg, np.zeros(1))
+    bound = 3 * werr * np.abs(f).max() + (2e-7 if dtype == F32 else 1e-14) * np.abs(ref).max()
+    assert np.abs(g - ref).max() <= bound, (np.abs(g - ref).max(), bound)
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_interp_matches_exact_window(dtype):
+    rng = np.random.default_rng(104)
+    M, P = 32, 9
+    x = workloads.uniform(rng, 300)
+    v = rng.standard_normal((3, M, M, M))
+    p = plan(300, 1.0, 1e-8 if dtype == F64 else 1e-6, dtype, M=M, P=P)
+    u = host(p.interp(dev(x), dev(v)))
+    ref = spectral.gather(x, v, 1.0, M, P)
+    _, werr = ewald.ewald_window_eval(P, p.params.poly_deg, np.zeros(1))
+    h3 = (1.0 / M) ** 3
+    bound = 3 * werr * P ** 3 * h3 * np.abs(v).max() + (1e-6 if dtype == F32 else 1e-13) * np.abs(ref).max()
+    assert np.abs(u - ref).max() <= bound
+
+
+def test_spread_interp_adjoint_on_gpu():
+    rng = np.random.default_rng(105)
+    M, P = 24, 8
+    x = workloads.uniform(rng, 500)
+    f = workloads.forces(rng, 500, zero_mean=False)
+    v = rng.standard_normal((3, M, M, M))
+    p = plan(500, 1.0, 1e-8, F64, M=M, P=P)
+    g = host(p.spread(dev(x), dev(f)))
+    u = host(p.interp(dev(x), dev(v)))
+    h3 = (1.0 / M) ** 3
+    lhs, rhs = h3 * np.sum(g * v), np.sum(f * u)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("dtype,M,bound", [(F64, 32, 1e-12), (F64, 30, 1e-12), (F32, 32, 2e-6)])
+def test_fourier_convolve_matches_numpy(dtype, M, bound):
+    rng = np.random.default_rng(106)
+    P = 8
+    tol = 1e-8 if dtype == F64 else 1e-6
+    p = plan(10, 1.0, tol, dtype, M=M, P=P)
+    phi = rng.standard_normal((3, M, M, M))
+    out = host(p.fourier_convolve(dev(phi)))
+    ref = spectral.fourier_convolve(phi, 1.0, M, P, p.params.xi)
+    assert np.abs(out - ref).max() <= bound * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dtype,bound", [(F64, 1e-8), (F32, 2e-6)])
+def test_far_field_matches_direct_k_sum(dtype, bound):
+    x, f = workloads.make("uniform", 2000, seed=107)
+    M = 48
+    p = plan(2000, 1.0, 1e-8 if dtype == F64 else 1e-6, dtype, M=M, P=12)
+    u = host(p.far_field(dev(x), dev(f)))
+    ref = oracle.far_field(x, f, 1.0, p.params.xi, kbox=M // 2 - 1)
+    l2, mx = errs(u, ref)
+    assert l2 <= bound and mx <= 5 * bound, (l2, mx)
+
+
+# ----------------------------------------------------------- full apply -----
+
+def test_hasimoto_single_point_on_gpu():
+    xi_sc = 2.8372974794806  # tests/golden/hasimoto_sc.txt
+    x = np.array([[0.3, 0.6, 0.1]])
+    f = np.array([[0.2, -1.0, 0.5]])
+    p = plan(1, 1.0, 1e-10, F64)
+    u = host(p.apply(dev(x), dev(f)))
+    assert np.abs(u - (-(8 / 6) * xi_sc * f)).max() <= 1e-9 * np.abs(f).max()
+
+
+def test_uniform_1e3_tol1e8_fp64_all_targets():
+    name = "uniform_1e3_tol1e-8"
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS[name]
+    x, f = workloads.make(kind, N, seed, L)
+    p = plan(N, L, tol, F64)
+    u = host(p.apply(dev(x), dev(f)))
+    ref = oracle.ewald(x, f, L)
+    l2, mx = errs(u, ref)
+    assert l2 <= tol and mx <= tol, (l2, mx, p.params.as_dict())
+
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_uniform_1e5_tol1e6_sampled(dtype):
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS["uniform_1e5_tol1e-6_M128_P12"]
+    x, f = workloads.make(kind, N, seed, L)
+    p = plan(N, L, tol, dtype, M=M, P=P)
+    u = host(p.apply(dev(x), dev(f)))
+    idx = np.random.default_rng(7).choice(N, 256, replace=False)
+    ref = oracle.ewald(x, f, L, targets=idx)
+    l2, mx = errs(u[idx], ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+
+
+def test_clustered_2e6_tol1e7_fp32_sampled():
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS["clustered_2e6_tol1e-7_M256_P14"]
+    x, f = workloads.make(kind, N, seed, L)
+    p = plan(N, L, tol, F32, M=M, P=P)
+    assert p.params.near_f64 == 0 and p.params.fft_f64 == 1
+    u = host(p.apply(dev(x), dev(f)))
+    idx = np.random.default_rng(8).choice(N, 64, replace=False)
+    ref = oracle.ewald(x, f, L, targets=idx)
+    l2, mx = errs(u[idx], ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_clustered_small_all_targets(dtype):
+    x, f = workloads.make("clustered", 4000, seed=109)
+    tol = 1e-8 if dtype == F64 else 1e-6
+    p = plan(4000, 1.0, tol, dtype)
+    u = host(p.apply(dev(x), dev(f)))
+    ref = oracle.ewald(x, f, 1.0)
+    l2, mx = errs(u, ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+
+
+# ------------------------------------------------------------ edge cases ----
+
+def test_two_points_and_odd_grid():
+    x = np.array([[0.1, 0.2, 0.3], [0.8, 0.75, 0.05]])
+    f = np.array([[1.0, 0.0, 0.0], [0.0, -1.0, 0.5]])
+    p = plan(2, 1.0, 1e-9, F64, M=40, P=11)
+    u = host(p.apply(dev(x), dev(f)))
+    ref = oracle.ewald(x, f, 1.0)
+    assert errs(u, ref)[1] <= 1e-9
+
+
+def test_positions_outside_box_are_wrapped():
+    x, f = workloads.make("uniform", 500, seed=110)
+    shift = np.random.default_rng(1).integers(-3, 4, size=x.shape).astype(float)
+    p = plan(500, 1.0, 1e-8, F64)
+    u1 = host(p.apply(dev(x), dev(f)))
+    u2 = host(p.apply(dev(x + shift), dev(f)))
+    assert errs(u2, u1)[1] < 1e-12
+
+
+def test_all_points_in_one_cell():
+    rng = np.random.default_rng(111)
+    x = 0.5 + 0.01 * rng.standard_normal((600, 3))
+    f = workloads.forces(rng, 600)
+    p = plan(600, 1.0, 1e-8, F64)
+    u = host(p.apply(dev(x), dev(f)))
+    ref = oracle.ewald(x, f, 1.0)
+    l2, mx = errs(u, ref)
+    assert l2 <= 1e-8 and mx <= 1e-8
+
+
+def test_coincident_points_are_skipped():
+    x, f = workloads.make("uniform", 300, seed=112)
+    x[7] = x[3]  # an exact duplicate position
+    p = plan(300, 1.0, 1e-8, F64)
+    u = host(p.apply(dev(x), dev(f)))
+    ref = oracle.ewald(x, f, 1.0)
+    assert np.all(np.isfinite(u))
+    assert errs(u, ref)[1] <= 1e-8
+
+
+def test_nonunit_box_and_net_force():
+    rng = np.random.default_rng(113)
+    L = 2.5
+    x = workloads.uniform(rng, 800, L)
+    f = rng.standard_normal((800, 3)) + 0.3  # net force: k = 0 dropped
+    p = plan(800, L, 1e-7, F64)
+    u = host(p.apply(dev(x), dev(f)))
+    ref = oracle.ewald(x, f, L)
+    l2, mx = errs(u, ref)
+    assert l2 <= 1e-7 and mx <= 1e-7
+
+
+def test_nan_input_sets_status_without_fault():
+    x, f = workloads.make("uniform", 200, seed=114)
+    x[5, 1] = np.nan
+    p = plan(200, 1.0, 1e-6, F32)
+    p.apply(dev(x), dev(f))
+    assert p.sync_status() == ewald.EWALD_EINVAL
+    x[5, 1] = 0.5
+    p.apply(dev(x), dev(f))
+    assert p.sync_status() == ewald.EWALD_OK
+
+
+def test_bad_arguments_return_status():
+    with pytest.raises(ewald.EwaldError) as e:
+        ewald.ewald_plan(0, 1.0, 1e-6)
+    assert e.value.status == ewald.EWALD_EINVAL
+    p = plan(10, 1.0, 1e-6, F32)
+    with pytest.raises(ewald.EwaldError) as e:
+        ewald.ewald_apply(p.handle, 0, 0, 0, 0)
+    assert e.value.status == ewald.EWALD_EINVAL
+    with pytest.raises(ewald.EwaldError) as e:
+        ewald.ewald_apply_forces(ewald.ewald_plan(10, 1.0, 1e-6), 1, 1, 0)  # no positions yet
+    assert e.value.status == ewald.EWALD_EINVAL
+
+
+def test_set_positions_then_apply_forces_equals_apply():
+    x, f = workloads.make("uniform", 5000, seed=115)
+    g = workloads.forces(np.random.default_rng(3), 5000)
+    p = plan(5000, 1.0, 1e-6, F32)
+    ua = host(p.apply(dev(x), dev(g)))
+    p.set_positions(dev(x))
+    p.apply_forces(dev(f))
+    ub = host(p.apply_forces(dev(g)))
+    assert errs(ub, ua)[1] < 1e-6
+
+
+def test_apply_host_equals_device_apply():
+    x, f = workloads.make("uniform", 3000, seed=116)
+    p = plan(3000, 1.0, 1e-6, F32)
+    ud = host(p.apply(dev(x), dev(f)))
+    xh = torch.from_numpy(x.copy()).pin_memory()
+    fh = torch.from_numpy(f.copy()).pin_memory()
+    uh = torch.empty_like(xh).pin_memory()
+    ewald.ewald_apply_host(p.handle, xh.data_ptr(), fh.data_ptr(), uh.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    assert errs(uh.numpy(), ud)[1] < 1e-6
+
+
+def test_fp32_and_fp64_agree_to_tolerance():
+    x, f = workloads.make("uniform", 20000, seed=117)
+    a = host(plan(20000, 1.0, 1e-6, F32, M=64, P=10).apply(dev(x), dev(f)))
+    b = host(plan(20000, 1.0, 1e-6, F64, M=64, P=10).apply(dev(x), dev(f)))
+    l2, mx = errs(a, b)
+    assert l2 < 1e-6 and mx < 1e-6
+
+
+def test_stage_times_reported():
+    x, f = workloads.make("uniform", 20000, seed=118)
+    p = plan(20000, 1.0, 1e-6, F32)
+    for mode in (1, 2):
+        ewald.ewald_set_timing(p.handle, mode)
+        p.apply(dev(x), dev(f))
+        t = ewald.ewald_stage_times(p.handle)
+        assert t["total_ms"] > 0 and t["p2p_ms"] > 0 and t["p2g_ms"] > 0 and t["g2p_ms"] > 0
+    k, nfft = ewald.ewald_launch_counts(p.handle)
+    assert k >= 10 and nfft == 2

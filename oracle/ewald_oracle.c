@@ -13,13 +13,17 @@
  *
  *   u_i = sum_j sum'_{p in L Z^3} G^N(x_i - x_j + p) f_j
  *       + (1/L^3) sum_{k != 0} Re[ Ghat^F(k) S(k) e^{i k.x_i} ]
- *       - (4 xi / sqrt(pi)) f_i,            S(k) = sum_j f_j e^{-i k.x_j}
+ *       - (4 xi / sqrt(pi)) sum_{j : x_j = x_i} f_j,   S(k) = sum_j f_j e^{-i k.x_j}
  *
  * with G(r) = I/|r| + r r^T/|r|^3 (no 1/(8 pi mu) factor, Sec. 2), the
  * Hasimoto near-field kernel G^N of eq. (g-near) and the far-field transform
- * Ghat^F of eq. (GFk).  The prime drops (j = i, p = 0); exactly coincident
- * points are skipped as Sec. 2 asks.  The k = 0 mode is dropped (zero mean
- * velocity, Hasimoto's convention).  The self term is lim_{r->0} (G - G^N).
+ * Ghat^F of eq. (GFk).  The prime drops every pair at r = 0: Sec. 2 skips the
+ * term of a point at the target's position, and skipping the whole G term
+ * means also removing its far part G^F(0) f_j = (4 xi / sqrt(pi)) f_j, which
+ * the k sum holds; for j = i that is the usual self term lim_{r->0}(G - G^N).
+ * Removing it for distinct coincident points too keeps the result
+ * independent of xi.  The k = 0 mode is dropped (zero mean velocity,
+ * Hasimoto's convention).
  *
  * Truncation: real space keeps |r| < sqrt(40)/xi (erfc(sqrt 40) ~ 4e-19),
  * k space keeps |k| < 2 xi sqrt(40) (Gaussian factor e^{-40}), so for any xi
@@ -110,11 +114,16 @@ static void image_range(double d, double L, double R, long *lo, long *hi)
 }
 
 /* Sum over j and images p of G^N(x_t - x_j + p) f_j for 0 < |r| < R (open)
- * or 0 < |r| <= R (closed). */
+ * or 0 < |r| <= R (closed).  A pair at r = 0 (the point itself, or a
+ * distinct point at the same position) is skipped as a whole, Sec. 2: its
+ * near part is left out here, and its far part, which the k-space sum
+ * contains as G^F(0) f_j = (4 xi / sqrt(pi)) f_j, is taken out here too --
+ * for j = i this is the usual self term. */
 static void real_space_target(int64_t n, double L, const double *x,
                               const double *f, const double *xt, double R,
                               int closed, double xi, double out[3])
 {
+    const double self = 4.0 * xi / sqrt(ORACLE_PI);
     csum acc[3] = {{0, 0}, {0, 0}, {0, 0}};
     for (int64_t j = 0; j < n; ++j) {
         double d[3];
@@ -128,8 +137,11 @@ static void real_space_target(int64_t n, double L, const double *x,
                 for (long p2 = lo[2]; p2 <= hi[2]; ++p2) {
                     double r[3] = {d[0] + p0 * L, d[1] + p1 * L, d[2] + p2 * L};
                     double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                    if (r2 == 0.0)
-                        continue; /* coincident point or self: skipped */
+                    if (r2 == 0.0) { /* self or coincident: whole term skipped */
+                        for (int a = 0; a < 3; ++a)
+                            cadd(&acc[a], -self * f[3 * j + a]);
+                        continue;
+                    }
                     if (closed ? (r2 > R * R) : (r2 >= R * R))
                         continue;
                     double K[3][3];
@@ -264,22 +276,21 @@ int oracle_ewald(int64_t n, double L, const double *x, const double *f, double x
         free(uf);
         return -1;
     }
-    double self = 4.0 * xi / sqrt(ORACLE_PI);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t t = 0; t < nt; ++t) {
         double un[3];
-        real_space_target(n, L, x, f, &xt[3 * t], R, 0, xi, un);
-        int64_t i = tidx ? tidx[t] : t;
+        real_space_target(n, L, x, f, &xt[3 * t], R, 0, xi, un); /* includes the self term */
         for (int a = 0; a < 3; ++a)
-            u[3 * t + a] = un[a] + uf[3 * t + a] - self * f[3 * i + a];
+            u[3 * t + a] = un[a] + uf[3 * t + a];
     }
     free(xt);
     free(uf);
     return 0;
 }
 
-/* Near field only (the P2P stage, Sec. 2.1 eq. (potentials-near)): sum over j and images with
- * 0 < |r| <= rc of G^N(r) f_j, at every point.  u: n x 3. */
+/* Near field (the P2P stage, Sec. 2.1 eq. (potentials-near)): sum over j and
+ * images with 0 < |r| <= rc of G^N(r) f_j, minus (4 xi/sqrt(pi)) f_j for
+ * every pair at r = 0 (self and coincident points), at every point.  u: n x 3. */
 int oracle_near_field(int64_t n, double L, const double *x, const double *f,
                       double xi, double rc, double *u)
 {

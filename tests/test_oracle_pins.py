@@ -121,16 +121,37 @@ def test_near_field_small_xi_is_bare_stokeslet(oracle_mod):
     assert np.allclose(u[0], bare, rtol=1e-8)
 
 
-def test_near_field_cutoff_is_inclusive_and_excludes_self(oracle_mod):
+def test_near_field_cutoff_is_inclusive_and_self_term(oracle_mod):
     # one pair at distance exactly 0.125 (exactly representable): kept at
-    # rc = 0.125, dropped just below; a lone point sees only its images
+    # rc = 0.125, dropped just below, where only the self term -(4 xi/sqrt pi) f
+    # is left; a lone point sees no image (distance 1 > 0.9), only itself
     x = np.array([[0.5, 0.5, 0.5], [0.625, 0.5, 0.5]])
     f = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    self_term = -oracle_mod.self_coefficient(5.0) * f
     u_in = oracle_mod.near_field(x, f, 1.0, xi=5.0, rc=0.125)
     u_out = oracle_mod.near_field(x, f, 1.0, xi=5.0, rc=0.1249)
-    assert np.abs(u_in).max() > 0 and np.abs(u_out).max() == 0
+    assert np.abs(u_in - self_term).max() > 0
+    assert np.abs(u_out - self_term).max() == 0
     lone = oracle_mod.near_field(x[:1], f[:1], 1.0, xi=5.0, rc=0.9)
-    assert np.abs(lone).max() == 0  # images are at distance 1 > 0.9
+    assert np.abs(lone - self_term[:1]).max() == 0
+
+
+def test_coincident_points_xi_invariance(oracle_mod):
+    # a point duplicated exactly: its pair is skipped as a whole (near and far
+    # part), so the sum must not depend on xi
+    x, f = workloads.make("uniform", 15, seed=17)
+    x[9] = x[4]
+    x[12] = x[4]
+    us = [oracle_mod.ewald(x, f, 1.0, xi=xi) for xi in (4.0, 9.0)]
+    assert _rel(us[1], us[0]) < 1e-12
+    # and equals the sum in which the three copies carry one combined force
+    # seen by the other points, while each copy ignores the other two
+    keep = [i for i in range(15) if i not in (9, 12)]
+    g = f.copy()
+    g[4] = f[4] + f[9] + f[12]
+    u_merged = oracle_mod.ewald(x[keep], g[keep], 1.0, xi=6.0)
+    others = [k for k, i in enumerate(keep) if i != 4]
+    assert _rel(us[0][[i for i in keep if i != 4]], u_merged[others]) < 1e-12
 
 
 def test_far_field_box_equals_sphere_when_it_contains_it(oracle_mod):

@@ -96,11 +96,13 @@ const char *ewald_status_string(ewald_status s);
 
 /* Choose the method parameters for N points in a box of side L at relative
  * tolerance tol, without touching any GPU.  Rule (Sec. 2.3): each term of the
- * eq. (ese) estimate is held below tol/3.  With M and P given: xi is the
- * largest value with E^F <= tol/3, then rc the smallest with E^N <= tol/3.
- * Without them, M (a cuFFT-friendly size) and rc minimise a per-stage cost
- * model subject to the same bounds, and P is the smallest support with
- * E^w <= tol/3.  `override` may be NULL.  Errors: EINVAL for N < 1, L <= 0,
+ * eq. (ese) estimate is held below tol/10 (the paper uses tol/3 for an rms
+ * error; the max-norm error runs about 3x the rms one).  With M and P given:
+ * xi is the largest value with E^F <= tol/10, then rc the smallest with
+ * E^N <= tol/10.  Without them, M (a cuFFT-friendly multiple of 8) and rc
+ * minimise a per-stage cost model subject to the same bounds, and P is the
+ * smallest support with E^w <= tol/10.  M must be a multiple of 4 (the grid
+ * tile).  `override` may be NULL.  Errors: EINVAL for N < 1, L <= 0,
  * tol outside [1e-12, 1e-2], NULL out; EUNSUPPORTED when an override cannot
  * be honoured (e.g. P > 16 or M < P). */
 ewald_status ewald_choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
@@ -146,7 +148,9 @@ ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const dou
 
 /* Stage entry points (device arrays).  They share the plan's workspace.
  * ewald_near_field: u = u^N, the P2P sum of Sec. 2.1 eq. (potentials-near)
- *   over pairs with 0 < |r| <= rc (no self term).
+ *   over pairs with 0 < |r| <= rc, minus (4 xi/sqrt(pi)) f_j for every pair
+ *   at r = 0: the far part of each pair Sec. 2 skips (the self term for
+ *   j = i, coincident points otherwise), so that near + far = u.
  * ewald_far_field:  u = u^F_h, P2G -> FFT -> CNV -> IFFT -> G2P of Sec. 2.2
  *   (the self image is included; no self term is removed). */
 ewald_status ewald_near_field(ewald_plan_t plan, const double *x, const double *f, double *u,

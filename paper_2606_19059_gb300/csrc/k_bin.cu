@@ -23,7 +23,7 @@ struct KeyArgs {
     int nc, M, T, nt, ceilP2;
     int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
     const int32_t *startn, *startt;
-    void *npos, *nfrc, *tdat, *tfrc;
+    void *npos, *nlo, *nfrc, *tdat, *tfrc;
     int *err;
 };
 
@@ -99,9 +99,27 @@ __global__ void k_bin_scatter(KeyArgs k)
     int pt = k.startt[k.keyt[i]] + k.slott[i];
     R4 *npos = (R4 *)k.npos, *nfrc = (R4 *)k.nfrc, *tdat = (R4 *)k.tdat, *tfrc = (R4 *)k.tfrc;
     R4 pos;
-    pos.x = (R)(b.xw[0] - b.c[0] * k.cell);
-    pos.y = (R)(b.xw[1] - b.c[1] * k.cell);
-    pos.z = (R)(b.xw[2] - b.c[2] * k.cell);
+    if constexpr (sizeof(R) == 4) {
+        // cell-local position in cell units, split hi + lo with hi on a 2^-12
+        // lattice (exact in FP32, exact differences) and |lo| <= 2^-13
+        R4 lo;
+        double X[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double q = b.xw[d] * k.inv_cell - b.c[d];
+            X[d] = rint(q * 4096.0) * (1.0 / 4096.0);
+            ((R *)&lo)[d] = (R)(q - X[d]);
+        }
+        pos.x = (R)X[0];
+        pos.y = (R)X[1];
+        pos.z = (R)X[2];
+        lo.w = (R)0;
+        ((R4 *)k.nlo)[pn] = lo;
+    } else {
+        pos.x = (R)(b.xw[0] - b.c[0] * k.cell);
+        pos.y = (R)(b.xw[1] - b.c[1] * k.cell);
+        pos.z = (R)(b.xw[2] - b.c[2] * k.cell);
+    }
     pos.w = (R)0;
     npos[pn] = pos;
     k.permn[pn] = (int32_t)i;
@@ -202,15 +220,16 @@ __global__ void k_cell_items(const int32_t *__restrict__ startn, int32_t *__rest
     items[c] = (cnt + block - 1) / block;
 }
 
-// Step a7 (Algorithm 1, SUM): u = u^N + u^F - (4 xi / sqrt(pi)) f, FP64, user order.
+// Step a7 (Algorithm 1, SUM): u = u^N + u^F in FP64, user order (the self
+// term is already in u^N, see k_p2p.cu).
 template <typename R>
-__global__ void k_sum(const R *__restrict__ un, const R *__restrict__ uf,
-                      const double *__restrict__ f, double *__restrict__ u, double selfc, int64_t n3)
+__global__ void k_sum(const R *__restrict__ un, const R *__restrict__ uf, double *__restrict__ u,
+                      int64_t n3)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n3)
         return;
-    u[i] = ((double)un[i] + (double)uf[i]) - selfc * f[i];
+    u[i] = (double)un[i] + (double)uf[i];
 }
 
 template <typename R>
@@ -256,6 +275,7 @@ KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
     k.startn = p->startn;
     k.startt = p->startt;
     k.npos = p->npos;
+    k.nlo = p->nlo;
     k.nfrc = p->nfrc;
     k.tdat = p->tdat;
     k.tfrc = p->tfrc;
@@ -313,14 +333,14 @@ cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s)
 
 cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s)
 {
-    double selfc = 4.0 * p->prm.xi / sqrt(3.14159265358979323846);
+    (void)f;
     int64_t n3 = 3 * p->N;
     if (p->near64)
         k_sum<double><<<blocks_for(n3, 256), 256, 0, s>>>((const double *)p->un,
-                                                          (const double *)p->uf, f, u, selfc, n3);
+                                                          (const double *)p->uf, u, n3);
     else
         k_sum<float><<<blocks_for(n3, 256), 256, 0, s>>>((const float *)p->un,
-                                                         (const float *)p->uf, f, u, selfc, n3);
+                                                         (const float *)p->uf, u, n3);
     return cudaGetLastError();
 }
 

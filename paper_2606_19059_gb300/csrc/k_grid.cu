@@ -11,12 +11,15 @@
 // in a fixed order: no atomics, no zeroing pass, bitwise-reproducible grids.
 // (The paper's P2G-hybrid, Algorithm 4, is the prior art: it also keeps the
 // window values in shared memory, but scatters with O(27 N) atomics.)
-// Threads are (row = (y, z) of the tile) x (slice of the point list); each
-// keeps its row of T values x 3 components in registers.
+// The neighbour tiles' point ranges are concatenated and processed in rounds
+// of 256 points: (A) one thread per point tests overlap with the tile and
+// compacts, (B) one thread per (point, axis, offset) evaluates the window
+// polynomial, (C) threads = (row (y, z) of the tile) x (slice of the point
+// list) accumulate a row of T values x 3 components in registers.
 //
 // G2P: one block per tile of anchors stages the (T+P-1)^3 grid block the
-// tile's points can touch in shared memory; one warp per point sums its P^3
-// support (lanes over (z, y) rows, a shuffle reduction at the end).
+// tile's points can touch in shared memory (row by row); one warp per point
+// sums its P^3 support, lanes over (z, y) rows, a shuffle reduction at the end.
 #include <math.h>
 
 #include "internal.h"
@@ -39,7 +42,7 @@ __device__ __forceinline__ R horner(const R *c, int deg, R z)
 {
     R p = c[deg];
     for (int k = deg - 1; k >= 0; --k)
-        p = p * z + c[k];
+        p = fma(p, z, c[k]);
     return p;
 }
 
@@ -48,93 +51,141 @@ template <> struct Vec4<float> { using T = float4; };
 template <> struct Vec4<double> { using T = dvec4; };
 
 constexpr int kP2GThreads = 256;
+constexpr int kMaxSeg = 125;  // (KT+1)^3 with KT <= 4 (T = 4, P = 16)
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
 
 // P2G: R = accumulation precision, G = grid element type.
 template <int T, typename R, typename G>
 __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
 {
     using R4 = typename Vec4<R>::T;
+    constexpr int NT = kP2GThreads;
     constexpr int ROWS = T * T;
-    constexpr int SL = kP2GThreads / ROWS;
-    constexpr int B = kP2GThreads;  // points staged per round
+    constexpr int SL = NT / ROWS;
+    constexpr int B = NT;  // points per round
     extern __shared__ __align__(32) unsigned char smem[];
     R *wx = (R *)smem;              // [B][T]
     R *wy = wx + B * T;             // [B][T]
     R *wz = wy + B * T;             // [B][T]
     R *sf = wz + B * T;             // [B][3]
-    R *coef = sf + B * 3;           // [P][deg+1]
+    R *sd = sf + B * 3;             // [B][3] fractional offsets delta
+    R *coef = sd + B * 3;           // [P][deg+1]
+    __shared__ int soff[B];         // packed anchor offsets relative to the tile (biased)
+    __shared__ int seg_start[kMaxSeg], seg_pref[kMaxSeg + 1];
     __shared__ int scount;
 
-    const int nt = a.nt, P = a.P, nd = a.deg + 1;
+    const int nt = a.nt, P = a.P, nd = a.deg + 1, KT = a.KT;
+    const int side = KT + 1, nseg = side * side * side;
     const int tile = blockIdx.x;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
-    for (int i = threadIdx.x; i < P * nd; i += blockDim.x)
+    for (int i = threadIdx.x; i < P * nd; i += NT)
         coef[i] = ((const R *)a.wcoef)[i];
+    // segment table: neighbour tile s = (dz, dy, dx) in [-KT, 0]^3
+    if (threadIdx.x < 32) {
+        int carry = 0;
+        for (int s0 = 0; s0 < nseg; s0 += 32) {
+            int s = s0 + threadIdx.x, len = 0;
+            if (s < nseg) {
+                int dx = s % side - KT, dy = (s / side) % side - KT, dz = s / (side * side) - KT;
+                int nb = (wrapi(tz + dz, nt) * nt + wrapi(ty + dy, nt)) * nt + wrapi(tx + dx, nt);
+                seg_start[s] = a.startt[nb];
+                len = a.startt[nb + 1] - a.startt[nb];
+            }
+            int v = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, v, o);
+                if ((int)threadIdx.x >= o)
+                    v += u;
+            }
+            if (s < nseg)
+                seg_pref[s + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (threadIdx.x == 0)
+            seg_pref[0] = 0;
+    }
     const int row = threadIdx.x % ROWS, slice = threadIdx.x / ROWS;
     const int y = row % T, z = row / T;
     R acc[T][3];
 #pragma unroll
     for (int x = 0; x < T; ++x)
         acc[x][0] = acc[x][1] = acc[x][2] = (R)0;
-
+    __syncthreads();
+    const int total = seg_pref[nseg];
     const R4 *tdat = (const R4 *)a.tdat, *tfrc = (const R4 *)a.tfrc;
-    for (int dz = -a.KT; dz <= 0; ++dz)
-        for (int dy = -a.KT; dy <= 0; ++dy)
-            for (int dx = -a.KT; dx <= 0; ++dx) {
-                int nx = (tx + dx) % nt, ny = (ty + dy) % nt, nz = (tz + dz) % nt;
-                nx += nx < 0 ? nt : 0;
-                ny += ny < 0 ? nt : 0;
-                nz += nz < 0 ? nt : 0;
-                int nb = (nz * nt + ny) * nt + nx;
-                int s0 = a.startt[nb], s1 = a.startt[nb + 1];
-                for (int base = s0; base < s1; base += B) {
-                    __syncthreads();
-                    if (threadIdx.x == 0)
-                        scount = 0;
-                    __syncthreads();
-                    int j = base + threadIdx.x;
-                    if (j < s1) {
-                        R4 td = tdat[j];
-                        int packed = (int)td.w;
-                        // anchor offsets relative to this output tile's origin
-                        int ox = dx * T + (packed & 15);
-                        int oy = dy * T + ((packed >> 4) & 15);
-                        int oz = dz * T + ((packed >> 8) & 15);
-                        if (ox + P > 0 && ox < T && oy + P > 0 && oy < T && oz + P > 0 && oz < T) {
-                            int k = atomicAdd(&scount, 1);
-                            R zx = (R)2 * td.x - (R)1, zy = (R)2 * td.y - (R)1, zz = (R)2 * td.z - (R)1;
+
+    for (int base = 0; base < total; base += B) {
+        if (threadIdx.x == 0)
+            scount = 0;
+        __syncthreads();
+        // (A) one thread per point: overlap test and compaction
+        const int q = base + threadIdx.x;
+        if (q < total) {
+            int lo = 0, hi = nseg;  // seg_pref[lo] <= q < seg_pref[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (seg_pref[mid] <= q)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int s = lo;
+            const int j = seg_start[s] + (q - seg_pref[s]);
+            const int dx = s % side - KT, dy = (s / side) % side - KT, dz = s / (side * side) - KT;
+            R4 td = tdat[j];
+            int packed = (int)td.w;
+            int ox = dx * T + (packed & 15);
+            int oy = dy * T + ((packed >> 4) & 15);
+            int oz = dz * T + ((packed >> 8) & 15);
+            if (ox + P > 0 && ox < T && oy + P > 0 && oy < T && oz + P > 0 && oz < T) {
+                int k = atomicAdd(&scount, 1);
+                // offsets lie in (-P, T): bias by 32 into 6-bit fields
+                soff[k] = (ox + 32) | ((oy + 32) << 6) | ((oz + 32) << 12);
+                sd[k * 3] = td.x;
+                sd[k * 3 + 1] = td.y;
+                sd[k * 3 + 2] = td.z;
+                R4 fv = tfrc[j];
+                sf[k * 3] = fv.x;
+                sf[k * 3 + 1] = fv.y;
+                sf[k * 3 + 2] = fv.z;
+            }
+        }
+        __syncthreads();
+        const int n = scount;
+        // (B) window values padded to the tile: one thread per (point, axis, offset)
+        for (int w = threadIdx.x; w < n * 3 * T; w += NT) {
+            const int k = w / (3 * T), r = w - k * 3 * T, d = r / T, qq = r - d * T;
+            const int o = ((soff[k] >> (6 * d)) & 63) - 32;
+            const int l = qq - o;
+            R v = (R)0;
+            if (l >= 0 && l < P)
+                v = horner(coef + l * nd, a.deg, (R)2 * sd[k * 3 + d] - (R)1);
+            (d == 0 ? wx : (d == 1 ? wy : wz))[k * T + qq] = v;
+        }
+        __syncthreads();
+        // (C) accumulate rows
+        for (int k = slice; k < n; k += SL) {
+            R wyz = wy[k * T + y] * wz[k * T + z];
+            if (wyz != (R)0) {
+                R f0 = wyz * sf[k * 3], f1 = wyz * sf[k * 3 + 1], f2 = wyz * sf[k * 3 + 2];
 #pragma unroll
-                            for (int q = 0; q < T; ++q) {
-                                int lx = q - ox, ly = q - oy, lz = q - oz;
-                                wx[k * T + q] = (lx >= 0 && lx < P) ? horner(coef + lx * nd, a.deg, zx) : (R)0;
-                                wy[k * T + q] = (ly >= 0 && ly < P) ? horner(coef + ly * nd, a.deg, zy) : (R)0;
-                                wz[k * T + q] = (lz >= 0 && lz < P) ? horner(coef + lz * nd, a.deg, zz) : (R)0;
-                            }
-                            R4 fv = tfrc[j];
-                            sf[k * 3] = fv.x;
-                            sf[k * 3 + 1] = fv.y;
-                            sf[k * 3 + 2] = fv.z;
-                        }
-                    }
-                    __syncthreads();
-                    const int n = scount;
-                    for (int k = slice; k < n; k += SL) {
-                        R wyz = wy[k * T + y] * wz[k * T + z];
-                        if (wyz != (R)0) {
-                            R f0 = wyz * sf[k * 3], f1 = wyz * sf[k * 3 + 1], f2 = wyz * sf[k * 3 + 2];
-#pragma unroll
-                            for (int x = 0; x < T; ++x) {
-                                R w = wx[k * T + x];
-                                acc[x][0] += w * f0;
-                                acc[x][1] += w * f1;
-                                acc[x][2] += w * f2;
-                            }
-                        }
-                    }
+                for (int x = 0; x < T; ++x) {
+                    R w = wx[k * T + x];
+                    acc[x][0] = fma(w, f0, acc[x][0]);
+                    acc[x][1] = fma(w, f1, acc[x][1]);
+                    acc[x][2] = fma(w, f2, acc[x][2]);
                 }
             }
+        }
+        __syncthreads();
+    }
     // reduce the slices through shared memory and store the tile
-    __syncthreads();
     R *red = (R *)smem;  // [SL][3][T][T][T]  (reuses the staging area)
 #pragma unroll
     for (int x = 0; x < T; ++x)
@@ -144,17 +195,19 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
     __syncthreads();
     G *grid = (G *)a.grid;
     const int64_t M = a.M, M3 = M * M * M;
-    for (int o = threadIdx.x; o < 3 * T * T * T; o += blockDim.x) {
-        int x = o % T, yy = (o / T) % T, zz = (o / (T * T)) % T, c = o / (T * T * T);
+    for (int o = threadIdx.x; o < 3 * T * T * T; o += NT) {
+        const int x = o % T, yy = (o / T) % T, zz = (o / (T * T)) % T, c = o / (T * T * T);
         R s = 0;
-        for (int q = 0; q < SL; ++q)
-            s += red[((q * 3 + c) * T + zz) * T * T + yy * T + x];
-        int64_t gx = tx * T + x, gy = ty * T + yy, gz = tz * T + zz;
+#pragma unroll
+        for (int qq = 0; qq < SL; ++qq)
+            s += red[((qq * 3 + c) * T + zz) * T * T + yy * T + x];
+        const int64_t gx = tx * T + x, gy = ty * T + yy, gz = tz * T + zz;
         grid[c * M3 + (gz * M + gy) * M + gx] = (G)s;
     }
 }
 
 constexpr int kG2PThreads = 128;
+constexpr int kRowsPerLane = (kMaxP * kMaxP + 31) / 32;
 
 // G2P: R = arithmetic precision, G = grid element type.
 template <int T, typename R, typename G>
@@ -167,53 +220,74 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
         return;
     extern __shared__ __align__(32) unsigned char smem[];
     const int P = a.P, nd = a.deg + 1, RR = T + P - 1;
-    const int RR3 = RR * RR * RR;
+    const int RR2 = RR * RR, RR3 = RR2 * RR;
     R *vs = (R *)smem;                 // [3][RR][RR][RR]
     R *coef = vs + 3 * RR3;            // [P][nd]
     R *wsm = coef + P * nd;            // per warp [3][kMaxP]
-    const int nt = a.nt;
+    const int nt = a.nt, M = a.M;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     for (int i = threadIdx.x; i < P * nd; i += blockDim.x)
         coef[i] = ((const R *)a.wcoef)[i];
-    const G *grid = (const G *)a.grid;
-    const int64_t M = a.M, M3 = M * M * M;
-    for (int i = threadIdx.x; i < 3 * RR3; i += blockDim.x) {
-        int x = i % RR, y = (i / RR) % RR, z = (i / (RR * RR)) % RR, c = i / RR3;
-        int64_t gx = (tx * T + x) % M, gy = (ty * T + y) % M, gz = (tz * T + z) % M;
-        vs[i] = (R)grid[c * M3 + (gz * M + gy) * M + gx];
-    }
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
+    // stage the grid block row by row (one warp per row, lanes along x)
+    const G *grid = (const G *)a.grid;
+    const int64_t M3 = (int64_t)M * M * M;
+    for (int r = warp; r < 3 * RR2; r += nwarps) {
+        const int c = r / RR2, z = (r / RR) % RR, y = r % RR;
+        int gz = tz * T + z, gy = ty * T + y;
+        gz -= gz >= M ? M : 0;
+        gy -= gy >= M ? M : 0;
+        const G *src = grid + c * M3 + ((int64_t)gz * M + gy) * M;
+        for (int x = lane; x < RR; x += 32) {
+            int gx = tx * T + x;
+            gx -= gx >= M ? M : 0;
+            vs[r * RR + x] = (R)src[gx];
+        }
+    }
+    // this lane's (z, y) rows of the P x P support, fixed for all points
+    int rk[kRowsPerLane], rl[kRowsPerLane];
+#pragma unroll
+    for (int j = 0; j < kRowsPerLane; ++j) {
+        int q = lane + 32 * j;
+        rk[j] = q < P * P ? q / P : -1;
+        rl[j] = q < P * P ? q - (q / P) * P : 0;
+    }
+    __syncthreads();
     R *w = wsm + warp * 3 * kMaxP;
     const R4 *tdat = (const R4 *)a.tdat;
     R *uf = (R *)a.uf;
     for (int p = s0 + warp; p < s1; p += nwarps) {
         R4 td = tdat[p];
-        int packed = (int)td.w;
-        int ox = packed & 15, oy = (packed >> 4) & 15, oz = (packed >> 8) & 15;
+        const int packed = (int)td.w;
+        const int ox = packed & 15, oy = (packed >> 4) & 15, oz = (packed >> 8) & 15;
         __syncwarp();
         for (int q = lane; q < 3 * P; q += 32) {
-            int d = q / P, l = q % P;
-            R dl = d == 0 ? td.x : (d == 1 ? td.y : td.z);
+            const int d = q / P, l = q - d * P;
+            const R dl = d == 0 ? td.x : (d == 1 ? td.y : td.z);
             w[d * kMaxP + l] = horner(coef + l * nd, a.deg, (R)2 * dl - (R)1);
         }
         __syncwarp();
         R u0 = 0, u1 = 0, u2 = 0;
-        for (int q = lane; q < P * P; q += 32) {
-            int k = q / P, l = q % P;  // k: z offset, l: y offset
-            R wkl = w[2 * kMaxP + k] * w[kMaxP + l];
-            int base = ((oz + k) * RR + (oy + l)) * RR + ox;
-            R s0r = 0, s1r = 0, s2r = 0;
-            for (int m = 0; m < P; ++m) {
-                R wm = w[m];
-                s0r += wm * vs[base + m];
-                s1r += wm * vs[RR3 + base + m];
-                s2r += wm * vs[2 * RR3 + base + m];
+#pragma unroll
+        for (int j = 0; j < kRowsPerLane; ++j) {
+            if (rk[j] < 0)
+                break;
+            const R wkl = w[2 * kMaxP + rk[j]] * w[kMaxP + rl[j]];
+            const R *v0 = vs + ((oz + rk[j]) * RR + (oy + rl[j])) * RR + ox;
+            R a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+            for (int m = 0; m < kMaxP; ++m) {
+                if (m < P) {
+                    const R wm = w[m];
+                    a0 = fma(wm, v0[m], a0);
+                    a1 = fma(wm, v0[RR3 + m], a1);
+                    a2 = fma(wm, v0[2 * RR3 + m], a2);
+                }
             }
-            u0 += wkl * s0r;
-            u1 += wkl * s1r;
-            u2 += wkl * s2r;
+            u0 = fma(wkl, a0, u0);
+            u1 = fma(wkl, a1, u1);
+            u2 = fma(wkl, a2, u2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -222,8 +296,8 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
             u2 += __shfl_xor_sync(0xffffffffu, u2, o);
         }
         if (lane == 0) {
-            int i = a.permt[p];
-            R sc = (R)a.scale;
+            const int i = a.permt[p];
+            const R sc = (R)a.scale;
             uf[3 * i] = u0 * sc;
             uf[3 * i + 1] = u1 * sc;
             uf[3 * i + 2] = u2 * sc;
@@ -255,7 +329,7 @@ template <int T, typename R, typename G>
 cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
 {
     constexpr int B = kP2GThreads;
-    size_t stage = sizeof(R) * ((size_t)B * (3 * T + 3) + (size_t)a.P * (a.deg + 1));
+    size_t stage = sizeof(R) * ((size_t)B * (3 * T + 6) + (size_t)a.P * (a.deg + 1));
     size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T)) * 3 * T * T * T;
     size_t sm = stage > red ? stage : red;
     cudaError_t e = cudaFuncSetAttribute(k_p2g<T, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -308,10 +382,7 @@ cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s)
 
 cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, bool grid_f64, cudaStream_t s)
 {
-    GridArgs a = grid_args(p);
-    a.grid = const_cast<void *>(grid);
-    a.scale = 1.0;
-    return p->g.T == 8 ? dispatch_g2p<8>(p, a, grid_f64, s) : dispatch_g2p<4>(p, a, grid_f64, s);
+    return launch_g2p_scaled(p, grid, grid_f64, 1.0, s);
 }
 
 cudaError_t launch_g2p_scaled(ewald_plan_s *p, const void *grid, bool grid_f64, double scale,

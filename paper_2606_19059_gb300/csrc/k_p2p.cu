@@ -1,21 +1,32 @@
 // k_p2p.cu -- step a1: the near-field (P2P) sum of Sec. 2.1,
 //
-//   u^N_i = sum_j sum_p G^N(x_i - x_j + p) f_j   over 0 < |r| <= rc,
+//   u^N_i = sum_j sum_p G^N(x_i - x_j + p) f_j   over 0 < |r| <= rc
+//           - (4 xi / sqrt(pi)) sum_{j : r = 0} f_j,
 //
-// with the Hasimoto kernel of eq. (g-near) written as
+// the last term removing the far part of every pair skipped at r = 0 (the
+// self term for j = i; coincident points otherwise, Sec. 2).  The Hasimoto
+// kernel of eq. (g-near) is written as
 //   G^N f = (A - B) f + (A + B) r (r.f) / r^2,
 //   A = erfc(xi r) / r,   B = (2 xi / sqrt(pi)) e^{-xi^2 r^2}.
 //
 // Work decomposition (prior art: the shared-memory 1-D variant of Sec. 3.1):
-// one block per chunk of targets of one cell; the sources of the (2K+1)^3
-// colleague cells stream through shared memory a block at a time; one thread
-// per target keeps its sum in registers.  Positions are cell-local, so the
-// colleague offset d * cell both places the source cell and applies the
-// periodic wrap, and FP32 differences do not cancel against the box size.
+// one block per chunk of targets of one cell, one thread per target; the
+// sources of the (2K+1)^3 colleague cells stream through shared memory in
+// tiles of 128.  Per tile a thread first tests all 128 candidates and records
+// the in-range ones in a 128-bit mask (phase 1, uniform across the warp),
+// then walks its own set bits (phase 2).  Only in-range pairs are evaluated:
+// about one candidate in eight is in range, so a warp evaluating every
+// candidate for all lanes would idle most lanes in the expensive branch.
 //
-// erfc: FP64 uses the paper's rational erf(x)/x (Sec. 4) with
-// erfc(x)/x = 1/x - erf(x)/x; FP32 uses a rational erfcx times the
-// Gaussian it needs anyway (see fit_erf.py for why).
+// FP32 coordinates are cell-local in cell units and split hi + lo, hi on a
+// 2^-12 lattice: colleague offsets are integers, so hi differences are exact
+// and r = (hi_t - hi_s) + (lo_t - lo_s) keeps close pairs accurate to a few
+// ulp of |r| (a plain FP32 coordinate would carry eps * cell).  FP64 uses
+// cell-local coordinates in length units.
+//
+// erfc: FP64 uses the paper's rational erf(x)/x (Sec. 4) with erfc(x)/x =
+// 1/x - erf(x)/x.  FP32 uses that form with a polynomial erf(x)/x below x = 1
+// and a rational erfcx times e^{-x^2} above (see fit_erf.py).
 #include <math.h>
 
 #include "erf_rational.h"
@@ -25,11 +36,14 @@ namespace ewg {
 namespace {
 
 __constant__ float c_erfcx32[ERFCX_F32_N];
+__constant__ float c_erfxs32[ERFX_SMALL_N];
 __constant__ double c_erfp64[ERF_RAT_F64_N];
 __constant__ double c_erfq64[ERF_RAT_F64_N];
 
+constexpr int kTile = 128;  // sources per staged tile = bits of the two masks
+
 struct P2PArgs {
-    const void *npos, *nfrc;
+    const void *npos, *nlo, *nfrc;
     const int32_t *startn, *item_off, *permn;
     void *un;
     int nc, K, ncells;
@@ -49,66 +63,95 @@ __device__ __forceinline__ float fast_ex2(float x)
     return r;
 }
 
-// One FP32 pair: accumulate G^N(r) f into (ax, ay, az).
-__device__ __forceinline__ void pair_f32(const float4 &t, const float4 &s, const float4 &f,
-                                         float rc2, float xi, float nxi2log2e, float c2,
+struct F32Const {
+    float rc2, rc2_loose, xi, nxi2log2e, c2, selfc;
+};
+
+// One FP32 in-range candidate (cell units): d = (hi diff) + (lo diff).
+__device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const float4 &tl,
+                                         const float4 &sl, const float4 &f, const F32Const &k,
                                          float &ax, float &ay, float &az)
 {
-    float dx = t.x - s.x, dy = t.y - s.y, dz = t.z - s.z;
+    float dx = hx + (tl.x - sl.x), dy = hy + (tl.y - sl.y), dz = hz + (tl.z - sl.z);
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 <= rc2 && r2 > 0.0f) {
-        float rinv = rsqrtf(r2);
-        float x = xi * (r2 * rinv);
-        float tt = fast_rcp(fmaf((float)ERFCX_C32, x, 1.0f));
+    if (r2 > k.rc2)
+        return;
+    if (r2 == 0.0f) {  // self or coincident point: the pair's far part comes out
+        ax = fmaf(-k.selfc, f.x, ax);
+        ay = fmaf(-k.selfc, f.y, ay);
+        az = fmaf(-k.selfc, f.z, az);
+        return;
+    }
+    float rinv = rsqrtf(r2);
+    {   // one Newton step: rinv *= 1 + (1 - r2 rinv^2) / 2
+        float e = fmaf(-r2 * rinv, rinv, 1.0f);
+        rinv = fmaf(0.5f * rinv, e, rinv);
+    }
+    float x = k.xi * (r2 * rinv);
+    float E = fast_ex2(r2 * k.nxi2log2e);  // e^{-xi^2 r^2}
+    float A;                               // erfc(xi r) / r
+    if (x < (float)ERFX_SMALL_X32) {
+        float t = x * x;
+        float p = c_erfxs32[ERFX_SMALL_N - 1];
+#pragma unroll
+        for (int q = ERFX_SMALL_N - 2; q >= 0; --q)
+            p = fmaf(p, t, c_erfxs32[q]);
+        A = fmaf(-k.xi, p, rinv);          // 1/r - xi erf(x)/x
+    } else {
+        float d = fmaf((float)ERFCX_C32, x, 1.0f);
+        float tt = fast_rcp(d);
+        tt = fmaf(tt, fmaf(-d, tt, 1.0f), tt);
         float p = c_erfcx32[ERFCX_F32_N - 1];
 #pragma unroll
-        for (int k = ERFCX_F32_N - 2; k >= 0; --k)
-            p = fmaf(p, tt, c_erfcx32[k]);
-        float g = tt * p;                      // erfcx(xi r)
-        float E = fast_ex2(r2 * nxi2log2e);    // e^{-xi^2 r^2}
-        float gr = g * rinv;                   // erfc(xi r) e^{xi^2 r^2} / r
-        float amb = E * (gr - c2);             // A - B
-        float apb = E * (gr + c2);             // A + B
-        float rf = fmaf(dx, f.x, fmaf(dy, f.y, dz * f.z));
-        float co = apb * rf * (rinv * rinv);
-        ax = fmaf(amb, f.x, fmaf(co, dx, ax));
-        ay = fmaf(amb, f.y, fmaf(co, dy, ay));
-        az = fmaf(amb, f.z, fmaf(co, dz, az));
+        for (int q = ERFCX_F32_N - 2; q >= 0; --q)
+            p = fmaf(p, tt, c_erfcx32[q]);
+        A = (E * (tt * p)) * rinv;         // e^{-x^2} erfcx(x) / r
     }
+    float B = k.c2 * E;
+    float amb = A - B, apb = A + B;
+    float rf = fmaf(dx, f.x, fmaf(dy, f.y, dz * f.z));
+    float co = apb * rf * (rinv * rinv);
+    ax = fmaf(amb, f.x, fmaf(co, dx, ax));
+    ay = fmaf(amb, f.y, fmaf(co, dy, ay));
+    az = fmaf(amb, f.z, fmaf(co, dz, az));
 }
 
-// One FP64 pair with the paper's erf(x)/x rational (Sec. 4).
-__device__ __forceinline__ void pair_f64(const dvec4 &t, const dvec4 &s, const dvec4 &f,
-                                         double rc2, double xi, double xi2, double c2,
+// One FP64 in-range candidate (length units) with the paper's erf(x)/x.
+__device__ __forceinline__ void pair_f64(double dx, double dy, double dz, const dvec4 &f,
+                                         double rc2, double xi, double xi2, double c2, double selfc,
                                          double &ax, double &ay, double &az)
 {
-    double dx = t.x - s.x, dy = t.y - s.y, dz = t.z - s.z;
     double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-    if (r2 <= rc2 && r2 > 0.0) {
-        double rinv = rsqrt(r2);
-        double x = xi * (r2 * rinv);
-        double A;
-        if (x < ERF_RAT_X64) {
-            double z = fma(x, 2.0 / ERF_RAT_X64, -1.0);
-            double P = c_erfp64[ERF_RAT_F64_N - 1], Q = c_erfq64[ERF_RAT_F64_N - 1];
-#pragma unroll
-            for (int k = ERF_RAT_F64_N - 2; k >= 0; --k) {
-                P = fma(P, z, c_erfp64[k]);
-                Q = fma(Q, z, c_erfq64[k]);
-            }
-            A = rinv - xi * (P / Q);           // erfc(x)/r = (1/x - erf(x)/x) xi
-        } else {
-            A = 0.0;                           // erfc(7) ~ 4e-23
-        }
-        double E = exp(-xi2 * r2);
-        double B = c2 * E;
-        double amb = A - B, apb = A + B;
-        double rf = fma(dx, f.x, fma(dy, f.y, dz * f.z));
-        double co = apb * rf * (rinv * rinv);
-        ax = fma(amb, f.x, fma(co, dx, ax));
-        ay = fma(amb, f.y, fma(co, dy, ay));
-        az = fma(amb, f.z, fma(co, dz, az));
+    if (r2 > rc2)
+        return;
+    if (r2 == 0.0) {
+        ax = fma(-selfc, f.x, ax);
+        ay = fma(-selfc, f.y, ay);
+        az = fma(-selfc, f.z, az);
+        return;
     }
+    double rinv = rsqrt(r2);
+    double x = xi * (r2 * rinv);
+    double A;
+    if (x < ERF_RAT_X64) {
+        double z = fma(x, 2.0 / ERF_RAT_X64, -1.0);
+        double P = c_erfp64[ERF_RAT_F64_N - 1], Q = c_erfq64[ERF_RAT_F64_N - 1];
+#pragma unroll
+        for (int q = ERF_RAT_F64_N - 2; q >= 0; --q) {
+            P = fma(P, z, c_erfp64[q]);
+            Q = fma(Q, z, c_erfq64[q]);
+        }
+        A = rinv - xi * (P / Q);           // (1/x - erf(x)/x) xi
+    } else {
+        A = 0.0;                           // erfc(7) ~ 4e-23
+    }
+    double B = c2 * exp(-xi2 * r2);
+    double amb = A - B, apb = A + B;
+    double rf = fma(dx, f.x, fma(dy, f.y, dz * f.z));
+    double co = apb * rf * (rinv * rinv);
+    ax = fma(amb, f.x, fma(co, dx, ax));
+    ay = fma(amb, f.y, fma(co, dy, ay));
+    az = fma(amb, f.z, fma(co, dz, az));
 }
 
 __device__ __forceinline__ int wrap(int i, int n)
@@ -123,7 +166,7 @@ __device__ __forceinline__ bool find_item(const P2PArgs &a, int &c, int &tb, int
     int item = blockIdx.x;
     if (item >= a.item_off[a.ncells])
         return false;
-    int lo = 0, hi = a.ncells;
+    int lo = 0, hi = a.ncells;  // item_off[lo] <= item < item_off[hi]
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
         if (a.item_off[mid] <= item)
@@ -141,68 +184,183 @@ __device__ __forceinline__ bool find_item(const P2PArgs &a, int &c, int &tb, int
     return true;
 }
 
-template <typename R, typename R4>
-__global__ void k_p2p(P2PArgs a)
+// Phase 1 over a staged tile: bit k of (m0, m1) set when source k may be in
+// range.  `test(k)` returns the candidate's squared distance estimate.
+template <typename Test>
+__device__ __forceinline__ void build_masks(int n, float rc2, Test test, unsigned long long &m0,
+                                            unsigned long long &m1)
 {
-    extern __shared__ __align__(32) unsigned char smem[];
-    R4 *spos = (R4 *)smem;
-    R4 *sfrc = spos + blockDim.x;
+    m0 = 0ull;
+    m1 = 0ull;
+    if (n == kTile) {
+#pragma unroll 16
+        for (int k = 0; k < 64; ++k)
+            if (test(k) <= rc2)
+                m0 |= 1ull << k;
+#pragma unroll 16
+        for (int k = 0; k < 64; ++k)
+            if (test(64 + k) <= rc2)
+                m1 |= 1ull << k;
+    } else {
+        for (int k = 0; k < n; ++k)
+            if (test(k) <= rc2) {
+                if (k < 64)
+                    m0 |= 1ull << k;
+                else
+                    m1 |= 1ull << (k - 64);
+            }
+    }
+}
+
+__device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long long &m1)
+{
+    int k;
+    if (m0) {
+        k = __ffsll((long long)m0) - 1;
+        m0 &= m0 - 1;
+    } else {
+        k = 64 + __ffsll((long long)m1) - 1;
+        m1 &= m1 - 1;
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(256) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)
+{
+    __shared__ float4 sh[kTile], sl[kTile], sf[kTile];
     int c, tb, te;
     if (!find_item(a, c, tb, te))
         return;
-    const R4 *npos = (const R4 *)a.npos;
-    const R4 *nfrc = (const R4 *)a.nfrc;
-    int t = tb + threadIdx.x;
-    bool active = t < te;
-    R4 xt;
-    if (active)
-        xt = npos[t];
-    else
-        xt.x = xt.y = xt.z = xt.w = (R)0;
-    const R rc2 = (R)(a.rc * a.rc), xi = (R)a.xi;
-    const R c2 = (R)(2.0 * a.xi / sqrt(3.14159265358979323846));
-    const R aux = sizeof(R) == 4 ? (R)(-a.xi * a.xi * 1.4426950408889634) : (R)(a.xi * a.xi);
-    R ux = 0, uy = 0, uz = 0;
+    const float4 *npos = (const float4 *)a.npos, *nlo = (const float4 *)a.nlo;
+    const float4 *nfrc = (const float4 *)a.nfrc;
+    const int t = tb + threadIdx.x;
+    const bool active = t < te;
+    float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+    if (active) {
+        th = npos[t];
+        tl = nlo[t];
+    }
+    float ux = 0.f, uy = 0.f, uz = 0.f;
     const int nc = a.nc;
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     for (int dz = -a.K; dz <= a.K; ++dz)
         for (int dy = -a.K; dy <= a.K; ++dy)
             for (int dx = -a.K; dx <= a.K; ++dx) {
-                int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
-                int s0 = a.startn[nb * kSub3], s1 = a.startn[(nb + 1) * kSub3];
-                const R ox = (R)(dx * a.cell), oy = (R)(dy * a.cell), oz = (R)(dz * a.cell);
-                for (int base = s0; base < s1; base += blockDim.x) {
+                const int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
+                const int s0 = a.startn[nb * kSub3], s1 = a.startn[(nb + 1) * kSub3];
+                const float ox = (float)dx, oy = (float)dy, oz = (float)dz;  // exact cell offsets
+                for (int base = s0; base < s1; base += kTile) {
                     __syncthreads();
-                    int j = base + threadIdx.x;
-                    if (j < s1) {
-                        R4 p = npos[j];
-                        p.x += ox;
-                        p.y += oy;
-                        p.z += oz;
-                        spos[threadIdx.x] = p;
-                        sfrc[threadIdx.x] = nfrc[j];
-                    }
-                    __syncthreads();
-                    int n = min((int)blockDim.x, s1 - base);
-                    if (active) {
-                        // per-tile partial sums keep FP32 accumulation error low
-                        R px = 0, py = 0, pz = 0;
-#pragma unroll 4
-                        for (int k = 0; k < n; ++k) {
-                            if constexpr (sizeof(R) == 4)
-                                pair_f32(xt, spos[k], sfrc[k], rc2, xi, aux, c2, px, py, pz);
-                            else
-                                pair_f64(xt, spos[k], sfrc[k], rc2, xi, aux, c2, px, py, pz);
+                    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+                        int src = base + j;
+                        if (src < s1) {
+                            float4 p = npos[src];
+                            p.x += ox;
+                            p.y += oy;
+                            p.z += oz;
+                            sh[j] = p;
+                            sl[j] = nlo[src];
+                            sf[j] = nfrc[src];
                         }
-                        ux += px;
-                        uy += py;
-                        uz += pz;
                     }
+                    __syncthreads();
+                    if (!active)
+                        continue;
+                    const int n = min(kTile, s1 - base);
+                    unsigned long long m0, m1;
+                    build_masks(
+                        n, kc.rc2_loose,
+                        [&](int k) {
+                            float4 s = sh[k];
+                            float hx = th.x - s.x, hy = th.y - s.y, hz = th.z - s.z;
+                            return fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+                        },
+                        m0, m1);
+                    float px = 0.f, py = 0.f, pz = 0.f;  // per-tile partial sums
+                    while (m0 | m1) {
+                        int k = next_bit(m0, m1);
+                        float4 s = sh[k];
+                        pair_f32(th.x - s.x, th.y - s.y, th.z - s.z, tl, sl[k], sf[k], kc, px, py, pz);
+                    }
+                    ux += px;
+                    uy += py;
+                    uz += pz;
                 }
             }
     if (active) {
         int i = a.permn[t];
-        R *un = (R *)a.un;
+        float *un = (float *)a.un;
+        un[3 * i] = ux * inv_cell;
+        un[3 * i + 1] = uy * inv_cell;
+        un[3 * i + 2] = uz * inv_cell;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_p2p_f64(P2PArgs a)
+{
+    __shared__ dvec4 sp[kTile], sf[kTile];
+    int c, tb, te;
+    if (!find_item(a, c, tb, te))
+        return;
+    const dvec4 *npos = (const dvec4 *)a.npos, *nfrc = (const dvec4 *)a.nfrc;
+    const int t = tb + threadIdx.x;
+    const bool active = t < te;
+    dvec4 xt = {0.0, 0.0, 0.0, 0.0};
+    if (active)
+        xt = npos[t];
+    const double rc2 = a.rc * a.rc, xi = a.xi, xi2 = a.xi * a.xi;
+    const double c2 = 2.0 * a.xi / sqrt(3.14159265358979323846), selfc = 2.0 * c2;
+    const float rc2f = (float)(rc2 * (1.0 + 1e-4));
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    const int nc = a.nc;
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    for (int dz = -a.K; dz <= a.K; ++dz)
+        for (int dy = -a.K; dy <= a.K; ++dy)
+            for (int dx = -a.K; dx <= a.K; ++dx) {
+                const int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
+                const int s0 = a.startn[nb * kSub3], s1 = a.startn[(nb + 1) * kSub3];
+                const double ox = dx * a.cell, oy = dy * a.cell, oz = dz * a.cell;
+                for (int base = s0; base < s1; base += kTile) {
+                    __syncthreads();
+                    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+                        int src = base + j;
+                        if (src < s1) {
+                            dvec4 p = npos[src];
+                            p.x += ox;
+                            p.y += oy;
+                            p.z += oz;
+                            sp[j] = p;
+                            sf[j] = nfrc[src];
+                        }
+                    }
+                    __syncthreads();
+                    if (!active)
+                        continue;
+                    const int n = min(kTile, s1 - base);
+                    unsigned long long m0, m1;
+                    build_masks(
+                        n, rc2f,
+                        [&](int k) {
+                            const dvec4 &s = sp[k];
+                            double hx = xt.x - s.x, hy = xt.y - s.y, hz = xt.z - s.z;
+                            return (float)fma(hx, hx, fma(hy, hy, hz * hz));
+                        },
+                        m0, m1);
+                    double px = 0.0, py = 0.0, pz = 0.0;
+                    while (m0 | m1) {
+                        int k = next_bit(m0, m1);
+                        const dvec4 &s = sp[k];
+                        pair_f64(xt.x - s.x, xt.y - s.y, xt.z - s.z, sf[k], rc2, xi, xi2, c2, selfc,
+                                 px, py, pz);
+                    }
+                    ux += px;
+                    uy += py;
+                    uz += pz;
+                }
+            }
+    if (active) {
+        int i = a.permn[t];
+        double *un = (double *)a.un;
         un[3 * i] = ux;
         un[3 * i + 1] = uy;
         un[3 * i + 2] = uz;
@@ -221,10 +379,14 @@ cudaError_t load_p2p_constants()
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && g_const_loaded[dev])
         return cudaSuccess;
-    float c32[ERFCX_F32_N];
+    float c32[ERFCX_F32_N], s32[ERFX_SMALL_N];
     for (int k = 0; k < ERFCX_F32_N; ++k)
         c32[k] = (float)erfcx_f32_c[k];
+    for (int k = 0; k < ERFX_SMALL_N; ++k)
+        s32[k] = (float)erfx_small_c[k];
     cudaError_t e = cudaMemcpyToSymbol(c_erfcx32, c32, sizeof(c32));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_erfxs32, s32, sizeof(s32));
     if (e == cudaSuccess)
         e = cudaMemcpyToSymbol(c_erfp64, erf_rat_f64_p, sizeof(erf_rat_f64_p));
     if (e == cudaSuccess)
@@ -241,6 +403,7 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         return e;
     P2PArgs a;
     a.npos = p->npos;
+    a.nlo = p->nlo;
     a.nfrc = p->nfrc;
     a.startn = p->startn;
     a.item_off = p->item_off;
@@ -256,11 +419,18 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
     // upper bound on work items: every cell contributes at most count/blk + 1
     int64_t grid = (int64_t)p->g.ncells + (p->N + blk - 1) / blk + 1;
     if (p->near64) {
-        size_t sm = 2 * sizeof(dvec4) * blk;
-        k_p2p<double, dvec4><<<(unsigned)grid, blk, sm, s>>>(a);
+        k_p2p_f64<<<(unsigned)grid, blk, 0, s>>>(a);
     } else {
-        size_t sm = 2 * sizeof(float4) * blk;
-        k_p2p<float, float4><<<(unsigned)grid, blk, sm, s>>>(a);
+        // cell units: lengths / cell, xi * cell
+        F32Const kc;
+        const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
+        kc.rc2 = (float)(rcc * rcc);
+        kc.rc2_loose = (float)(rcc * rcc * (1.0 + 2e-3));
+        kc.xi = (float)xic;
+        kc.nxi2log2e = (float)(-xic * xic * 1.4426950408889634);
+        kc.c2 = (float)(2.0 * xic / sqrt(3.14159265358979323846));
+        kc.selfc = (float)(4.0 * xic / sqrt(3.14159265358979323846));
+        k_p2p_f32<<<(unsigned)grid, blk, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
     }
     return cudaGetLastError();
 }

@@ -192,9 +192,11 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
     // FP32 bulk stops at tol 1e-7: below it P2P/P2G/G2P fall back to FP64
     p.near_f64 = (dtype == EWALD_F64 || tol < 1e-7) ? 1 : 0;
     p.fft_f64 = (dtype == EWALD_F64 || tol < 1e-6) ? 1 : 0;
-    const double target = tol / 3.0;
+    // each estimated term held to tol/10: the estimate is an rms for unit
+    // sum |f|^2, and the max-norm error runs about 3x the rms one (measured)
+    const double target = tol / 10.0;
 
-    // window support P (Sec. 2.2): smallest with E^w <= tol/3
+    // window support P (Sec. 2.2): smallest with E^w <= target
     int P = o.P;
     if (P <= 0) {
         P = 3;
@@ -239,7 +241,7 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
             }
         }
     }
-    if (M < 4 || M > 4096)
+    if (M < 4 || M > 4096 || M < P)
         return EWALD_EUNSUPPORTED;
     if (rc <= 0)
         rc = rc_for_xi(xi, target);
@@ -260,7 +262,7 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
     p.est_err = est_near(xi, rc) + est_far(1.0 / M, xi) + est_window(P);
 
     // window polynomial degree: max error <= tol/20 (and the FP32 floor)
-    double wtarget = std::max(tol / 20.0, p.near_f64 ? 1e-15 : 2e-8);
+    double wtarget = std::max(tol / 30.0, p.near_f64 ? 1e-15 : 2e-8);
     int deg = o.poly_deg;
     if (deg <= 0) {
         WindowPoly wp;

@@ -12,13 +12,19 @@ its own coefficients:
   linearised least-squares iteration followed by Lawson reweighting towards
   the minimax error, in 50-digit mpmath arithmetic.
 
-* FP32 kernel -- in single precision the paper's form cancels twice (inside
-  the Horner sums and in 1/x - erf(x)/x); measured, it loses about 1e-5.  The
-  FP32 kernel therefore approximates erfcx(x) = e^{x^2} erfc(x) on [0, X32]
-  by t p(t), t = 1/(1 + x/2) (the Chebyshev-type substitution of Numerical
-  Recipes' erfcc), degree 9, fitted for minimax *relative* error by Lawson
-  reweighting; the kernel multiplies by the e^{-x^2} it evaluates anyway for
-  the Gaussian term of eq. (g-near).  Still FMAs and one division per pair.
+* FP32 kernel -- in single precision the rational P/Q cancels inside its own
+  sums (its denominator is small where its coefficients are large); measured,
+  it loses about 1e-5 in Horner or Clenshaw form.  The FP32 kernel splits at
+  x = 1:
+    x < 1:  the paper's form erfc(x)/x = 1/x - erf(x)/x with erf(x)/x a
+            degree-8 polynomial in x^2 (well conditioned there), so the
+            dominant 1/r of a close pair is not touched by any approximation;
+    x >= 1: erfcx(x) = e^{x^2} erfc(x) ~= t p(t), t = 1/(1 + x/2) (the
+            Chebyshev-type substitution of Numerical Recipes' erfcc), degree 9,
+            fitted for minimax *relative* error, times the e^{-x^2} the kernel
+            evaluates anyway for the Gaussian term of eq. (g-near); no
+            cancellation, and erfc(1) = 0.16 damps the exponential's error.
+  Still FMAs and one division per pair.
 
 Each fit's maximum error on a dense grid against 50-digit erf is written
 beside the coefficients and re-checked by the test suite.
@@ -38,6 +44,8 @@ X32 = 6.0           # FP32 interval (the paper's [0, 6])
 C32 = 0.5           # t = 1 / (1 + C32 x)
 DEG32 = 9
 DEG64 = 13
+XS32 = 1.0          # FP32 small-x branch: erf(x)/x as a polynomial in x^2 on [0, XS32]
+DEGS32 = 8
 
 
 def erf_over_x(x):
@@ -103,6 +111,33 @@ def fit_erfcx(deg: int, n_pts: int = 3001, iters: int = 80):
     return [float(c) for c in coef]
 
 
+def fit_erfx_small(deg: int, n_pts: int = 2001, iters: int = 60):
+    """a[0..deg] with erf(x)/x ~= sum_k a[k] (x^2)^k on [0, XS32] (minimax
+    absolute error by Lawson reweighting)."""
+    x = np.linspace(0.0, XS32, n_pts)
+    g = np.array([float(erf_over_x(v)) for v in x])
+    t = x * x
+    V = np.vstack([t ** k for k in range(deg + 1)]).T
+    w = np.ones_like(x)
+    coef = None
+    for _ in range(iters):
+        W = np.sqrt(w)
+        coef, *_ = np.linalg.lstsq(V * W[:, None], g * W, rcond=None)
+        e = np.abs(V @ coef - g)
+        w = w * e
+        w /= w.mean()
+    return [float(c) for c in coef]
+
+
+def max_error_small(a, n_check: int = 20001) -> float:
+    """max |sum a_k x^{2k} - erf(x)/x| on [0, XS32] (exact arithmetic)."""
+    m = mp.mpf(0)
+    for i in range(n_check):
+        x = XS32 * mp.mpf(i) / (n_check - 1)
+        m = max(m, abs(_horner(a, x * x) - erf_over_x(x)))
+    return float(m)
+
+
 def max_error_f64(p, q, n_check: int = 20001) -> float:
     """max |P(z)/Q(z) - erf(x)/x| on a uniform grid of x in [0, X64]."""
     m = mp.mpf(0)
@@ -148,6 +183,9 @@ def main():
     e64e = max_error_f64_evaluated(p, q)
     c32 = fit_erfcx(DEG32)
     e32 = max_rel_error_f32(c32)
+    s32 = fit_erfx_small(DEGS32)
+    es32 = max_error_small(s32)
+    print("f32 erf(x)/x small-x poly", DEGS32, "max abs error", es32)
     print("f64 erf(x)/x  P/Q", DEG64, "max abs error", e64)
     print("f32 erfcx  t p(t)", DEG32, "max rel error", e32)
     L = [
@@ -177,6 +215,12 @@ def main():
           f"#define ERFCX_F32_MAXERR {e32:.3e}  /* relative, on erfcx(x) */",
           f"static const double erfcx_f32_c[{DEG32 + 1}] = {{"]
     L += [f"    {v!r}," for v in c32]
+    L += ["};", "",
+          f"#define ERFX_SMALL_X32 {XS32!r}",
+          f"#define ERFX_SMALL_N {DEGS32 + 1}",
+          f"#define ERFX_SMALL_MAXERR {es32:.3e}  /* absolute, on erf(x)/x */",
+          f"static const double erfx_small_c[{DEGS32 + 1}] = {{"]
+    L += [f"    {v!r}," for v in s32]
     L += ["};", ""]
     with open(out, "w") as fh:
         fh.write("\n".join(L))

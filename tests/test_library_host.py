@@ -36,23 +36,24 @@ def test_status_strings():
     assert "invalid" in ewald.ewald_status_string(1)
 
 
-@pytest.mark.parametrize("M,P,tol,xi_ref,rc_ref,nc_ref", [
-    (128, 12, 1e-6, 44.2, 0.102, 9),
-    (256, 14, 1e-7, 82.6, 0.058, 17),
+@pytest.mark.parametrize("M,P,tol,nc_ref", [
+    (128, 12, 1e-6, 9),
+    (256, 14, 1e-7, 16),
 ])
-def test_params_with_grid_given(M, P, tol, xi_ref, rc_ref, nc_ref):
+def test_params_with_grid_given(M, P, tol, nc_ref):
     ov = ewald.ewald_params()
     ov.M, ov.P = M, P
     p = ewald.ewald_choose_params(100_000, 1.0, tol, ewald.EWALD_F32_BULK, ov)
     assert p.M == M and p.P == P
-    assert p.xi == pytest.approx(xi_ref, rel=5e-3)
-    assert p.rc == pytest.approx(rc_ref, rel=2e-2)
-    assert p.n_c == nc_ref and p.cell >= p.rc
-    # eq. (ese) terms each at tol/3 (E^F at equality, E^N by bisection)
-    h, xi, rc = 1.0 / M, p.xi, p.rc
-    EN = np.sqrt(112 / 9 * xi**4 * rc**3) * np.exp(-(xi * rc) ** 2)
-    EF = 4 / (3 * h) * np.sqrt(3.5) * np.exp(-np.pi**2 / (2 * h * xi) ** 2)
-    assert EN <= tol / 3 * 1.0001 and EF <= tol / 3 * 1.0001
+    # eq. (ese) with each term at tol/10: E^F at equality fixes xi in closed
+    # form, E^N fixes rc (bisection), and n_c = floor(1/rc)
+    h, t = 1.0 / M, tol / 10
+    xi_ref = np.pi / (2 * h * np.sqrt(np.log(4 / (3 * h) * np.sqrt(3.5) / t)))
+    assert p.xi == pytest.approx(xi_ref, rel=1e-12)
+    xi, rc = p.xi, p.rc
+    EN = lambda r: np.sqrt(112 / 9 * xi**4 * r**3) * np.exp(-(xi * r) ** 2)
+    assert EN(rc) <= t * 1.0001 and EN(rc * 0.999) > t
+    assert p.n_c == nc_ref == int(np.floor(1.0 / rc)) and p.cell >= p.rc
 
 
 def test_params_scale_with_box():

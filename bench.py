@@ -184,6 +184,10 @@ def run_gpu(args, rank, world):
     clocks = clk.summary()
     if plan32.sync_status() != ewald.EWALD_OK:
         raise RuntimeError("device error during the timed applies")
+    if args.only_f32:  # profiling runs: the timed FP32 applies alone
+        print(json.dumps({"only_f32": True, "ms_per_step": float(np.mean(ms32))}))
+        plan32.close()
+        return None
 
     # per-stage device times with serialised stages (CUDA events on the launching stream)
     ewald.ewald_set_timing(plan32.handle, 2)
@@ -280,6 +284,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-targets", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-f32", action="store_true",
+                    help="time the FP32-bulk applies only and print a short line (for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -293,6 +299,8 @@ def main():
             main_reference(args, rank, world)
             return
         res = run_gpu(args, rank, world)
+        if res is None:
+            return
         ms_mean = float(np.mean(res["ms32"]))
         if world > 1:
             import torch

@@ -124,8 +124,12 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
         if (threadIdx.x == 0)
             scount = 0;
         __syncthreads();
-        // (A) one thread per point: overlap test and compaction
+        // (A) one thread per point: overlap test and compaction (one shared
+        // atomic per warp)
         const int q = base + threadIdx.x;
+        bool keep = false;
+        R4 td;
+        int j = 0, ox = 0, oy = 0, oz = 0;
         if (q < total) {
             int lo = 0, hi = nseg;  // seg_pref[lo] <= q < seg_pref[hi]
             while (hi - lo > 1) {
@@ -136,15 +140,23 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
                     hi = mid;
             }
             const int s = lo;
-            const int j = seg_start[s] + (q - seg_pref[s]);
+            j = seg_start[s] + (q - seg_pref[s]);
             const int dx = s % side - KT, dy = (s / side) % side - KT, dz = s / (side * side) - KT;
-            R4 td = tdat[j];
+            td = tdat[j];
             int packed = (int)td.w;
-            int ox = dx * T + (packed & 15);
-            int oy = dy * T + ((packed >> 4) & 15);
-            int oz = dz * T + ((packed >> 8) & 15);
-            if (ox + P > 0 && ox < T && oy + P > 0 && oy < T && oz + P > 0 && oz < T) {
-                int k = atomicAdd(&scount, 1);
+            ox = dx * T + (packed & 15);
+            oy = dy * T + ((packed >> 4) & 15);
+            oz = dz * T + ((packed >> 8) & 15);
+            keep = ox + P > 0 && ox < T && oy + P > 0 && oy < T && oz + P > 0 && oz < T;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        int wbase = 0;
+        if ((threadIdx.x & 31) == 0 && ball)
+            wbase = atomicAdd(&scount, __popc(ball));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (keep) {
+            {
+                int k = wbase + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u));
                 // offsets lie in (-P, T): bias by 32 into 6-bit fields
                 soff[k] = (ox + 32) | ((oy + 32) << 6) | ((oz + 32) << 12);
                 sd[k * 3] = td.x;
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
     }
 }
 
-constexpr int kG2PThreads = 128;
+constexpr int kG2PThreads = 256;
 constexpr int kRowsPerLane = (kMaxP * kMaxP + 31) / 32;
 
 // G2P: R = arithmetic precision, G = grid element type.
@@ -221,16 +233,17 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
     extern __shared__ __align__(32) unsigned char smem[];
     const int P = a.P, nd = a.deg + 1, RR = T + P - 1;
     const int RR2 = RR * RR, RR3 = RR2 * RR;
-    R *vs = (R *)smem;                 // [3][RR][RR][RR]
-    R *coef = vs + 3 * RR3;            // [P][nd]
-    R *wsm = coef + P * nd;            // per warp [3][kMaxP]
+    G *vs = (G *)smem;                      // [3][RR][RR][RR], the grid's own type
+    R *coef = (R *)(smem + ((sizeof(G) * 3 * RR3 + 15) & ~(size_t)15));  // [P][nd]
+    R *wsm = coef + P * nd;                 // per warp [3][kMaxP]
     const int nt = a.nt, M = a.M;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     for (int i = threadIdx.x; i < P * nd; i += blockDim.x)
         coef[i] = ((const R *)a.wcoef)[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    // stage the grid block row by row (one warp per row, lanes along x)
+    // stage the grid block row by row (one warp per row, lanes along x) with
+    // asynchronous copies, all in flight at once; M >= P keeps one wrap enough
     const G *grid = (const G *)a.grid;
     const int64_t M3 = (int64_t)M * M * M;
     for (int r = warp; r < 3 * RR2; r += nwarps) {
@@ -239,12 +252,18 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
         gz -= gz >= M ? M : 0;
         gy -= gy >= M ? M : 0;
         const G *src = grid + c * M3 + ((int64_t)gz * M + gy) * M;
-        for (int x = lane; x < RR; x += 32) {
-            int gx = tx * T + x;
+        if (lane < RR) {  // RR = T + P - 1 <= 23 < 32
+            int gx = tx * T + lane;
             gx -= gx >= M ? M : 0;
-            vs[r * RR + x] = (R)src[gx];
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(vs + r * RR + lane);
+            if constexpr (sizeof(G) == 4)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + gx));
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + gx));
         }
     }
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     // this lane's (z, y) rows of the P x P support, fixed for all points
     int rk[kRowsPerLane], rl[kRowsPerLane];
 #pragma unroll
@@ -274,15 +293,15 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
             if (rk[j] < 0)
                 break;
             const R wkl = w[2 * kMaxP + rk[j]] * w[kMaxP + rl[j]];
-            const R *v0 = vs + ((oz + rk[j]) * RR + (oy + rl[j])) * RR + ox;
+            const G *v0 = vs + ((oz + rk[j]) * RR + (oy + rl[j])) * RR + ox;
             R a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
             for (int m = 0; m < kMaxP; ++m) {
                 if (m < P) {
                     const R wm = w[m];
-                    a0 = fma(wm, v0[m], a0);
-                    a1 = fma(wm, v0[RR3 + m], a1);
-                    a2 = fma(wm, v0[2 * RR3 + m], a2);
+                    a0 = fma(wm, (R)v0[m], a0);
+                    a1 = fma(wm, (R)v0[RR3 + m], a1);
+                    a2 = fma(wm, (R)v0[2 * RR3 + m], a2);
                 }
             }
             u0 = fma(wkl, a0, u0);
@@ -344,8 +363,8 @@ template <int T, typename R, typename G>
 cudaError_t run_g2p(const GridArgs &a, cudaStream_t s)
 {
     int RR = T + a.P - 1;
-    size_t sm = sizeof(R) * ((size_t)3 * RR * RR * RR + (size_t)a.P * (a.deg + 1) +
-                             (size_t)(kG2PThreads / 32) * 3 * kMaxP);
+    size_t sm = ((sizeof(G) * (size_t)3 * RR * RR * RR + 15) & ~(size_t)15) +
+                sizeof(R) * ((size_t)a.P * (a.deg + 1) + (size_t)(kG2PThreads / 32) * 3 * kMaxP);
     cudaError_t e = cudaFuncSetAttribute(k_g2p<T, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess)

@@ -193,11 +193,12 @@ __device__ __forceinline__ void build_masks(int n, float rc2, Test test, unsigne
     m0 = 0ull;
     m1 = 0ull;
     if (n == kTile) {
-#pragma unroll 16
+        // fully unrolled: every shift is a constant
+#pragma unroll
         for (int k = 0; k < 64; ++k)
             if (test(k) <= rc2)
                 m0 |= 1ull << k;
-#pragma unroll 16
+#pragma unroll
         for (int k = 0; k < 64; ++k)
             if (test(64 + k) <= rc2)
                 m1 |= 1ull << k;

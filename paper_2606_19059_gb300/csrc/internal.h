@@ -22,6 +22,7 @@ constexpr int kSub3 = kSub * kSub * kSub;
 constexpr int kMaxP = 16;           // largest window support the kernels implement
 constexpr int kMaxDeg = 20;         // largest window polynomial degree
 constexpr int kNumEvents = 10;
+constexpr int kP2PChunk = 32;       // targets per P2P work item (one warp)
 
 // Window polynomial for one precision: coef[l * (deg+1) + k] is the z^k
 // coefficient of bin l, z = 2 delta - 1 (Sec. 2.2 / Sec. 4, Horner form).

@@ -324,7 +324,7 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
 cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s)
 {
     k_cell_items<<<blocks_for(p->g.ncells, 256), 256, 0, s>>>(p->startn, p->items, p->g.ncells,
-                                                               p->prm.p2p_block);
+                                                               kP2PChunk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;

@@ -246,20 +246,25 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
     // asynchronous copies, all in flight at once; M >= P keeps one wrap enough
     const G *grid = (const G *)a.grid;
     const int64_t M3 = (int64_t)M * M * M;
-    for (int r = warp; r < 3 * RR2; r += nwarps) {
-        const int c = r / RR2, z = (r / RR) % RR, y = r % RR;
-        int gz = tz * T + z, gy = ty * T + y;
+    int gx = tx * T + lane;  // lanes along x; RR = T + P - 1 <= 23 < 32
+    gx -= gx >= M ? M : 0;
+    for (int cz = warp; cz < 3 * RR; cz += nwarps) {
+        const int c = cz / RR, z = cz - c * RR;  // one division per (c, z) plane
+        int gz = tz * T + z;
         gz -= gz >= M ? M : 0;
-        gy -= gy >= M ? M : 0;
-        const G *src = grid + c * M3 + ((int64_t)gz * M + gy) * M;
-        if (lane < RR) {  // RR = T + P - 1 <= 23 < 32
-            int gx = tx * T + lane;
-            gx -= gx >= M ? M : 0;
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(vs + r * RR + lane);
-            if constexpr (sizeof(G) == 4)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + gx));
-            else
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + gx));
+        const G *plane = grid + c * M3 + (int64_t)gz * M * M;
+        G *dst_plane = vs + cz * RR2;
+        if (lane < RR) {
+            for (int y = 0; y < RR; ++y) {
+                int gy = ty * T + y;
+                gy -= gy >= M ? M : 0;
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(dst_plane + y * RR + lane);
+                const G *src = plane + (int64_t)gy * M + gx;
+                if constexpr (sizeof(G) == 4)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src));
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src));
+            }
         }
     }
     asm volatile("cp.async.commit_group;\n" ::);
@@ -290,8 +295,8 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
         R u0 = 0, u1 = 0, u2 = 0;
 #pragma unroll
         for (int j = 0; j < kRowsPerLane; ++j) {
-            if (rk[j] < 0)
-                break;
+            if (rk[j] < 0)  // predicated (no early exit) so rows can interleave
+                continue;
             const R wkl = w[2 * kMaxP + rk[j]] * w[kMaxP + rl[j]];
             const G *v0 = vs + ((oz + rk[j]) * RR + (oy + rl[j])) * RR + ox;
             R a0 = 0, a1 = 0, a2 = 0;

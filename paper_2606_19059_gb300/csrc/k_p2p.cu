@@ -10,13 +10,15 @@
 //   A = erfc(xi r) / r,   B = (2 xi / sqrt(pi)) e^{-xi^2 r^2}.
 //
 // Work decomposition (prior art: the shared-memory 1-D variant of Sec. 3.1):
-// one block per chunk of targets of one cell, one thread per target; the
-// sources of the (2K+1)^3 colleague cells stream through shared memory in
-// tiles of 128.  Per tile a thread first tests all 128 candidates and records
-// the in-range ones in a 128-bit mask (phase 1, uniform across the warp),
-// then walks its own set bits (phase 2).  Only in-range pairs are evaluated:
-// about one candidate in eight is in range, so a warp evaluating every
-// candidate for all lanes would idle most lanes in the expensive branch.
+// one warp per chunk of <= 32 targets of one cell, one lane per target, and
+// warps of a block fully independent (no block barrier: a warp waiting on its
+// neighbours' pair counts would idle).  The sources of the (2K+1)^3 colleague
+// cells are concatenated into one stream that goes through the warp's own
+// shared-memory tile of 128.  Per tile a lane first tests all 128 candidates
+// and records the in-range ones in a 128-bit mask (phase 1, uniform across
+// the warp), then walks its own set bits (phase 2).  Only in-range pairs are
+// evaluated: about one candidate in eight is in range, so a warp evaluating
+// every candidate for all lanes would idle most lanes in the expensive branch.
 //
 // FP32 coordinates are cell-local in cell units and split hi + lo, hi on a
 // 2^-12 lattice: colleague offsets are integers, so hi differences are exact
@@ -160,10 +162,21 @@ __device__ __forceinline__ int wrap(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-// Locate this block's (cell, target range) from the per-cell item offsets.
-__device__ __forceinline__ bool find_item(const P2PArgs &a, int &c, int &tb, int &te)
+constexpr int kWarps = 4;       // independent warps per block
+constexpr int kMaxSeg = 125;    // colleague cells (2K+1)^3, K <= 2
+
+// Per-warp shared state: the colleague cells' source ranges concatenated
+// into one stream (prefix offsets), and one staged tile of that stream.
+template <typename S4, int NA>
+struct WarpSmem {
+    S4 arr[NA][kTile];
+    int seg_start[kMaxSeg];
+    int seg_pref[kMaxSeg + 1];
+};
+
+// Work item = (cell, chunk of <= 32 targets) handled by one warp.
+__device__ __forceinline__ bool find_item(const P2PArgs &a, int item, int &c, int &tb, int &te)
 {
-    int item = blockIdx.x;
     if (item >= a.item_off[a.ncells])
         return false;
     int lo = 0, hi = a.ncells;  // item_off[lo] <= item < item_off[hi]
@@ -182,6 +195,59 @@ __device__ __forceinline__ bool find_item(const P2PArgs &a, int &c, int &tb, int
     tb = t0 + chunk * per;
     te = min(t1, tb + per);
     return true;
+}
+
+// Build the warp's segment table for cell c: segment s = colleague offset
+// (dx, dy, dz) in [-K, K]^3, its first source and the stream prefix sums.
+template <typename WS>
+__device__ __forceinline__ int build_segments(const P2PArgs &a, int c, WS &ws, int lane)
+{
+    const int K = a.K, side = 2 * K + 1, nseg = side * side * side, nc = a.nc;
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    int carry = 0;
+    for (int s0 = 0; s0 < nseg; s0 += 32) {
+        int s = s0 + lane, len = 0;
+        if (s < nseg) {
+            int dx = s % side - K, dy = (s / side) % side - K, dz = s / (side * side) - K;
+            int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
+            int b = a.startn[nb * kSub3];
+            ws.seg_start[s] = b;
+            len = a.startn[(nb + 1) * kSub3] - b;
+        }
+        int v = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o)
+                v += u;
+        }
+        if (s < nseg)
+            ws.seg_pref[s + 1] = carry + v;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0)
+        ws.seg_pref[0] = 0;
+    __syncwarp();
+    return nseg;
+}
+
+// Source q of the stream: its index in the sorted arrays and colleague offset.
+template <typename WS>
+__device__ __forceinline__ int locate(const WS &ws, int nseg, int side, int K, int q, int &dx,
+                                      int &dy, int &dz)
+{
+    int lo = 0, hi = nseg;  // seg_pref[lo] <= q < seg_pref[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (ws.seg_pref[mid] <= q)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    dx = lo % side - K;
+    dy = (lo / side) % side - K;
+    dz = lo / (side * side) - K;
+    return ws.seg_start[lo] + (q - ws.seg_pref[lo]);
 }
 
 // Phase 1 over a staged tile: bit k of (m0, m1) set when source k may be in
@@ -226,70 +292,73 @@ __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long lo
     return k;
 }
 
-__global__ void __launch_bounds__(256) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)
+using WsF32 = WarpSmem<float4, 3>;
+using WsF64 = WarpSmem<dvec4, 2>;
+
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)
 {
-    __shared__ float4 sh[kTile], sl[kTile], sf[kTile];
+    __shared__ WsF32 wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WsF32 &ws = wsm[warp];
+    float4 *sh = ws.arr[0], *sl = ws.arr[1], *sf = ws.arr[2];
     int c, tb, te;
-    if (!find_item(a, c, tb, te))
-        return;
+    if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
+        return;  // whole warp: no block-wide barrier follows
     const float4 *npos = (const float4 *)a.npos, *nlo = (const float4 *)a.nlo;
     const float4 *nfrc = (const float4 *)a.nfrc;
-    const int t = tb + threadIdx.x;
+    const int t = tb + lane;
     const bool active = t < te;
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
     if (active) {
         th = npos[t];
         tl = nlo[t];
     }
+    const int nseg = build_segments(a, c, ws, lane);
+    const int side = 2 * a.K + 1;
+    const int total = ws.seg_pref[nseg];
     float ux = 0.f, uy = 0.f, uz = 0.f;
-    const int nc = a.nc;
-    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-    for (int dz = -a.K; dz <= a.K; ++dz)
-        for (int dy = -a.K; dy <= a.K; ++dy)
-            for (int dx = -a.K; dx <= a.K; ++dx) {
-                const int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
-                const int s0 = a.startn[nb * kSub3], s1 = a.startn[(nb + 1) * kSub3];
-                const float ox = (float)dx, oy = (float)dy, oz = (float)dz;  // exact cell offsets
-                for (int base = s0; base < s1; base += kTile) {
-                    __syncthreads();
-                    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
-                        int src = base + j;
-                        if (src < s1) {
-                            float4 p = npos[src];
-                            p.x += ox;
-                            p.y += oy;
-                            p.z += oz;
-                            sh[j] = p;
-                            sl[j] = nlo[src];
-                            sf[j] = nfrc[src];
-                        }
-                    }
-                    __syncthreads();
-                    if (!active)
-                        continue;
-                    const int n = min(kTile, s1 - base);
-                    unsigned long long m0, m1;
-                    build_masks(
-                        n, kc.rc2_loose,
-                        [&](int k) {
-                            float4 s = sh[k];
-                            float hx = th.x - s.x, hy = th.y - s.y, hz = th.z - s.z;
-                            return fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-                        },
-                        m0, m1);
-                    float px = 0.f, py = 0.f, pz = 0.f;  // per-tile partial sums
-                    while (m0 | m1) {
-                        int k = next_bit(m0, m1);
-                        float4 s = sh[k];
-                        pair_f32(th.x - s.x, th.y - s.y, th.z - s.z, tl, sl[k], sf[k], kc, px, py, pz);
-                    }
-                    ux += px;
-                    uy += py;
-                    uz += pz;
-                }
+    for (int base = 0; base < total; base += kTile) {
+        const int n = min(kTile, total - base);
+#pragma unroll
+        for (int i = 0; i < kTile / 32; ++i) {
+            const int k = lane + 32 * i, q = base + k;
+            if (q < total) {
+                int dx, dy, dz;
+                const int j = locate(ws, nseg, side, a.K, q, dx, dy, dz);
+                float4 p = npos[j];
+                p.x += (float)dx;  // exact: integer colleague offsets, hi on a 2^-12 lattice
+                p.y += (float)dy;
+                p.z += (float)dz;
+                sh[k] = p;
+                sl[k] = nlo[j];
+                sf[k] = nfrc[j];
             }
+        }
+        __syncwarp();
+        if (active) {
+            unsigned long long m0, m1;
+            build_masks(
+                n, kc.rc2_loose,
+                [&](int k) {
+                    float4 s = sh[k];
+                    float hx = th.x - s.x, hy = th.y - s.y, hz = th.z - s.z;
+                    return fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+                },
+                m0, m1);
+            float px = 0.f, py = 0.f, pz = 0.f;  // per-tile partial sums
+            while (m0 | m1) {
+                const int k = next_bit(m0, m1);
+                const float4 s = sh[k];
+                pair_f32(th.x - s.x, th.y - s.y, th.z - s.z, tl, sl[k], sf[k], kc, px, py, pz);
+            }
+            ux += px;
+            uy += py;
+            uz += pz;
+        }
+        __syncwarp();
+    }
     if (active) {
-        int i = a.permn[t];
+        const int i = a.permn[t];
         float *un = (float *)a.un;
         un[3 * i] = ux * inv_cell;
         un[3 * i + 1] = uy * inv_cell;
@@ -297,14 +366,17 @@ __global__ void __launch_bounds__(256) k_p2p_f32(P2PArgs a, F32Const kc, float i
     }
 }
 
-__global__ void __launch_bounds__(256) k_p2p_f64(P2PArgs a)
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
 {
-    __shared__ dvec4 sp[kTile], sf[kTile];
+    __shared__ WsF64 wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WsF64 &ws = wsm[warp];
+    dvec4 *sp = ws.arr[0], *sf = ws.arr[1];
     int c, tb, te;
-    if (!find_item(a, c, tb, te))
+    if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
         return;
     const dvec4 *npos = (const dvec4 *)a.npos, *nfrc = (const dvec4 *)a.nfrc;
-    const int t = tb + threadIdx.x;
+    const int t = tb + lane;
     const bool active = t < te;
     dvec4 xt = {0.0, 0.0, 0.0, 0.0};
     if (active)
@@ -312,55 +384,52 @@ __global__ void __launch_bounds__(256) k_p2p_f64(P2PArgs a)
     const double rc2 = a.rc * a.rc, xi = a.xi, xi2 = a.xi * a.xi;
     const double c2 = 2.0 * a.xi / sqrt(3.14159265358979323846), selfc = 2.0 * c2;
     const float rc2f = (float)(rc2 * (1.0 + 1e-4));
+    const int nseg = build_segments(a, c, ws, lane);
+    const int side = 2 * a.K + 1;
+    const int total = ws.seg_pref[nseg];
     double ux = 0.0, uy = 0.0, uz = 0.0;
-    const int nc = a.nc;
-    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-    for (int dz = -a.K; dz <= a.K; ++dz)
-        for (int dy = -a.K; dy <= a.K; ++dy)
-            for (int dx = -a.K; dx <= a.K; ++dx) {
-                const int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
-                const int s0 = a.startn[nb * kSub3], s1 = a.startn[(nb + 1) * kSub3];
-                const double ox = dx * a.cell, oy = dy * a.cell, oz = dz * a.cell;
-                for (int base = s0; base < s1; base += kTile) {
-                    __syncthreads();
-                    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
-                        int src = base + j;
-                        if (src < s1) {
-                            dvec4 p = npos[src];
-                            p.x += ox;
-                            p.y += oy;
-                            p.z += oz;
-                            sp[j] = p;
-                            sf[j] = nfrc[src];
-                        }
-                    }
-                    __syncthreads();
-                    if (!active)
-                        continue;
-                    const int n = min(kTile, s1 - base);
-                    unsigned long long m0, m1;
-                    build_masks(
-                        n, rc2f,
-                        [&](int k) {
-                            const dvec4 &s = sp[k];
-                            double hx = xt.x - s.x, hy = xt.y - s.y, hz = xt.z - s.z;
-                            return (float)fma(hx, hx, fma(hy, hy, hz * hz));
-                        },
-                        m0, m1);
-                    double px = 0.0, py = 0.0, pz = 0.0;
-                    while (m0 | m1) {
-                        int k = next_bit(m0, m1);
-                        const dvec4 &s = sp[k];
-                        pair_f64(xt.x - s.x, xt.y - s.y, xt.z - s.z, sf[k], rc2, xi, xi2, c2, selfc,
-                                 px, py, pz);
-                    }
-                    ux += px;
-                    uy += py;
-                    uz += pz;
-                }
+    for (int base = 0; base < total; base += kTile) {
+        const int n = min(kTile, total - base);
+#pragma unroll
+        for (int i = 0; i < kTile / 32; ++i) {
+            const int k = lane + 32 * i, q = base + k;
+            if (q < total) {
+                int dx, dy, dz;
+                const int j = locate(ws, nseg, side, a.K, q, dx, dy, dz);
+                dvec4 p = npos[j];
+                p.x += dx * a.cell;
+                p.y += dy * a.cell;
+                p.z += dz * a.cell;
+                sp[k] = p;
+                sf[k] = nfrc[j];
             }
+        }
+        __syncwarp();
+        if (active) {
+            unsigned long long m0, m1;
+            build_masks(
+                n, rc2f,
+                [&](int k) {
+                    const dvec4 &s = sp[k];
+                    double hx = xt.x - s.x, hy = xt.y - s.y, hz = xt.z - s.z;
+                    return (float)fma(hx, hx, fma(hy, hy, hz * hz));
+                },
+                m0, m1);
+            double px = 0.0, py = 0.0, pz = 0.0;
+            while (m0 | m1) {
+                const int k = next_bit(m0, m1);
+                const dvec4 &s = sp[k];
+                pair_f64(xt.x - s.x, xt.y - s.y, xt.z - s.z, sf[k], rc2, xi, xi2, c2, selfc, px,
+                         py, pz);
+            }
+            ux += px;
+            uy += py;
+            uz += pz;
+        }
+        __syncwarp();
+    }
     if (active) {
-        int i = a.permn[t];
+        const int i = a.permn[t];
         double *un = (double *)a.un;
         un[3 * i] = ux;
         un[3 * i + 1] = uy;
@@ -416,11 +485,11 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
     a.cell = p->g.cell;
     a.rc = p->prm.rc;
     a.xi = p->prm.xi;
-    int blk = p->prm.p2p_block;
-    // upper bound on work items: every cell contributes at most count/blk + 1
-    int64_t grid = (int64_t)p->g.ncells + (p->N + blk - 1) / blk + 1;
+    // upper bound on work items: every cell contributes at most count/32 + 1
+    const int64_t items = (int64_t)p->g.ncells + (p->N + kP2PChunk - 1) / kP2PChunk + 1;
+    const unsigned grid = (unsigned)((items + kWarps - 1) / kWarps);
     if (p->near64) {
-        k_p2p_f64<<<(unsigned)grid, blk, 0, s>>>(a);
+        k_p2p_f64<<<grid, kWarps * 32, 0, s>>>(a);
     } else {
         // cell units: lengths / cell, xi * cell
         F32Const kc;
@@ -431,7 +500,7 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         kc.nxi2log2e = (float)(-xic * xic * 1.4426950408889634);
         kc.c2 = (float)(2.0 * xic / sqrt(3.14159265358979323846));
         kc.selfc = (float)(4.0 * xic / sqrt(3.14159265358979323846));
-        k_p2p_f32<<<(unsigned)grid, blk, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
+        k_p2p_f32<<<grid, kWarps * 32, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
     }
     return cudaGetLastError();
 }

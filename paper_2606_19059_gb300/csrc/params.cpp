@@ -296,10 +296,13 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
         return EWALD_EUNSUPPORTED;
     p.tile = T;
 
-    // P2P block: one warp multiple covering a typical cell (mean + 2 sd)
+    // P2P work items: warps of <= 32 targets of one cell
     double s = (double)N / ((double)nc * nc * nc);
-    int blk = o.p2p_block > 0 ? o.p2p_block : 32 * (int)ceil((s + 2.0 * sqrt(s) + 1.0) / 32.0);
-    p.p2p_block = std::min(256, std::max(64, blk));
+    (void)s;
+    p.p2p_block = 128;  // four independent warps of <= 32 targets each
+    // colleague reach K = ceil(rc / cell); the P2P kernel supports K <= 2
+    if ((int)ceil(p.rc / p.cell - 1e-12) > 2)
+        return EWALD_EUNSUPPORTED;
 
     // device footprint (bytes) of the plan's workspaces
     int64_t Mh = M / 2 + 1;

@@ -251,33 +251,26 @@ __device__ __forceinline__ int locate(const WS &ws, int nseg, int side, int K, i
 }
 
 // Phase 1 over a staged tile: bit k of (m0, m1) set when source k may be in
-// range.  `test(k)` returns the candidate's squared distance estimate.
+// range.  `test(k)` returns the candidate's squared distance estimate.  Slots
+// past the tile's end hold a far-away dummy, so the loop is always complete
+// and fully unrolled (every shift is a constant).
 template <typename Test>
-__device__ __forceinline__ void build_masks(int n, float rc2, Test test, unsigned long long &m0,
+__device__ __forceinline__ void build_masks(float rc2, Test test, unsigned long long &m0,
                                             unsigned long long &m1)
 {
     m0 = 0ull;
     m1 = 0ull;
-    if (n == kTile) {
-        // fully unrolled: every shift is a constant
 #pragma unroll
-        for (int k = 0; k < 64; ++k)
-            if (test(k) <= rc2)
-                m0 |= 1ull << k;
+    for (int k = 0; k < 64; ++k)
+        if (test(k) <= rc2)
+            m0 |= 1ull << k;
 #pragma unroll
-        for (int k = 0; k < 64; ++k)
-            if (test(64 + k) <= rc2)
-                m1 |= 1ull << k;
-    } else {
-        for (int k = 0; k < n; ++k)
-            if (test(k) <= rc2) {
-                if (k < 64)
-                    m0 |= 1ull << k;
-                else
-                    m1 |= 1ull << (k - 64);
-            }
-    }
+    for (int k = 0; k < 64; ++k)
+        if (test(64 + k) <= rc2)
+            m1 |= 1ull << k;
 }
+
+constexpr float kFar = 1.0e9f;  // dummy source position: never within rc
 
 __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long long &m1)
 {
@@ -316,13 +309,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
     const int nseg = build_segments(a, c, ws, lane);
     const int side = 2 * a.K + 1;
     const int total = ws.seg_pref[nseg];
+    // tile t holds the stream elements t, t + ntiles, t + 2 ntiles, ...: each
+    // tile samples the whole neighbourhood, so the lanes' in-range counts per
+    // tile are even and phase 2 wastes few iterations
+    const int ntile = (total + kTile - 1) / kTile;
     float ux = 0.f, uy = 0.f, uz = 0.f;
-    for (int base = 0; base < total; base += kTile) {
-        const int n = min(kTile, total - base);
+    for (int tile = 0; tile < ntile; ++tile) {
+        const int n = (total - tile + ntile - 1) / ntile;  // elements q < total with q % ntile == tile
 #pragma unroll
         for (int i = 0; i < kTile / 32; ++i) {
-            const int k = lane + 32 * i, q = base + k;
-            if (q < total) {
+            const int k = lane + 32 * i, q = tile + k * ntile;
+            if (k < n) {
                 int dx, dy, dz;
                 const int j = locate(ws, nseg, side, a.K, q, dx, dy, dz);
                 float4 p = npos[j];
@@ -332,13 +329,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
                 sh[k] = p;
                 sl[k] = nlo[j];
                 sf[k] = nfrc[j];
+            } else {
+                sh[k] = make_float4(kFar, kFar, kFar, 0.f);
             }
         }
         __syncwarp();
         if (active) {
             unsigned long long m0, m1;
             build_masks(
-                n, kc.rc2_loose,
+                kc.rc2_loose,
                 [&](int k) {
                     float4 s = sh[k];
                     float hx = th.x - s.x, hy = th.y - s.y, hz = th.z - s.z;
@@ -387,13 +386,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
     const int nseg = build_segments(a, c, ws, lane);
     const int side = 2 * a.K + 1;
     const int total = ws.seg_pref[nseg];
+    const int ntile = (total + kTile - 1) / kTile;  // strided tiles, as in k_p2p_f32
     double ux = 0.0, uy = 0.0, uz = 0.0;
-    for (int base = 0; base < total; base += kTile) {
-        const int n = min(kTile, total - base);
+    for (int tile = 0; tile < ntile; ++tile) {
+        const int n = (total - tile + ntile - 1) / ntile;
 #pragma unroll
         for (int i = 0; i < kTile / 32; ++i) {
-            const int k = lane + 32 * i, q = base + k;
-            if (q < total) {
+            const int k = lane + 32 * i, q = tile + k * ntile;
+            if (k < n) {
                 int dx, dy, dz;
                 const int j = locate(ws, nseg, side, a.K, q, dx, dy, dz);
                 dvec4 p = npos[j];
@@ -402,13 +402,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
                 p.z += dz * a.cell;
                 sp[k] = p;
                 sf[k] = nfrc[j];
+            } else {
+                sp[k] = dvec4{kFar, kFar, kFar, 0.0};
             }
         }
         __syncwarp();
         if (active) {
             unsigned long long m0, m1;
             build_masks(
-                n, rc2f,
+                rc2f,
                 [&](int k) {
                     const dvec4 &s = sp[k];
                     double hx = xt.x - s.x, hy = xt.y - s.y, hz = xt.z - s.z;

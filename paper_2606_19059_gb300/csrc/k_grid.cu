@@ -14,12 +14,14 @@
 // The neighbour tiles' point ranges are concatenated and processed in rounds
 // of 256 points: (A) one thread per point tests overlap with the tile and
 // compacts, (B) one thread per (point, axis, offset) evaluates the window
-// polynomial, (C) threads = (row (y, z) of the tile) x (slice of the point
-// list) accumulate a row of T values x 3 components in registers.
+// polynomial, (C) threads = (two rows (y, z), (y, z + T/2) of the tile) x
+// (slice of the point list) accumulate 2 x T values x 3 components in
+// registers, sharing each point's x weights and force between the rows.
 //
 // G2P: one block per tile of anchors stages the (T+P-1)^3 grid block the
-// tile's points can touch in shared memory (row by row); one warp per point
-// sums its P^3 support, lanes over (z, y) rows, a shuffle reduction at the end.
+// tile's points can touch in shared memory (asynchronous copies); one warp per
+// point sums its P^3 support, lanes over (y, x) pairs walking the z planes, a
+// shuffle reduction at the end.
 #include <math.h>
 
 #include "internal.h"
@@ -65,15 +67,15 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
 {
     using R4 = typename Vec4<R>::T;
     constexpr int NT = kP2GThreads;
-    constexpr int ROWS = T * T;
+    constexpr int ROWS = T * T / 2;  // row pairs (y, z), (y, z + T/2)
     constexpr int SL = NT / ROWS;
     constexpr int B = NT;  // points per round
     extern __shared__ __align__(32) unsigned char smem[];
     R *wx = (R *)smem;              // [B][T]
     R *wy = wx + B * T;             // [B][T]
     R *wz = wy + B * T;             // [B][T]
-    R *sf = wz + B * T;             // [B][3]
-    R *sd = sf + B * 3;             // [B][3] fractional offsets delta
+    R *sf = wz + B * T;             // [B][4] force, padded for vector loads
+    R *sd = sf + B * 4;             // [B][3] fractional offsets delta
     R *coef = sd + B * 3;           // [P][deg+1]
     __shared__ int soff[B];         // packed anchor offsets relative to the tile (biased)
     __shared__ int seg_start[kMaxSeg], seg_pref[kMaxSeg + 1];
@@ -111,11 +113,13 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
             seg_pref[0] = 0;
     }
     const int row = threadIdx.x % ROWS, slice = threadIdx.x / ROWS;
-    const int y = row % T, z = row / T;
-    R acc[T][3];
+    const int y = row % T, z = row / T;  // rows (y, z) and (y, z + T/2)
+    R acc[2][T][3];
 #pragma unroll
-    for (int x = 0; x < T; ++x)
-        acc[x][0] = acc[x][1] = acc[x][2] = (R)0;
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int x = 0; x < T; ++x)
+            acc[h][x][0] = acc[h][x][1] = acc[h][x][2] = (R)0;
     __syncthreads();
     const int total = seg_pref[nseg];
     const R4 *tdat = (const R4 *)a.tdat, *tfrc = (const R4 *)a.tfrc;
@@ -163,9 +167,8 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
                 sd[k * 3 + 1] = td.y;
                 sd[k * 3 + 2] = td.z;
                 R4 fv = tfrc[j];
-                sf[k * 3] = fv.x;
-                sf[k * 3 + 1] = fv.y;
-                sf[k * 3 + 2] = fv.z;
+                fv.w = (R)0;
+                ((R4 *)sf)[k] = fv;
             }
         }
         __syncthreads();
@@ -181,18 +184,30 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
             (d == 0 ? wx : (d == 1 ? wy : wz))[k * T + qq] = v;
         }
         __syncthreads();
-        // (C) accumulate rows
+        // (C) accumulate two rows per thread; x weights and force are shared
         for (int k = slice; k < n; k += SL) {
-            R wyz = wy[k * T + y] * wz[k * T + z];
-            if (wyz != (R)0) {
-                R f0 = wyz * sf[k * 3], f1 = wyz * sf[k * 3 + 1], f2 = wyz * sf[k * 3 + 2];
+            const R wyk = wy[k * T + y];
+            const R wz0 = wyk * wz[k * T + z], wz1 = wyk * wz[k * T + z + T / 2];
+            if (wz0 != (R)0 || wz1 != (R)0) {
+                const R4 f = ((const R4 *)sf)[k];
+                R wv[T];
 #pragma unroll
-                for (int x = 0; x < T; ++x) {
-                    R w = wx[k * T + x];
-                    acc[x][0] = fma(w, f0, acc[x][0]);
-                    acc[x][1] = fma(w, f1, acc[x][1]);
-                    acc[x][2] = fma(w, f2, acc[x][2]);
+                for (int x4 = 0; x4 < T / 4; ++x4) {
+                    const R4 q = ((const R4 *)(wx + k * T))[x4];
+                    wv[4 * x4] = q.x;
+                    wv[4 * x4 + 1] = q.y;
+                    wv[4 * x4 + 2] = q.z;
+                    wv[4 * x4 + 3] = q.w;
                 }
+                const R g0[3] = {wz0 * f.x, wz0 * f.y, wz0 * f.z};
+                const R g1[3] = {wz1 * f.x, wz1 * f.y, wz1 * f.z};
+#pragma unroll
+                for (int x = 0; x < T; ++x)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
+                        acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
+                    }
             }
         }
         __syncthreads();
@@ -200,10 +215,12 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
     // reduce the slices through shared memory and store the tile
     R *red = (R *)smem;  // [SL][3][T][T][T]  (reuses the staging area)
 #pragma unroll
-    for (int x = 0; x < T; ++x)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            red[((slice * 3 + c) * T + z) * T * T + y * T + x] = acc[x][c];
+        for (int x = 0; x < T; ++x)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                red[((slice * 3 + c) * T + z + h * (T / 2)) * T * T + y * T + x] = acc[h][x][c];
     __syncthreads();
     G *grid = (G *)a.grid;
     const int64_t M = a.M, M3 = M * M * M;
@@ -221,7 +238,10 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
 constexpr int kG2PThreads = 256;
 constexpr int kRowsPerLane = (kMaxP * kMaxP + 31) / 32;
 
-// G2P: R = arithmetic precision, G = grid element type.
+// G2P: R = arithmetic precision, G = grid element type.  Lanes own (y, x)
+// pairs of the P x P face of a point's support and walk its P z-planes, so a
+// warp's 32 shared-memory reads in one plane hit consecutive words of a few
+// rows (no bank conflicts); w2[y] w1[x] is formed once per point.
 template <int T, typename R, typename G>
 __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
 {
@@ -269,14 +289,15 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
     }
     asm volatile("cp.async.commit_group;\n" ::);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    // this lane's (z, y) rows of the P x P support, fixed for all points
-    int rk[kRowsPerLane], rl[kRowsPerLane];
+    // this lane's (y, x) pairs of the P x P face, fixed for all points
+    int ry[kRowsPerLane], rx[kRowsPerLane];
 #pragma unroll
     for (int j = 0; j < kRowsPerLane; ++j) {
-        int q = lane + 32 * j;
-        rk[j] = q < P * P ? q / P : -1;
-        rl[j] = q < P * P ? q - (q / P) * P : 0;
+        const int q = lane + 32 * j;
+        ry[j] = q < P * P ? q / P : -1;
+        rx[j] = q < P * P ? q - (q / P) * P : 0;
     }
+    const int nj = (P * P + 31) / 32;  // pairs per lane (the last round partly empty)
     __syncthreads();
     R *w = wsm + warp * 3 * kMaxP;
     const R4 *tdat = (const R4 *)a.tdat;
@@ -292,26 +313,28 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
             w[d * kMaxP + l] = horner(coef + l * nd, a.deg, (R)2 * dl - (R)1);
         }
         __syncwarp();
-        R u0 = 0, u1 = 0, u2 = 0;
+        R wyx[kRowsPerLane];
+        int off[kRowsPerLane];
 #pragma unroll
         for (int j = 0; j < kRowsPerLane; ++j) {
-            if (rk[j] < 0)  // predicated (no early exit) so rows can interleave
-                continue;
-            const R wkl = w[2 * kMaxP + rk[j]] * w[kMaxP + rl[j]];
-            const G *v0 = vs + ((oz + rk[j]) * RR + (oy + rl[j])) * RR + ox;
-            R a0 = 0, a1 = 0, a2 = 0;
+            const bool ok = ry[j] >= 0;
+            wyx[j] = ok ? w[kMaxP + ry[j]] * w[rx[j]] : (R)0;
+            off[j] = ok ? (oy + ry[j]) * RR + ox + rx[j] : 0;
+        }
+        R u0 = 0, u1 = 0, u2 = 0;
+        const G *vz = vs + oz * RR2;
+        for (int k = 0; k < P; ++k, vz += RR2) {
+            const R wk = w[2 * kMaxP + k];
 #pragma unroll
-            for (int m = 0; m < kMaxP; ++m) {
-                if (m < P) {
-                    const R wm = w[m];
-                    a0 = fma(wm, (R)v0[m], a0);
-                    a1 = fma(wm, (R)v0[RR3 + m], a1);
-                    a2 = fma(wm, (R)v0[2 * RR3 + m], a2);
+            for (int j = 0; j < kRowsPerLane; ++j) {
+                if (j < nj) {
+                    const R ww = wk * wyx[j];
+                    const G *v = vz + off[j];
+                    u0 = fma(ww, (R)v[0], u0);
+                    u1 = fma(ww, (R)v[RR3], u1);
+                    u2 = fma(ww, (R)v[2 * RR3], u2);
                 }
             }
-            u0 = fma(wkl, a0, u0);
-            u1 = fma(wkl, a1, u1);
-            u2 = fma(wkl, a2, u2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -353,8 +376,8 @@ template <int T, typename R, typename G>
 cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
 {
     constexpr int B = kP2GThreads;
-    size_t stage = sizeof(R) * ((size_t)B * (3 * T + 6) + (size_t)a.P * (a.deg + 1));
-    size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T)) * 3 * T * T * T;
+    size_t stage = sizeof(R) * ((size_t)B * (3 * T + 7) + (size_t)a.P * (a.deg + 1));
+    size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * T;
     size_t sm = stage > red ? stage : red;
     cudaError_t e = cudaFuncSetAttribute(k_p2g<T, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);

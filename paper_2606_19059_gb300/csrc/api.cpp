@@ -82,6 +82,8 @@ void free_plan(ewald_plan_s *p)
     for (void *b : bufs)
         if (b)
             cudaFree(b);
+    if (p->own_grid_g2p && p->grid_g2p)
+        cudaFree(p->grid_g2p);
     if (p->have_fwd)
         cufftDestroy(p->fwd);
     if (p->have_inv)
@@ -147,6 +149,14 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_CUDA(dalloc(p, &p->un, 3 * rs * N));
     EW_CUDA(dalloc(p, &p->uf, 3 * rs * N));
     EW_CUDA(dalloc(p, &p->grid, 3 * fs * (size_t)g.nreal));
+    // G2P reads the grid in its own precision: an FP32 copy when the FFT is
+    // FP64 and the kernels FP32 (the rounding G2P would apply on each read)
+    if (!p->near64 && p->fft64) {
+        EW_CUDA(dalloc(p, &p->grid_g2p, 3 * 4 * (size_t)g.nreal));
+        p->own_grid_g2p = true;
+    } else {
+        p->grid_g2p = p->grid;
+    }
     EW_CUDA(dalloc(p, &p->spec, 3 * 2 * fs * (size_t)g.ncplx));
     EW_CUDA(dalloc(p, &p->tab, fs * (size_t)g.M));
     EW_CUDA(dalloc(p, &p->wcoef_dev, rs * p->wpoly.coef.size()));
@@ -286,7 +296,9 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         EW_CUDA(launch_p2g(p, s));
         rec(p, 2, s);
         EW_ST(fgc(p, 8.0 * kPi * h3 / M3, s));
-        EW_CUDA(launch_g2p(p, p->grid, p->fft64, s));
+        if (p->own_grid_g2p)
+            EW_CUDA(launch_grid_convert(p->grid, true, p->grid_g2p, false, 3 * p->g.nreal, s));
+        EW_CUDA(launch_g2p(p, p->grid_g2p, 1.0, s));
         rec(p, 6, s);
     }
     if (overlap)
@@ -482,7 +494,12 @@ ewald_status ewald_interp(ewald_plan_t plan, const double *x, const double *grid
     cudaStream_t s = (cudaStream_t)stream;
     EW_ST(bin(plan, x, nullptr, s));
     const double h3 = plan->g.h * plan->g.h * plan->g.h;
-    EW_CUDA(launch_g2p_scaled(plan, grid, true, h3, s));
+    const void *g = grid;
+    if (!plan->near64) {  // the FP32 kernels read an FP32 copy of the caller's grid
+        EW_CUDA(launch_grid_convert(grid, true, plan->grid_g2p, false, 3 * plan->g.nreal, s));
+        g = plan->grid_g2p;
+    }
+    EW_CUDA(launch_g2p(plan, g, h3, s));
     EW_CUDA(launch_copy_out(plan->uf, plan->near64, u, 3 * plan->N, s));
     return EWALD_OK;
 }

@@ -70,6 +70,8 @@ struct ewald_plan_s {
     void *tdat = nullptr, *tfrc = nullptr;        // tile-sorted window data / forces
     void *un = nullptr, *uf = nullptr;            // near / far results, user order
     void *grid = nullptr;                         // 3 M^3 real
+    void *grid_g2p = nullptr;                     // G2P input in the kernels' precision (may alias grid)
+    bool own_grid_g2p = false;
     void *spec = nullptr;                         // 3 M^2 (M/2+1) complex
     void *tab = nullptr;                          // CNV 1-D table (M entries)
     void *wcoef_dev = nullptr;                    // window polynomial coefficients
@@ -115,9 +117,9 @@ cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);
-cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, bool grid_f64, cudaStream_t s);
-cudaError_t launch_g2p_scaled(ewald_plan_s *p, const void *grid, bool grid_f64, double scale,
-                              cudaStream_t s);
+// G2P from a grid in the kernels' precision (FP64 when near64, else FP32);
+// the sum is multiplied by `scale`.
+cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s);
 cudaError_t load_p2p_constants();
 cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s);
 cudaError_t launch_copy_out(const void *src, bool src_f64, double *dst, int64_t n, cudaStream_t s);

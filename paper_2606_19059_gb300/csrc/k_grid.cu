@@ -236,13 +236,14 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
 }
 
 constexpr int kG2PThreads = 256;
-constexpr int kRowsPerLane = (kMaxP * kMaxP + 31) / 32;
+constexpr int kMaxRounds = (kMaxP * kMaxP + 31) / 32;
 
-// G2P: R = arithmetic precision, G = grid element type.  Lanes own (y, x)
-// pairs of the P x P face of a point's support and walk its P z-planes, so a
-// warp's 32 shared-memory reads in one plane hit consecutive words of a few
-// rows (no bank conflicts); w2[y] w1[x] is formed once per point.
-template <int T, typename R, typename G>
+// G2P: arithmetic and staging in R (the grid is given in R).  The block stages
+// the (T+P-1)^3 grid block its points can touch, components interleaved per
+// point, so one 16-byte (FP32) shared load returns all three.  Lanes own
+// (y, x) pairs of the P x P face of a point's support and walk its P z-planes
+// with one shared address each; w2[y] w1[x] is formed once per pair.
+template <int T, typename R>
 __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
 {
     using R4 = typename Vec4<R>::T;
@@ -253,34 +254,40 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
     extern __shared__ __align__(32) unsigned char smem[];
     const int P = a.P, nd = a.deg + 1, RR = T + P - 1;
     const int RR2 = RR * RR, RR3 = RR2 * RR;
-    G *vs = (G *)smem;                      // [3][RR][RR][RR], the grid's own type
-    R *coef = (R *)(smem + ((sizeof(G) * 3 * RR3 + 15) & ~(size_t)15));  // [P][nd]
-    R *wsm = coef + P * nd;                 // per warp [3][kMaxP]
+    R4 *vs = (R4 *)smem;                         // [RR][RR][RR] points, (x, y, z, -)
+    R *coef = (R *)(vs + RR3);                   // [P][nd]
+    R *wsm = coef + P * nd;                      // per warp [3][kMaxP]
+    int *tab = (int *)(wsm + (kG2PThreads / 32) * 3 * kMaxP);  // [kMaxRounds][32]
     const int nt = a.nt, M = a.M;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     for (int i = threadIdx.x; i < P * nd; i += blockDim.x)
         coef[i] = ((const R *)a.wcoef)[i];
+    // (y, x) pair of lane l in round j: q = l + 32 j, packed y << 8 | x, -1 past P^2
+    for (int i = threadIdx.x; i < kMaxRounds * 32; i += blockDim.x)
+        tab[i] = i < P * P ? ((i / P) << 8) | (i % P) : -1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    // stage the grid block row by row (one warp per row, lanes along x) with
-    // asynchronous copies, all in flight at once; M >= P keeps one wrap enough
-    const G *grid = (const G *)a.grid;
+    // stage the grid block with asynchronous copies, all in flight at once:
+    // warps over (component, z) planes, lanes along x; M >= P keeps one wrap
+    // enough
+    const R *grid = (const R *)a.grid;
     const int64_t M3 = (int64_t)M * M * M;
-    int gx = tx * T + lane;  // lanes along x; RR = T + P - 1 <= 23 < 32
+    int gx = tx * T + lane;  // RR = T + P - 1 <= 23 < 32
     gx -= gx >= M ? M : 0;
     for (int cz = warp; cz < 3 * RR; cz += nwarps) {
-        const int c = cz / RR, z = cz - c * RR;  // one division per (c, z) plane
+        const int c = cz / RR, z = cz - c * RR;
         int gz = tz * T + z;
         gz -= gz >= M ? M : 0;
-        const G *plane = grid + c * M3 + (int64_t)gz * M * M;
-        G *dst_plane = vs + cz * RR2;
+        const R *plane = grid + c * M3 + (int64_t)gz * M * M;
+        R *dst_plane = (R *)(vs + z * RR2) + c;
         if (lane < RR) {
             for (int y = 0; y < RR; ++y) {
                 int gy = ty * T + y;
                 gy -= gy >= M ? M : 0;
-                const unsigned dst = (unsigned)__cvta_generic_to_shared(dst_plane + y * RR + lane);
-                const G *src = plane + (int64_t)gy * M + gx;
-                if constexpr (sizeof(G) == 4)
+                const unsigned dst =
+                    (unsigned)__cvta_generic_to_shared(dst_plane + 4 * (y * RR + lane));
+                const R *src = plane + (int64_t)gy * M + gx;
+                if constexpr (sizeof(R) == 4)
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src));
                 else
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src));
@@ -289,16 +296,8 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
     }
     asm volatile("cp.async.commit_group;\n" ::);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    // this lane's (y, x) pairs of the P x P face, fixed for all points
-    int ry[kRowsPerLane], rx[kRowsPerLane];
-#pragma unroll
-    for (int j = 0; j < kRowsPerLane; ++j) {
-        const int q = lane + 32 * j;
-        ry[j] = q < P * P ? q / P : -1;
-        rx[j] = q < P * P ? q - (q / P) * P : 0;
-    }
-    const int nj = (P * P + 31) / 32;  // pairs per lane (the last round partly empty)
     __syncthreads();
+    const int nr = (P * P + 31) / 32;  // rounds of 32 (y, x) pairs
     R *w = wsm + warp * 3 * kMaxP;
     const R4 *tdat = (const R4 *)a.tdat;
     R *uf = (R *)a.uf;
@@ -313,27 +312,20 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
             w[d * kMaxP + l] = horner(coef + l * nd, a.deg, (R)2 * dl - (R)1);
         }
         __syncwarp();
-        R wyx[kRowsPerLane];
-        int off[kRowsPerLane];
-#pragma unroll
-        for (int j = 0; j < kRowsPerLane; ++j) {
-            const bool ok = ry[j] >= 0;
-            wyx[j] = ok ? w[kMaxP + ry[j]] * w[rx[j]] : (R)0;
-            off[j] = ok ? (oy + ry[j]) * RR + ox + rx[j] : 0;
-        }
         R u0 = 0, u1 = 0, u2 = 0;
-        const G *vz = vs + oz * RR2;
-        for (int k = 0; k < P; ++k, vz += RR2) {
-            const R wk = w[2 * kMaxP + k];
-#pragma unroll
-            for (int j = 0; j < kRowsPerLane; ++j) {
-                if (j < nj) {
-                    const R ww = wk * wyx[j];
-                    const G *v = vz + off[j];
-                    u0 = fma(ww, (R)v[0], u0);
-                    u1 = fma(ww, (R)v[RR3], u1);
-                    u2 = fma(ww, (R)v[2 * RR3], u2);
-                }
+        for (int j = 0; j < nr; ++j) {
+            const int e = tab[j * 32 + lane];
+            const bool ok = e >= 0;
+            const int yy = ok ? e >> 8 : 0, xx = ok ? e & 255 : 0;
+            const R wyx = ok ? w[kMaxP + yy] * w[xx] : (R)0;
+            const R4 *v = vs + ((oz * RR + oy + yy) * RR + ox + xx);
+#pragma unroll 4
+            for (int k = 0; k < P; ++k) {
+                const R4 q = v[k * RR2];
+                const R ww = wyx * w[2 * kMaxP + k];
+                u0 = fma(ww, q.x, u0);
+                u1 = fma(ww, q.y, u1);
+                u2 = fma(ww, q.z, u2);
             }
         }
 #pragma unroll
@@ -387,17 +379,18 @@ cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int T, typename R, typename G>
+template <int T, typename R>
 cudaError_t run_g2p(const GridArgs &a, cudaStream_t s)
 {
-    int RR = T + a.P - 1;
-    size_t sm = ((sizeof(G) * (size_t)3 * RR * RR * RR + 15) & ~(size_t)15) +
-                sizeof(R) * ((size_t)a.P * (a.deg + 1) + (size_t)(kG2PThreads / 32) * 3 * kMaxP);
-    cudaError_t e = cudaFuncSetAttribute(k_g2p<T, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    using R4 = typename Vec4<R>::T;
+    const int RR = T + a.P - 1;
+    const size_t sm = sizeof(R4) * (size_t)RR * RR * RR +
+                      sizeof(R) * ((size_t)a.P * (a.deg + 1) + (size_t)(kG2PThreads / 32) * 3 * kMaxP) +
+                      sizeof(int) * kMaxRounds * 32;
+    cudaError_t e = cudaFuncSetAttribute(k_g2p<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess)
         return e;
-    k_g2p<T, R, G><<<a.nt * a.nt * a.nt, kG2PThreads, sm, s>>>(a);
+    k_g2p<T, R><<<a.nt * a.nt * a.nt, kG2PThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -411,14 +404,6 @@ cudaError_t dispatch_p2g(ewald_plan_s *p, const GridArgs &a, cudaStream_t s)
     return run_p2g<T, float, float>(a, s);
 }
 
-template <int T>
-cudaError_t dispatch_g2p(ewald_plan_s *p, const GridArgs &a, bool grid64, cudaStream_t s)
-{
-    if (p->near64)
-        return grid64 ? run_g2p<T, double, double>(a, s) : run_g2p<T, double, float>(a, s);
-    return grid64 ? run_g2p<T, float, double>(a, s) : run_g2p<T, float, float>(a, s);
-}
-
 }  // namespace
 
 cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s)
@@ -427,18 +412,15 @@ cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s)
     return p->g.T == 8 ? dispatch_p2g<8>(p, a, s) : dispatch_p2g<4>(p, a, s);
 }
 
-cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, bool grid_f64, cudaStream_t s)
-{
-    return launch_g2p_scaled(p, grid, grid_f64, 1.0, s);
-}
-
-cudaError_t launch_g2p_scaled(ewald_plan_s *p, const void *grid, bool grid_f64, double scale,
-                              cudaStream_t s)
+// G2P from a grid in the kernels' precision (FP64 when near64, else FP32).
+cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s)
 {
     GridArgs a = grid_args(p);
     a.grid = const_cast<void *>(grid);
     a.scale = scale;
-    return p->g.T == 8 ? dispatch_g2p<8>(p, a, grid_f64, s) : dispatch_g2p<4>(p, a, grid_f64, s);
+    if (p->near64)
+        return p->g.T == 8 ? run_g2p<8, double>(a, s) : run_g2p<4, double>(a, s);
+    return p->g.T == 8 ? run_g2p<8, float>(a, s) : run_g2p<4, float>(a, s);
 }
 
 }  // namespace ewg

@@ -280,15 +280,16 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
 
     // grid tile T: the G2P block of (T + P - 1)^3 x 3 values must fit in
     // shared memory (<= 222 KB of the 227 KB a block may use)
-    // (G2P stages it in the grid's type: FP64 when the FFT is FP64)
-    int esz = p.fft_f64 ? 8 : 4;
+    // (G2P stages it as 4-vectors of the kernels' precision: 16 or 32 bytes
+    // per grid point)
+    const double esz = p.near_f64 ? 32.0 : 16.0;
     int T = o.tile > 0 ? o.tile : 8;
     if (T != 4 && T != 8)
         return EWALD_EUNSUPPORTED;
-    const double smem_cap = 222.0 * 1024;
-    if (3.0 * pow(T + P - 1, 3) * esz > smem_cap)
+    const double smem_cap = 220.0 * 1024;
+    if (pow(T + P - 1, 3) * esz > smem_cap)
         T = 4;
-    if (3.0 * pow(T + P - 1, 3) * esz > smem_cap)
+    if (pow(T + P - 1, 3) * esz > smem_cap)
         return EWALD_EUNSUPPORTED;
     if (M % T)
         T = (M % 4 == 0) ? 4 : 0;

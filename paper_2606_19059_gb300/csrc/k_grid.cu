@@ -243,7 +243,9 @@ constexpr int kMaxRounds = (kMaxP * kMaxP + 31) / 32;
 // point, so one 16-byte (FP32) shared load returns all three.  Lanes own
 // (y, x) pairs of the P x P face of a point's support and walk its P z-planes
 // with one shared address each; w2[y] w1[x] is formed once per pair.
-template <int T, typename R>
+// PC > 0 fixes P at compile time (every offset into the staged block becomes
+// an immediate and the loops unroll); PC = 0 reads P at run time.
+template <int T, typename R, int PC>
 __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
 {
     using R4 = typename Vec4<R>::T;
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
     if (s0 == s1)
         return;
     extern __shared__ __align__(32) unsigned char smem[];
-    const int P = a.P, nd = a.deg + 1, RR = T + P - 1;
+    const int P = PC > 0 ? PC : a.P, nd = a.deg + 1, RR = T + P - 1;
     const int RR2 = RR * RR, RR3 = RR2 * RR;
     R4 *vs = (R4 *)smem;                         // [RR][RR][RR] points, (x, y, z, -)
     R *coef = (R *)(vs + RR3);                   // [P][nd]
@@ -313,19 +315,45 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
         }
         __syncwarp();
         R u0 = 0, u1 = 0, u2 = 0;
-        for (int j = 0; j < nr; ++j) {
-            const int e = tab[j * 32 + lane];
-            const bool ok = e >= 0;
-            const int yy = ok ? e >> 8 : 0, xx = ok ? e & 255 : 0;
-            const R wyx = ok ? w[kMaxP + yy] * w[xx] : (R)0;
-            const R4 *v = vs + ((oz * RR + oy + yy) * RR + ox + xx);
+        if constexpr (PC > 0) {
+            // z weights in registers, rows unrolled, immediate plane offsets
+            R wz[PC];
+#pragma unroll
+            for (int k = 0; k < PC; ++k)
+                wz[k] = w[2 * kMaxP + k];
+            const R4 *vb = vs + (oz * RR + oy) * RR + ox;
+#pragma unroll
+            for (int j = 0; j < (PC * PC + 31) / 32; ++j) {
+                const int q = lane + 32 * j;
+                if (q < PC * PC) {
+                    const int yy = q / PC, xx = q - yy * PC;
+                    const R wyx = w[kMaxP + yy] * w[xx];
+                    const R4 *v = vb + yy * RR + xx;
+#pragma unroll
+                    for (int k = 0; k < PC; ++k) {
+                        const R4 qv = v[k * RR2];
+                        const R ww = wyx * wz[k];
+                        u0 = fma(ww, qv.x, u0);
+                        u1 = fma(ww, qv.y, u1);
+                        u2 = fma(ww, qv.z, u2);
+                    }
+                }
+            }
+        } else {
+            for (int j = 0; j < nr; ++j) {
+                const int e = tab[j * 32 + lane];
+                const bool ok = e >= 0;
+                const int yy = ok ? e >> 8 : 0, xx = ok ? e & 255 : 0;
+                const R wyx = ok ? w[kMaxP + yy] * w[xx] : (R)0;
+                const R4 *v = vs + ((oz * RR + oy + yy) * RR + ox + xx);
 #pragma unroll 4
-            for (int k = 0; k < P; ++k) {
-                const R4 q = v[k * RR2];
-                const R ww = wyx * w[2 * kMaxP + k];
-                u0 = fma(ww, q.x, u0);
-                u1 = fma(ww, q.y, u1);
-                u2 = fma(ww, q.z, u2);
+                for (int k = 0; k < P; ++k) {
+                    const R4 q = v[k * RR2];
+                    const R ww = wyx * w[2 * kMaxP + k];
+                    u0 = fma(ww, q.x, u0);
+                    u1 = fma(ww, q.y, u1);
+                    u2 = fma(ww, q.z, u2);
+                }
             }
         }
 #pragma unroll
@@ -379,7 +407,7 @@ cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int T, typename R>
+template <int T, typename R, int PC>
 cudaError_t run_g2p(const GridArgs &a, cudaStream_t s)
 {
     using R4 = typename Vec4<R>::T;
@@ -387,11 +415,25 @@ cudaError_t run_g2p(const GridArgs &a, cudaStream_t s)
     const size_t sm = sizeof(R4) * (size_t)RR * RR * RR +
                       sizeof(R) * ((size_t)a.P * (a.deg + 1) + (size_t)(kG2PThreads / 32) * 3 * kMaxP) +
                       sizeof(int) * kMaxRounds * 32;
-    cudaError_t e = cudaFuncSetAttribute(k_g2p<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_g2p<T, R, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess)
         return e;
-    k_g2p<T, R><<<a.nt * a.nt * a.nt, kG2PThreads, sm, s>>>(a);
+    k_g2p<T, R, PC><<<a.nt * a.nt * a.nt, kG2PThreads, sm, s>>>(a);
     return cudaGetLastError();
+}
+
+// FP32, T = 8: a compile-time-P kernel for every supported P
+template <int PC>
+cudaError_t run_g2p_f32_fixed(const GridArgs &a, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return run_g2p<8, float, 0>(a, s);
+    } else {
+        if (a.P == PC)
+            return run_g2p<8, float, PC>(a, s);
+        return run_g2p_f32_fixed<PC + 1>(a, s);
+    }
 }
 
 template <int T>
@@ -419,8 +461,8 @@ cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStre
     a.grid = const_cast<void *>(grid);
     a.scale = scale;
     if (p->near64)
-        return p->g.T == 8 ? run_g2p<8, double>(a, s) : run_g2p<4, double>(a, s);
-    return p->g.T == 8 ? run_g2p<8, float>(a, s) : run_g2p<4, float>(a, s);
+        return p->g.T == 8 ? run_g2p<8, double, 0>(a, s) : run_g2p<4, double, 0>(a, s);
+    return p->g.T == 8 ? run_g2p_f32_fixed<2>(a, s) : run_g2p<4, float, 0>(a, s);
 }
 
 }  // namespace ewg

@@ -31,6 +31,8 @@
 // and a rational erfcx times e^{-x^2} above (see fit_erf.py).
 #include <math.h>
 
+#include <type_traits>
+
 #include "erf_rational.h"
 #include "internal.h"
 
@@ -69,19 +71,41 @@ struct F32Const {
     float rc2, rc2_loose, xi, nxi2log2e, c2, selfc;
 };
 
+// Kahan-compensated FP32 accumulation: s + c carries the sum to about one
+// rounding of the largest partial, whatever the number of terms.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
 // One FP32 in-range candidate (cell units): d = (hi diff) + (lo diff).
+// KAHAN selects compensated accumulation (tol < 1e-6): a blob point sums
+// thousands of terms, and plain FP32 sums then lose ~eps sqrt(n/2).
+template <bool KAHAN, typename Acc>
 __device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const float4 &tl,
                                          const float4 &sl, const float4 &f, const F32Const &k,
-                                         float &ax, float &ay, float &az)
+                                         Acc &ax, Acc &ay, Acc &az)
 {
     float dx = hx + (tl.x - sl.x), dy = hy + (tl.y - sl.y), dz = hz + (tl.z - sl.z);
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 > k.rc2)
         return;
     if (r2 == 0.0f) {  // self or coincident point: the pair's far part comes out
-        ax = fmaf(-k.selfc, f.x, ax);
-        ay = fmaf(-k.selfc, f.y, ay);
-        az = fmaf(-k.selfc, f.z, az);
+        if constexpr (KAHAN) {
+            ax.add(-k.selfc * f.x);
+            ay.add(-k.selfc * f.y);
+            az.add(-k.selfc * f.z);
+        } else {
+            ax = fmaf(-k.selfc, f.x, ax);
+            ay = fmaf(-k.selfc, f.y, ay);
+            az = fmaf(-k.selfc, f.z, az);
+        }
         return;
     }
     float rinv = rsqrtf(r2);
@@ -113,9 +137,15 @@ __device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const flo
     float amb = A - B, apb = A + B;
     float rf = fmaf(dx, f.x, fmaf(dy, f.y, dz * f.z));
     float co = apb * rf * (rinv * rinv);
-    ax = fmaf(amb, f.x, fmaf(co, dx, ax));
-    ay = fmaf(amb, f.y, fmaf(co, dy, ay));
-    az = fmaf(amb, f.z, fmaf(co, dz, az));
+    if constexpr (KAHAN) {
+        ax.add(fmaf(amb, f.x, co * dx));
+        ay.add(fmaf(amb, f.y, co * dy));
+        az.add(fmaf(amb, f.z, co * dz));
+    } else {
+        ax = fmaf(amb, f.x, fmaf(co, dx, ax));
+        ay = fmaf(amb, f.y, fmaf(co, dy, ay));
+        az = fmaf(amb, f.z, fmaf(co, dz, az));
+    }
 }
 
 // One FP64 in-range candidate (length units) with the paper's erf(x)/x.
@@ -288,8 +318,11 @@ __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long lo
 using WsF32 = WarpSmem<float4, 3>;
 using WsF64 = WarpSmem<dvec4, 2>;
 
+// KAHAN: compensated per-tile sums and FP64 accumulation across tiles.
+template <bool KAHAN>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)
 {
+    using Tot = typename std::conditional<KAHAN, double, float>::type;
     __shared__ WsF32 wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WsF32 &ws = wsm[warp];
@@ -313,7 +346,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
     // tile samples the whole neighbourhood, so the lanes' in-range counts per
     // tile are even and phase 2 wastes few iterations
     const int ntile = (total + kTile - 1) / kTile;
-    float ux = 0.f, uy = 0.f, uz = 0.f;
+    Tot ux = 0, uy = 0, uz = 0;
     for (int tile = 0; tile < ntile; ++tile) {
         const int n = (total - tile + ntile - 1) / ntile;  // elements q < total with q % ntile == tile
 #pragma unroll
@@ -344,24 +377,32 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
                     return fmaf(hx, hx, fmaf(hy, hy, hz * hz));
                 },
                 m0, m1);
-            float px = 0.f, py = 0.f, pz = 0.f;  // per-tile partial sums
+            // per-tile partial sums
+            typename std::conditional<KAHAN, KSum, float>::type px{}, py{}, pz{};
             while (m0 | m1) {
                 const int k = next_bit(m0, m1);
                 const float4 s = sh[k];
-                pair_f32(th.x - s.x, th.y - s.y, th.z - s.z, tl, sl[k], sf[k], kc, px, py, pz);
+                pair_f32<KAHAN>(th.x - s.x, th.y - s.y, th.z - s.z, tl, sl[k], sf[k], kc, px, py,
+                                pz);
             }
-            ux += px;
-            uy += py;
-            uz += pz;
+            if constexpr (KAHAN) {
+                ux += (double)px.s + (double)px.c * -1.0;
+                uy += (double)py.s + (double)py.c * -1.0;
+                uz += (double)pz.s + (double)pz.c * -1.0;
+            } else {
+                ux += px;
+                uy += py;
+                uz += pz;
+            }
         }
         __syncwarp();
     }
     if (active) {
         const int i = a.permn[t];
         float *un = (float *)a.un;
-        un[3 * i] = ux * inv_cell;
-        un[3 * i + 1] = uy * inv_cell;
-        un[3 * i + 2] = uz * inv_cell;
+        un[3 * i] = (float)(ux * inv_cell);
+        un[3 * i + 1] = (float)(uy * inv_cell);
+        un[3 * i + 2] = (float)(uz * inv_cell);
     }
 }
 
@@ -502,7 +543,10 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         kc.nxi2log2e = (float)(-xic * xic * 1.4426950408889634);
         kc.c2 = (float)(2.0 * xic / sqrt(3.14159265358979323846));
         kc.selfc = (float)(4.0 * xic / sqrt(3.14159265358979323846));
-        k_p2p_f32<<<grid, kWarps * 32, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
+        if (p->prm.tol < 1e-6)  // compensated sums below tol 1e-6
+            k_p2p_f32<true><<<grid, kWarps * 32, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
+        else
+            k_p2p_f32<false><<<grid, kWarps * 32, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
     }
     return cudaGetLastError();
 }

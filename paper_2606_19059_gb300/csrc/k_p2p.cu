@@ -68,8 +68,28 @@ __device__ __forceinline__ float fast_ex2(float x)
 }
 
 struct F32Const {
-    float rc2, rc2_loose, xi, nxi2log2e, c2, selfc;
+    float rc2, rc2_loose, xi, nxi2log2e, nxi2log2e_lo, c2, selfc;
 };
+
+__constant__ float c_exp2f32[EXP2_F32_N];
+
+// e^{-xi^2 r^2} = 2^y, y = r2 * (chi + clo) kept as y_hi + y_lo (the product's
+// rounding recovered by an FMA), reduced to 2^f, |f| <= 1/2, by a minimax
+// polynomial (fit_erf.py) and scaled by 2^n through the exponent bits.  About
+// one ulp, where the hardware approximation and the FP32 rounding of y would
+// each cost a few.  Valid for -125 <= y <= 0 (here y >= -50).
+__device__ __forceinline__ float exp2_accurate(float r2, float chi, float clo)
+{
+    const float yh = r2 * chi;
+    const float yl = fmaf(r2, chi, -yh) + r2 * clo;
+    const float n = rintf(yh);
+    const float f = (yh - n) + yl;
+    float p = c_exp2f32[EXP2_F32_N - 1];
+#pragma unroll
+    for (int q = EXP2_F32_N - 2; q >= 0; --q)
+        p = fmaf(p, f, c_exp2f32[q]);
+    return __int_as_float(__float_as_int(p) + ((int)n << 23));
+}
 
 // Kahan-compensated FP32 accumulation: s + c carries the sum to about one
 // rounding of the largest partial, whatever the number of terms.
@@ -85,8 +105,9 @@ struct KSum {
 };
 
 // One FP32 in-range candidate (cell units): d = (hi diff) + (lo diff).
-// KAHAN selects compensated accumulation (tol < 1e-6): a blob point sums
-// thousands of terms, and plain FP32 sums then lose ~eps sqrt(n/2).
+// KAHAN selects the tight-tolerance form (tol < 1e-6): compensated
+// accumulation (a blob point sums thousands of terms, and plain FP32 sums lose
+// ~eps sqrt(n/2)) and the accurate exponential above.
 template <bool KAHAN, typename Acc>
 __device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const float4 &tl,
                                          const float4 &sl, const float4 &f, const F32Const &k,
@@ -114,7 +135,11 @@ __device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const flo
         rinv = fmaf(0.5f * rinv, e, rinv);
     }
     float x = k.xi * (r2 * rinv);
-    float E = fast_ex2(r2 * k.nxi2log2e);  // e^{-xi^2 r^2}
+    float E;  // e^{-xi^2 r^2}
+    if constexpr (KAHAN)
+        E = exp2_accurate(r2, k.nxi2log2e, k.nxi2log2e_lo);
+    else
+        E = fast_ex2(r2 * k.nxi2log2e);
     float A;                               // erfc(xi r) / r
     if (x < (float)ERFX_SMALL_X32) {
         float t = x * x;
@@ -500,6 +525,12 @@ cudaError_t load_p2p_constants()
     cudaError_t e = cudaMemcpyToSymbol(c_erfcx32, c32, sizeof(c32));
     if (e == cudaSuccess)
         e = cudaMemcpyToSymbol(c_erfxs32, s32, sizeof(s32));
+    if (e == cudaSuccess) {
+        float x2[EXP2_F32_N];
+        for (int k = 0; k < EXP2_F32_N; ++k)
+            x2[k] = (float)exp2_f32_c[k];
+        e = cudaMemcpyToSymbol(c_exp2f32, x2, sizeof(x2));
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyToSymbol(c_erfp64, erf_rat_f64_p, sizeof(erf_rat_f64_p));
     if (e == cudaSuccess)
@@ -540,7 +571,9 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         kc.rc2 = (float)(rcc * rcc);
         kc.rc2_loose = (float)(rcc * rcc * (1.0 + 2e-3));
         kc.xi = (float)xic;
-        kc.nxi2log2e = (float)(-xic * xic * 1.4426950408889634);
+        const double c = -xic * xic * 1.4426950408889634;  // -xi^2 log2(e), cell units
+        kc.nxi2log2e = (float)c;
+        kc.nxi2log2e_lo = (float)(c - (double)kc.nxi2log2e);
         kc.c2 = (float)(2.0 * xic / sqrt(3.14159265358979323846));
         kc.selfc = (float)(4.0 * xic / sqrt(3.14159265358979323846));
         if (p->prm.tol < 1e-6)  // compensated sums below tol 1e-6

@@ -46,6 +46,7 @@ DEG32 = 9
 DEG64 = 13
 XS32 = 1.0          # FP32 small-x branch: erf(x)/x as a polynomial in x^2 on [0, XS32]
 DEGS32 = 8
+DEGX2 = 6           # FP32 2^f on [-1/2, 1/2] (tight-tolerance exponential)
 
 
 def erf_over_x(x):
@@ -138,6 +139,32 @@ def max_error_small(a, n_check: int = 20001) -> float:
     return float(m)
 
 
+def fit_exp2(deg: int, n_pts: int = 2001, iters: int = 60):
+    """c[0..deg] with 2^f ~= sum_k c[k] f^k on [-1/2, 1/2], minimax relative
+    error (Lawson reweighting); used by the tight-tolerance FP32 kernel to
+    evaluate e^{-x^2} = 2^(n + f) without the hardware approximation."""
+    f = np.linspace(-0.5, 0.5, n_pts)
+    g = np.array([float(mp.power(2, mp.mpf(v))) for v in f])
+    V = np.vstack([f ** k for k in range(deg + 1)]).T
+    w = np.ones_like(f)
+    coef = None
+    for _ in range(iters):
+        W = np.sqrt(w) / g
+        coef, *_ = np.linalg.lstsq(V * W[:, None], g * W, rcond=None)
+        e = np.abs(V @ coef - g) / g
+        w = w * e
+        w /= w.mean()
+    return [float(c) for c in coef]
+
+
+def max_rel_error_exp2(c, n_check: int = 20001) -> float:
+    m = mp.mpf(0)
+    for i in range(n_check):
+        f = mp.mpf(-0.5) + mp.mpf(i) / (n_check - 1)
+        m = max(m, abs(_horner(c, f) / mp.power(2, f) - 1))
+    return float(m)
+
+
 def max_error_f64(p, q, n_check: int = 20001) -> float:
     """max |P(z)/Q(z) - erf(x)/x| on a uniform grid of x in [0, X64]."""
     m = mp.mpf(0)
@@ -186,6 +213,9 @@ def main():
     s32 = fit_erfx_small(DEGS32)
     es32 = max_error_small(s32)
     print("f32 erf(x)/x small-x poly", DEGS32, "max abs error", es32)
+    x2 = fit_exp2(DEGX2)
+    ex2 = max_rel_error_exp2(x2)
+    print("f32 2^f poly", DEGX2, "max rel error", ex2)
     print("f64 erf(x)/x  P/Q", DEG64, "max abs error", e64)
     print("f32 erfcx  t p(t)", DEG32, "max rel error", e32)
     L = [
@@ -221,6 +251,11 @@ def main():
           f"#define ERFX_SMALL_MAXERR {es32:.3e}  /* absolute, on erf(x)/x */",
           f"static const double erfx_small_c[{DEGS32 + 1}] = {{"]
     L += [f"    {v!r}," for v in s32]
+    L += ["};", "",
+          f"#define EXP2_F32_N {DEGX2 + 1}",
+          f"#define EXP2_F32_MAXERR {ex2:.3e}  /* relative, on 2^f, |f| <= 1/2 */",
+          f"static const double exp2_f32_c[{DEGX2 + 1}] = {{"]
+    L += [f"    {v!r}," for v in x2]
     L += ["};", ""]
     with open(out, "w") as fh:
         fh.write("\n".join(L))

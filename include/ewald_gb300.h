@@ -198,6 +198,30 @@ ewald_status ewald_window_eval(int32_t P, int32_t nu, int64_t n, const double *t
                                double *max_err);
 ewald_status ewald_window_hat(int32_t P, double h, int64_t n, const double *k, double *what);
 
+/* The near field of ewald_near_field() without any device allocation.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- code running inside a pre-sized memory pool or a custom
+ * allocator that owns the device, plugins that must leave the host
+ * application's allocator alone, and paths that must not synchronise the
+ * device, which cudaMalloc/cudaFree may do.  Its workspace is one fixed
+ * array in device memory (about 7 MB) that every GPU loading this library
+ * holds until the process exits.
+ *   N      points (1 .. 32768; larger N returns EWALD_EUNSUPPORTED)
+ *   prm    host struct read for L, xi, rc, near_f64 (1: FP64 kernels, 0: FP32),
+ *          tol (FP32 below 1e-6 uses the compensated form) and n_c (<= 0:
+ *          floor(L / rc)); n_c must be <= 16 and the cutoff may reach at most
+ *          two cells (else EWALD_EUNSUPPORTED).  ewald_get_params() of a plan
+ *          gives a consistent set.
+ *   x, f   device, N x 3 FP64 (read); u: device, N x 3 FP64 (written): u^N as
+ *          ewald_near_field() defines it.
+ * The first call on a device looks up the array's address on that device;
+ * make it before any stream capture.  All calls share the array and it keeps
+ * the last call's contents; each call clears what must start at zero on
+ * `stream`, and calls that overlap on the GPU (other streams or threads)
+ * race.  NaN inputs give unspecified values; they are not reported. */
+ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *prm, const double *x,
+                                      const double *f, double *u, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,7 @@ _SIGS = [
     ("ewald_window_eval", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
                                          ctypes.POINTER(ctypes.c_double)]),
     ("ewald_window_hat", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _P, _P]),
+    ("ewald_near_field_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ewald_params), _P, _P, _P, _P]),
 ]
 EXPORTED = [name for name, _, _ in _SIGS]
 
@@ -232,6 +233,13 @@ def ewald_window_hat(P: int, h: float, k):
     _check(load().ewald_window_hat(int(P), float(h), k.size, k.ctypes.data, w.ctypes.data),
            "ewald_window_hat")
     return w
+
+
+def ewald_near_field_noalloc(N: int, params: ewald_params, x_ptr, f_ptr, u_ptr, stream=0):
+    """Near field with no device allocation (fixed in-library workspace, N <= 32768);
+    for callers that cannot allocate device memory themselves."""
+    _check(load().ewald_near_field_noalloc(int(N), ctypes.byref(params), x_ptr, f_ptr, u_ptr, stream),
+           "ewald_near_field_noalloc")
 
 
 class Plan:

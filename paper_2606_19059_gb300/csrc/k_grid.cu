@@ -61,32 +61,48 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-// P2G: R = accumulation precision, G = grid element type.
-template <int T, typename R, typename G>
-__global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
+// P2G: R = accumulation precision, G = grid element type.  PC > 0 fixes P at
+// compile time: (B) then evaluates all P bins of one (point, axis) in one
+// thread -- every bin shares z = 2 delta - 1, so the coefficient loads are
+// warp-uniform broadcasts and the P Horner chains run side by side.
+template <int T, typename R, typename G, int PC>
+__global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(GridArgs a)
 {
     using R4 = typename Vec4<R>::T;
     constexpr int NT = kP2GThreads;
     constexpr int ROWS = T * T / 2;  // row pairs (y, z), (y, z + T/2)
     constexpr int SL = NT / ROWS;
     constexpr int B = NT;  // points per round
+    constexpr int H = T / 2;
+    // a warp holds one slice when ROWS is a multiple of 32: per-point tests
+    // are then warp-uniform, and the tile halves [0, H), [H, T) in x and z
+    // that the point's support misses are skipped as a whole
+    constexpr bool kSkip = ROWS % 32 == 0;
+    constexpr int PS = (PC + 3) & ~3;  // padded bins per coefficient row (PC > 0)
     extern __shared__ __align__(32) unsigned char smem[];
     R *wx = (R *)smem;              // [B][T]
     R *wy = wx + B * T;             // [B][T]
     R *wz = wy + B * T;             // [B][T]
     R *sf = wz + B * T;             // [B][4] force, padded for vector loads
     R *sd = sf + B * 4;             // [B][3] fractional offsets delta
-    R *coef = sd + B * 3;           // [P][deg+1]
+    R *coef = sd + B * 3;           // PC = 0: [P][deg+1]; PC > 0: [deg+1][PS]
     __shared__ int soff[B];         // packed anchor offsets relative to the tile (biased)
     __shared__ int seg_start[kMaxSeg], seg_pref[kMaxSeg + 1];
     __shared__ int scount;
 
-    const int nt = a.nt, P = a.P, nd = a.deg + 1, KT = a.KT;
+    const int nt = a.nt, P = PC > 0 ? PC : a.P, nd = a.deg + 1, KT = a.KT;
     const int side = KT + 1, nseg = side * side * side;
     const int tile = blockIdx.x;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
-    for (int i = threadIdx.x; i < P * nd; i += NT)
-        coef[i] = ((const R *)a.wcoef)[i];
+    if constexpr (PC > 0) {
+        for (int i = threadIdx.x; i < nd * PS; i += NT) {
+            const int j = i / PS, l = i - j * PS;
+            coef[i] = l < PC ? ((const R *)a.wcoef)[l * nd + j] : (R)0;
+        }
+    } else {
+        for (int i = threadIdx.x; i < P * nd; i += NT)
+            coef[i] = ((const R *)a.wcoef)[i];
+    }
     // segment table: neighbour tile s = (dz, dy, dx) in [-KT, 0]^3
     if (threadIdx.x < 32) {
         int carry = 0;
@@ -173,41 +189,104 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
         }
         __syncthreads();
         const int n = scount;
-        // (B) window values padded to the tile: one thread per (point, axis, offset)
-        for (int w = threadIdx.x; w < n * 3 * T; w += NT) {
-            const int k = w / (3 * T), r = w - k * 3 * T, d = r / T, qq = r - d * T;
-            const int o = ((soff[k] >> (6 * d)) & 63) - 32;
-            const int l = qq - o;
-            R v = (R)0;
-            if (l >= 0 && l < P)
-                v = horner(coef + l * nd, a.deg, (R)2 * sd[k * 3 + d] - (R)1);
-            (d == 0 ? wx : (d == 1 ? wy : wz))[k * T + qq] = v;
+        // (B) window values padded to the tile
+        if constexpr (PC > 0) {
+            // one thread per (point, axis): all P bins at once
+            for (int w = threadIdx.x; w < n * 3; w += NT) {
+                const int k = w / 3, d = w - 3 * k;
+                const int o = ((soff[k] >> (6 * d)) & 63) - 32;
+                const R zz = (R)2 * sd[k * 3 + d] - (R)1;
+                R pv[PS];
+                const R *cd = coef + (nd - 1) * PS;
+#pragma unroll
+                for (int l = 0; l < PS; ++l)
+                    pv[l] = cd[l];
+                for (int jj = nd - 2; jj >= 0; --jj) {
+                    const R *cj = coef + jj * PS;
+#pragma unroll
+                    for (int l = 0; l < PS; ++l)
+                        pv[l] = fma(pv[l], zz, cj[l]);
+                }
+                R *rowp = (d == 0 ? wx : (d == 1 ? wy : wz)) + k * T;
+#pragma unroll
+                for (int x = 0; x < T; ++x)
+                    rowp[x] = (R)0;
+#pragma unroll
+                for (int l = 0; l < PC; ++l) {
+                    const int qq = o + l;
+                    if ((unsigned)qq < (unsigned)T)
+                        rowp[qq] = pv[l];
+                }
+            }
+        } else {
+            // one thread per (point, axis, offset)
+            for (int w = threadIdx.x; w < n * 3 * T; w += NT) {
+                const int k = w / (3 * T), r = w - k * 3 * T, d = r / T, qq = r - d * T;
+                const int o = ((soff[k] >> (6 * d)) & 63) - 32;
+                const int l = qq - o;
+                R v = (R)0;
+                if (l >= 0 && l < P)
+                    v = horner(coef + l * nd, a.deg, (R)2 * sd[k * 3 + d] - (R)1);
+                (d == 0 ? wx : (d == 1 ? wy : wz))[k * T + qq] = v;
+            }
         }
         __syncthreads();
         // (C) accumulate two rows per thread; x weights and force are shared
         for (int k = slice; k < n; k += SL) {
+            bool hx0 = true, hx1 = true, hz0 = true, hz1 = true;
+            if constexpr (kSkip) {
+                const int so = soff[k];
+                const int okx = (so & 63) - 32, okz = ((so >> 12) & 63) - 32;
+                hx0 = okx < H;
+                hx1 = okx + P > H;
+                hz0 = okz < H;
+                hz1 = okz + P > H;
+            }
             const R wyk = wy[k * T + y];
-            const R wz0 = wyk * wz[k * T + z], wz1 = wyk * wz[k * T + z + T / 2];
-            if (wz0 != (R)0 || wz1 != (R)0) {
-                const R4 f = ((const R4 *)sf)[k];
-                R wv[T];
+            const R wz0 = wyk * wz[k * T + z], wz1 = wyk * wz[k * T + z + H];
+            const R4 f = ((const R4 *)sf)[k];
+            R wv[T];
 #pragma unroll
-                for (int x4 = 0; x4 < T / 4; ++x4) {
-                    const R4 q = ((const R4 *)(wx + k * T))[x4];
-                    wv[4 * x4] = q.x;
-                    wv[4 * x4 + 1] = q.y;
-                    wv[4 * x4 + 2] = q.z;
-                    wv[4 * x4 + 3] = q.w;
-                }
+            for (int x4 = 0; x4 < T / 4; ++x4) {
+                const R4 qv = ((const R4 *)(wx + k * T))[x4];
+                wv[4 * x4] = qv.x;
+                wv[4 * x4 + 1] = qv.y;
+                wv[4 * x4 + 2] = qv.z;
+                wv[4 * x4 + 3] = qv.w;
+            }
+            if (hz0) {
                 const R g0[3] = {wz0 * f.x, wz0 * f.y, wz0 * f.z};
+                if (hx0) {
+#pragma unroll
+                    for (int x = 0; x < H; ++x)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
+                }
+                if (hx1) {
+#pragma unroll
+                    for (int x = H; x < T; ++x)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
+                }
+            }
+            if (hz1) {
                 const R g1[3] = {wz1 * f.x, wz1 * f.y, wz1 * f.z};
+                if (hx0) {
 #pragma unroll
-                for (int x = 0; x < T; ++x)
+                    for (int x = 0; x < H; ++x)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
-                        acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
-                    }
+                        for (int c = 0; c < 3; ++c)
+                            acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
+                }
+                if (hx1) {
+#pragma unroll
+                    for (int x = H; x < T; ++x)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
+                }
             }
         }
         __syncthreads();
@@ -220,7 +299,7 @@ __global__ void __launch_bounds__(kP2GThreads) k_p2g(GridArgs a)
         for (int x = 0; x < T; ++x)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                red[((slice * 3 + c) * T + z + h * (T / 2)) * T * T + y * T + x] = acc[h][x][c];
+                red[((slice * 3 + c) * T + z + h * H) * T * T + y * T + x] = acc[h][x][c];
     __syncthreads();
     G *grid = (G *)a.grid;
     const int64_t M = a.M, M3 = M * M * M;
@@ -372,6 +451,173 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
     }
 }
 
+// Planar G2P staging (FP32, T = 8).  The block stages the grid block as
+// three planar arrays [c][z][y][x] with row stride S (a multiple of 4 floats,
+// so 16-byte asynchronous copies fill it).  A point's P x P (y, x) pairs are
+// dealt to lanes by bank: lane b takes the pairs with (S yy + xx) mod 32 = b,
+// one per round, so in every round the 32 lanes read 32 different banks
+// whatever the point's offset (a shift moves all banks alike).  The number of
+// rounds is the largest number of pairs on one bank; S is picked to keep it
+// near ceil(P^2 / 32).
+__host__ __device__ constexpr int g2p_rounds(int P, int S)
+{
+    int mx = 0;
+    for (int b = 0; b < 32; ++b) {
+        int cnt = 0;
+        for (int yy = 0; yy < P; ++yy)
+            if (((b - S * yy) & 31) < P)
+                ++cnt;
+        mx = cnt > mx ? cnt : mx;
+    }
+    return mx;
+}
+__host__ __device__ constexpr int g2p_stride(int P)
+{
+    const int s0 = (P + 7 + 3) & ~3;  // T + P - 1 rounded up to 4
+    int best = s0, br = g2p_rounds(P, s0);
+    for (int S = s0 + 4; S <= s0 + 8; S += 4) {
+        const int r = g2p_rounds(P, S);
+        if (r < br) {
+            best = S;
+            br = r;
+        }
+    }
+    return best;
+}
+
+template <int PC>
+struct G2PPlanar {
+    static constexpr int T = 8, RR = T + PC - 1, S = g2p_stride(PC), NR = g2p_rounds(PC, S);
+    static constexpr int NCH = (RR + 3) / 4;  // 16-byte chunks per staged row
+    static constexpr int PS = (PC + 3) & ~3;
+    static constexpr int NW = kG2PThreads / 32;
+    static constexpr size_t grid_bytes = sizeof(float) * 3 * RR * RR * S;
+    static size_t smem(int deg)
+    {
+        return grid_bytes + sizeof(int) * NR * 32 + sizeof(float) * (NW * 3 * PS + (deg + 1) * PS);
+    }
+};
+
+template <int PC>
+__global__ void __launch_bounds__(kG2PThreads) k_g2p_planar(GridArgs a)
+{
+    using G = G2PPlanar<PC>;
+    constexpr int T = G::T, RR = G::RR, S = G::S, NR = G::NR, NCH = G::NCH, PS = G::PS;
+    constexpr int PLANE = RR * S, VOL = RR * PLANE;
+    const int tile = blockIdx.x;
+    const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
+    if (s0 == s1)
+        return;
+    extern __shared__ __align__(32) unsigned char smem[];
+    float *vs = (float *)smem;                                  // [3][RR][RR][S]
+    int *tab = (int *)(smem + G::grid_bytes);                   // [NR][32]
+    float *wsm = (float *)(tab + NR * 32);                      // per warp [3][PS]
+    float *coef = wsm + G::NW * 3 * PS;                         // [deg+1][PS]
+    const int nt = a.nt, M = a.M, nd = a.deg + 1;
+    const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // stage: 16-byte copies, M a multiple of 8 keeps every chunk on one side of
+    // the periodic wrap and M >= P keeps one wrap enough
+    const float *grid = (const float *)a.grid;
+    const int64_t M3 = (int64_t)M * M * M;
+    for (int i = threadIdx.x; i < 3 * RR * RR * NCH; i += kG2PThreads) {
+        const int ch = i % NCH, row = i / NCH;
+        const int y = row % RR, z = (row / RR) % RR, c = row / (RR * RR);
+        int gx = tx * T + 4 * ch, gy = ty * T + y, gz = tz * T + z;
+        gx -= gx >= M ? M : 0;
+        gy -= gy >= M ? M : 0;
+        gz -= gz >= M ? M : 0;
+        const float *src = grid + c * M3 + ((int64_t)gz * M + gy) * M + gx;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(vs + (c * RR + z) * PLANE + y * S + 4 * ch);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+    // bank-dealt (y, x) pairs: lane b, round r -> the r-th row yy whose pair
+    // on bank b exists, packed yy << 8 | xx, -1 past the last
+    if (threadIdx.x < 32) {
+        int r = 0;
+        for (int yy = 0; yy < PC; ++yy) {
+            const int xx = (lane - S * yy) & 31;
+            if (xx < PC)
+                tab[r++ * 32 + lane] = (yy << 8) | xx;
+        }
+        for (; r < NR; ++r)
+            tab[r * 32 + lane] = -1;
+    }
+    for (int i = threadIdx.x; i < nd * PS; i += kG2PThreads) {
+        const int j = i / PS, l = i - j * PS;
+        coef[i] = l < PC ? ((const float *)a.wcoef)[l * nd + j] : 0.f;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    float *w = wsm + warp * 3 * PS;
+    const float4 *tdat = (const float4 *)a.tdat;
+    float *uf = (float *)a.uf;
+    for (int p = s0 + warp; p < s1; p += G::NW) {
+        const float4 td = tdat[p];
+        const int packed = (int)td.w;
+        const int ox = packed & 15, oy = (packed >> 4) & 15, oz = (packed >> 8) & 15;
+        __syncwarp();
+        // window weights: lane (d, l) and (d', l') = lane + 32, shared z per axis
+        {
+            const int q0 = lane, q1 = lane + 32;
+            const int d0 = q0 / PC, l0 = q0 - d0 * PC, d1 = q1 / PC, l1 = q1 - d1 * PC;
+            const bool ok0 = q0 < 3 * PC, ok1 = q1 < 3 * PC;
+            const float z0 = 2.f * (d0 == 0 ? td.x : (d0 == 1 ? td.y : td.z)) - 1.f;
+            const float z1 = 2.f * (d1 == 0 ? td.x : (d1 == 1 ? td.y : td.z)) - 1.f;
+            const int c0 = ok0 ? l0 : 0, c1 = ok1 ? l1 : 0;
+            float v0 = coef[(nd - 1) * PS + c0], v1 = coef[(nd - 1) * PS + c1];
+            for (int j = nd - 2; j >= 0; --j) {
+                v0 = fmaf(v0, z0, coef[j * PS + c0]);
+                v1 = fmaf(v1, z1, coef[j * PS + c1]);
+            }
+            if (ok0)
+                w[d0 * PS + l0] = v0;
+            if (ok1)
+                w[d1 * PS + l1] = v1;
+        }
+        __syncwarp();
+        float wz[PC];
+#pragma unroll
+        for (int k = 0; k < PC; ++k)
+            wz[k] = w[2 * PS + k];
+        const float *vb = vs + (oz * RR + oy) * S + ox;
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int e = tab[r * 32 + lane];
+            if (e >= 0) {
+                const int yy = e >> 8, xx = e & 255;
+                const float wyx = w[PS + yy] * w[xx];
+                const float *v = vb + yy * S + xx;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < PC; ++k) {
+                    a0 = fmaf(wz[k], v[k * PLANE], a0);
+                    a1 = fmaf(wz[k], v[VOL + k * PLANE], a1);
+                    a2 = fmaf(wz[k], v[2 * VOL + k * PLANE], a2);
+                }
+                u0 = fmaf(wyx, a0, u0);
+                u1 = fmaf(wyx, a1, u1);
+                u2 = fmaf(wyx, a2, u2);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            u0 += __shfl_xor_sync(0xffffffffu, u0, o);
+            u1 += __shfl_xor_sync(0xffffffffu, u1, o);
+            u2 += __shfl_xor_sync(0xffffffffu, u2, o);
+        }
+        if (lane == 0) {
+            const int i = a.permt[p];
+            const float sc = (float)a.scale;
+            uf[3 * i] = u0 * sc;
+            uf[3 * i + 1] = u1 * sc;
+            uf[3 * i + 2] = u2 * sc;
+        }
+    }
+}
+
 GridArgs grid_args(ewald_plan_s *p)
 {
     GridArgs a;
@@ -392,19 +638,33 @@ GridArgs grid_args(ewald_plan_s *p)
     return a;
 }
 
-template <int T, typename R, typename G>
+template <int T, typename R, typename G, int PC>
 cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
 {
     constexpr int B = kP2GThreads;
-    size_t stage = sizeof(R) * ((size_t)B * (3 * T + 7) + (size_t)a.P * (a.deg + 1));
+    const size_t ncoef = PC > 0 ? (size_t)(a.deg + 1) * ((PC + 3) & ~3) : (size_t)a.P * (a.deg + 1);
+    size_t stage = sizeof(R) * ((size_t)B * (3 * T + 7) + ncoef);
     size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * T;
     size_t sm = stage > red ? stage : red;
-    cudaError_t e = cudaFuncSetAttribute(k_p2g<T, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_p2g<T, R, G, PC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess)
         return e;
-    k_p2g<T, R, G><<<a.nt * a.nt * a.nt, kP2GThreads, sm, s>>>(a);
+    k_p2g<T, R, G, PC><<<a.nt * a.nt * a.nt, kP2GThreads, sm, s>>>(a);
     return cudaGetLastError();
+}
+
+// FP32 (grid G), T = 8: a compile-time-P kernel for every supported P
+template <typename G, int PC>
+cudaError_t run_p2g_f32_fixed(const GridArgs &a, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return run_p2g<8, float, G, 0>(a, s);
+    } else {
+        if (a.P == PC)
+            return run_p2g<8, float, G, PC>(a, s);
+        return run_p2g_f32_fixed<G, PC + 1>(a, s);
+    }
 }
 
 template <int T, typename R, int PC>
@@ -423,6 +683,18 @@ cudaError_t run_g2p(const GridArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int PC>
+cudaError_t run_g2p_planar(const GridArgs &a, cudaStream_t s)
+{
+    const size_t sm = G2PPlanar<PC>::smem(a.deg);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_g2p_planar<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess)
+        return e;
+    k_g2p_planar<PC><<<a.nt * a.nt * a.nt, kG2PThreads, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
 // FP32, T = 8: a compile-time-P kernel for every supported P
 template <int PC>
 cudaError_t run_g2p_f32_fixed(const GridArgs &a, cudaStream_t s)
@@ -431,7 +703,7 @@ cudaError_t run_g2p_f32_fixed(const GridArgs &a, cudaStream_t s)
         return run_g2p<8, float, 0>(a, s);
     } else {
         if (a.P == PC)
-            return run_g2p<8, float, PC>(a, s);
+            return run_g2p_planar<PC>(a, s);
         return run_g2p_f32_fixed<PC + 1>(a, s);
     }
 }
@@ -440,10 +712,16 @@ template <int T>
 cudaError_t dispatch_p2g(ewald_plan_s *p, const GridArgs &a, cudaStream_t s)
 {
     if (p->near64)
-        return run_p2g<T, double, double>(a, s);
-    if (p->fft64)
-        return run_p2g<T, float, double>(a, s);
-    return run_p2g<T, float, float>(a, s);
+        return run_p2g<T, double, double, 0>(a, s);
+    if constexpr (T == 8) {
+        if (p->fft64)
+            return run_p2g_f32_fixed<double, 2>(a, s);
+        return run_p2g_f32_fixed<float, 2>(a, s);
+    } else {
+        if (p->fft64)
+            return run_p2g<T, float, double, 0>(a, s);
+        return run_p2g<T, float, float, 0>(a, s);
+    }
 }
 
 }  // namespace

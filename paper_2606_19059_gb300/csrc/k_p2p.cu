@@ -12,13 +12,15 @@
 // Work decomposition (prior art: the shared-memory 1-D variant of Sec. 3.1):
 // one warp per chunk of <= 32 targets of one cell, one lane per target, and
 // warps of a block fully independent (no block barrier: a warp waiting on its
-// neighbours' pair counts would idle).  The sources of the (2K+1)^3 colleague
-// cells are concatenated into one stream that goes through the warp's own
-// shared-memory tile of 128.  Per tile a lane first tests all 128 candidates
-// and records the in-range ones in a 128-bit mask (phase 1, uniform across
-// the warp), then walks its own set bits (phase 2).  Only in-range pairs are
-// evaluated: about one candidate in eight is in range, so a warp evaluating
-// every candidate for all lanes would idle most lanes in the expensive branch.
+// neighbours' pair counts would idle).  The sources of the colleague cells
+// (for K = 1: those of their half-cell sub-cells that come within rc of the
+// warp's target bounding box, about half the colleague volume) are
+// concatenated into one stream that goes through the warp's own shared-memory
+// tile of 128.  Per tile a lane first tests all 128 candidates and records the
+// in-range ones in a 128-bit mask (phase 1, uniform across the warp), then
+// walks its own set bits (phase 2).  Only in-range pairs are evaluated: about
+// one candidate in four is in range, so a warp evaluating every candidate for
+// all lanes would idle most lanes in the expensive branch.
 //
 // FP32 coordinates are cell-local in cell units and split hi + lo, hi on a
 // 2^-12 lattice: colleague offsets are integers, so hi differences are exact
@@ -68,20 +70,20 @@ __device__ __forceinline__ float fast_ex2(float x)
 }
 
 struct F32Const {
-    float rc2, rc2_loose, xi, nxi2log2e, nxi2log2e_lo, c2, selfc;
+    float rc2, rc2_loose, rcm, xi, nxi2log2e, nxi2log2e_lo, c2, selfc;
 };
 
 __constant__ float c_exp2f32[EXP2_F32_N];
 
-// e^{-xi^2 r^2} = 2^y, y = r2 * (chi + clo) kept as y_hi + y_lo (the product's
-// rounding recovered by an FMA), reduced to 2^f, |f| <= 1/2, by a minimax
+// e^{-xi^2 r^2} = 2^y, y = (r2 + r2lo) * (chi + clo) kept as y_hi + y_lo (the
+// product's rounding recovered by an FMA), reduced to 2^f, |f| <= 1/2, by a minimax
 // polynomial (fit_erf.py) and scaled by 2^n through the exponent bits.  About
 // one ulp, where the hardware approximation and the FP32 rounding of y would
 // each cost a few.  Valid for -125 <= y <= 0 (here y >= -50).
-__device__ __forceinline__ float exp2_accurate(float r2, float chi, float clo)
+__device__ __forceinline__ float exp2_accurate(float r2, float r2lo, float chi, float clo)
 {
     const float yh = r2 * chi;
-    const float yl = fmaf(r2, chi, -yh) + r2 * clo;
+    const float yl = fmaf(r2, chi, -yh) + fmaf(r2lo, chi, r2 * clo);
     const float n = rintf(yh);
     const float f = (yh - n) + yl;
     float p = c_exp2f32[EXP2_F32_N - 1];
@@ -104,16 +106,15 @@ struct KSum {
     }
 };
 
-// One FP32 in-range candidate (cell units): d = (hi diff) + (lo diff).
-// KAHAN selects the tight-tolerance form (tol < 1e-6): compensated
+// One FP32 in-range candidate (cell units) at d = x_target - x_source, force
+// f.  KAHAN selects the tight-tolerance form (tol < 1e-6): compensated
 // accumulation (a blob point sums thousands of terms, and plain FP32 sums lose
-// ~eps sqrt(n/2)) and the accurate exponential above.
+// ~eps sqrt(n/2)), Newton-refined reciprocals and the accurate exponential
+// above.
 template <bool KAHAN, typename Acc>
-__device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const float4 &tl,
-                                         const float4 &sl, const float4 &f, const F32Const &k,
-                                         Acc &ax, Acc &ay, Acc &az)
+__device__ __forceinline__ void pair_f32(float dx, float dy, float dz, const float3 &f,
+                                         const F32Const &k, Acc &ax, Acc &ay, Acc &az)
 {
-    float dx = hx + (tl.x - sl.x), dy = hy + (tl.y - sl.y), dz = hz + (tl.z - sl.z);
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 > k.rc2)
         return;
@@ -129,15 +130,29 @@ __device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const flo
         }
         return;
     }
+    // tight form: the rounding error of r2 as well, r2 + r2lo exact to ~2^-48
+    // relative -- e^{-x^2} multiplies the relative error of r2 by x^2 (up to
+    // ~25 at the cutoff), which would otherwise dominate the term's error
+    float r2lo = 0.0f;
+    if constexpr (KAHAN) {
+        // _rn intrinsics: no contraction into FMAs, so each two-sum is exact
+        const float px = __fmul_rn(dx, dx), py = __fmul_rn(dy, dy), pz = __fmul_rn(dz, dz);
+        const float ex = fmaf(dx, dx, -px), ey = fmaf(dy, dy, -py), ez = fmaf(dz, dz, -pz);
+        const float s1 = __fadd_rn(px, py), b1 = __fsub_rn(s1, px);
+        const float e1 = __fadd_rn(__fsub_rn(px, __fsub_rn(s1, b1)), __fsub_rn(py, b1));
+        const float s2 = __fadd_rn(s1, pz), b2 = __fsub_rn(s2, s1);
+        const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, b2)), __fsub_rn(pz, b2));
+        r2lo = ((ex + ey) + (ez + e1)) + e2 + __fsub_rn(s2, r2);
+    }
     float rinv = rsqrtf(r2);
-    {   // one Newton step: rinv *= 1 + (1 - r2 rinv^2) / 2
+    if constexpr (KAHAN) {  // one Newton step: rinv *= 1 + (1 - r2 rinv^2) / 2
         float e = fmaf(-r2 * rinv, rinv, 1.0f);
         rinv = fmaf(0.5f * rinv, e, rinv);
     }
     float x = k.xi * (r2 * rinv);
     float E;  // e^{-xi^2 r^2}
     if constexpr (KAHAN)
-        E = exp2_accurate(r2, k.nxi2log2e, k.nxi2log2e_lo);
+        E = exp2_accurate(r2, r2lo, k.nxi2log2e, k.nxi2log2e_lo);
     else
         E = fast_ex2(r2 * k.nxi2log2e);
     float A;                               // erfc(xi r) / r
@@ -151,7 +166,8 @@ __device__ __forceinline__ void pair_f32(float hx, float hy, float hz, const flo
     } else {
         float d = fmaf((float)ERFCX_C32, x, 1.0f);
         float tt = fast_rcp(d);
-        tt = fmaf(tt, fmaf(-d, tt, 1.0f), tt);
+        if constexpr (KAHAN)
+            tt = fmaf(tt, fmaf(-d, tt, 1.0f), tt);
         float p = c_erfcx32[ERFCX_F32_N - 1];
 #pragma unroll
         for (int q = ERFCX_F32_N - 2; q >= 0; --q)
@@ -218,15 +234,16 @@ __device__ __forceinline__ int wrap(int i, int n)
 }
 
 constexpr int kWarps = 4;       // independent warps per block
-constexpr int kMaxSeg = 125;    // colleague cells (2K+1)^3, K <= 2
+constexpr int kMaxSeg = 216;    // K = 1: the 6^3 colleague sub-cells; K = 2: 125 colleague cells
 
-// Per-warp shared state: the colleague cells' source ranges concatenated
-// into one stream (prefix offsets), and one staged tile of that stream.
-template <typename S4, int NA>
+// Per-warp shared state: the colleague source ranges kept for this warp,
+// concatenated into one stream (prefix offsets), and one staged tile of it.
+template <typename Tile>
 struct WarpSmem {
-    S4 arr[NA][kTile];
+    Tile tile;
     int seg_start[kMaxSeg];
     int seg_pref[kMaxSeg + 1];
+    uint16_t seg_off[kMaxSeg];  // colleague cell offset, (dx+2) | (dy+2) << 4 | (dz+2) << 8
 };
 
 // Work item = (cell, chunk of <= 32 targets) handled by one warp.
@@ -252,44 +269,100 @@ __device__ __forceinline__ bool find_item(const P2PArgs &a, int item, int &c, in
     return true;
 }
 
-// Build the warp's segment table for cell c: segment s = colleague offset
-// (dx, dy, dz) in [-K, K]^3, its first source and the stream prefix sums.
-template <typename WS>
-__device__ __forceinline__ int build_segments(const P2PArgs &a, int c, WS &ws, int lane)
+__device__ __forceinline__ float warp_min(float v)
 {
-    const int K = a.K, side = 2 * K + 1, nseg = side * side * side, nc = a.nc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Build the warp's source stream for cell c.  K = 1: the 6^3 sub-cells (half
+// a cell wide) of the 27 colleague cells, keeping those whose box comes within
+// rc of the bounding box [blo, bhi] of the warp's targets -- the warp's 32
+// targets sit in one or two sub-cells, so about a third of the colleague
+// volume is out of reach.  K = 2 (small boxes): the 125 colleague cells, all
+// kept.  Coordinates are cell-local; `hw` is half a cell in their units and
+// `rcm` the cutoff plus a margin.  Empty segments are dropped.
+template <typename WS>
+__device__ __forceinline__ int build_segments(const P2PArgs &a, int c, WS &ws, int lane, float3 blo,
+                                              float3 bhi, float hw, float rcm)
+{
+    const int K = a.K, nc = a.nc;
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-    int carry = 0;
-    for (int s0 = 0; s0 < nseg; s0 += 32) {
-        int s = s0 + lane, len = 0;
-        if (s < nseg) {
-            int dx = s % side - K, dy = (s / side) % side - K, dz = s / (side * side) - K;
-            int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
-            int b = a.startn[nb * kSub3];
-            ws.seg_start[s] = b;
-            len = a.startn[(nb + 1) * kSub3] - b;
+    const bool sub = K == 1;
+    const int side = 2 * K + 1;
+    const int nent = sub ? 216 : side * side * side;
+    int carry = 0, kept = 0;
+    for (int s0 = 0; s0 < nent; s0 += 32) {
+        const int s = s0 + lane;
+        bool keep = false;
+        int start = 0, len = 0, off = 0;
+        if (s < nent) {
+            int dx, dy, dz, key_lo, key_hi;
+            if (sub) {
+                // half-cell index relative to this cell's corner, -2..3 per axis
+                const int ix = s % 6 - 2, iy = (s / 6) % 6 - 2, iz = s / 36 - 2;
+                const float gx = fmaxf(0.f, fmaxf(ix * hw - bhi.x, blo.x - (ix + 1) * hw));
+                const float gy = fmaxf(0.f, fmaxf(iy * hw - bhi.y, blo.y - (iy + 1) * hw));
+                const float gz = fmaxf(0.f, fmaxf(iz * hw - bhi.z, blo.z - (iz + 1) * hw));
+                keep = gx * gx + gy * gy + gz * gz <= rcm * rcm;
+                dx = ix >> 1;  // floor division by 2
+                dy = iy >> 1;
+                dz = iz >> 1;
+                const int sc = ((iz & 1) * kSub + (iy & 1)) * kSub + (ix & 1);
+                const int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
+                key_lo = nb * kSub3 + sc;
+                key_hi = key_lo + 1;
+            } else {
+                dx = s % side - K;
+                dy = (s / side) % side - K;
+                dz = s / (side * side) - K;
+                keep = true;
+                const int nb = (wrap(cz + dz, nc) * nc + wrap(cy + dy, nc)) * nc + wrap(cx + dx, nc);
+                key_lo = nb * kSub3;
+                key_hi = key_lo + kSub3;
+            }
+            if (keep) {
+                start = a.startn[key_lo];
+                len = a.startn[key_hi] - start;
+                keep = len > 0;
+                off = (dx + 2) | ((dy + 2) << 4) | ((dz + 2) << 8);
+            }
         }
-        int v = len;
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        int v = keep ? len : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int u = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o)
                 v += u;
         }
-        if (s < nseg)
-            ws.seg_pref[s + 1] = carry + v;
+        if (keep) {
+            const int pos = kept + __popc(ball & ((1u << lane) - 1u));
+            ws.seg_start[pos] = start;
+            ws.seg_off[pos] = (uint16_t)off;
+            ws.seg_pref[pos + 1] = carry + v;
+        }
         carry += __shfl_sync(0xffffffffu, v, 31);
+        kept += __popc(ball);
     }
     if (lane == 0)
         ws.seg_pref[0] = 0;
     __syncwarp();
-    return nseg;
+    return kept;
 }
 
 // Source q of the stream: its index in the sorted arrays and colleague offset.
 template <typename WS>
-__device__ __forceinline__ int locate(const WS &ws, int nseg, int side, int K, int q, int &dx,
-                                      int &dy, int &dz)
+__device__ __forceinline__ int locate(const WS &ws, int nseg, int q, int &dx, int &dy, int &dz)
 {
     int lo = 0, hi = nseg;  // seg_pref[lo] <= q < seg_pref[hi]
     while (hi - lo > 1) {
@@ -299,9 +372,10 @@ __device__ __forceinline__ int locate(const WS &ws, int nseg, int side, int K, i
         else
             hi = mid;
     }
-    dx = lo % side - K;
-    dy = (lo / side) % side - K;
-    dz = lo / (side * side) - K;
+    const int off = ws.seg_off[lo];
+    dx = (off & 15) - 2;
+    dy = ((off >> 4) & 15) - 2;
+    dz = ((off >> 8) & 15) - 2;
     return ws.seg_start[lo] + (q - ws.seg_pref[lo]);
 }
 
@@ -327,21 +401,31 @@ __device__ __forceinline__ void build_masks(float rc2, Test test, unsigned long 
 
 constexpr float kFar = 1.0e9f;  // dummy source position: never within rc
 
+// Next set bit of the 128-bit mask (m0 first), without divergent branches.
 __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long long &m1)
 {
-    int k;
-    if (m0) {
-        k = __ffsll((long long)m0) - 1;
-        m0 &= m0 - 1;
-    } else {
-        k = 64 + __ffsll((long long)m1) - 1;
-        m1 &= m1 - 1;
-    }
+    const bool first = m0 != 0ull;
+    unsigned long long m = first ? m0 : m1;
+    const int k = __ffsll((long long)m) - 1 + (first ? 0 : 64);
+    m &= m - 1;
+    m0 = first ? m : m0;
+    m1 = first ? m1 : m;
     return k;
 }
 
-using WsF32 = WarpSmem<float4, 3>;
-using WsF64 = WarpSmem<dvec4, 2>;
+// FP32 tile of 128 sources: sa = (hi + colleague offset, lo.x), sb = (lo.y,
+// lo.z, f.x, f.y), sc = f.z -- 36 bytes a source, phase 1 reading sa only.
+struct TileF32 {
+    float4 sa[kTile];
+    float4 sb[kTile];
+    float sc[kTile];
+};
+struct TileF64 {
+    dvec4 sp[kTile];
+    dvec4 sf[kTile];
+};
+using WsF32 = WarpSmem<TileF32>;
+using WsF64 = WarpSmem<TileF64>;
 
 // KAHAN: compensated per-tile sums and FP64 accumulation across tiles.
 template <bool KAHAN>
@@ -351,7 +435,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
     __shared__ WsF32 wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WsF32 &ws = wsm[warp];
-    float4 *sh = ws.arr[0], *sl = ws.arr[1], *sf = ws.arr[2];
+    float4 *sa = ws.tile.sa, *sb = ws.tile.sb;
+    float *sc = ws.tile.sc;
     int c, tb, te;
     if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
         return;  // whole warp: no block-wide barrier follows
@@ -364,8 +449,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
         th = npos[t];
         tl = nlo[t];
     }
-    const int nseg = build_segments(a, c, ws, lane);
-    const int side = 2 * a.K + 1;
+    // the warp's target bounding box (hi parts; the margin covers lo)
+    const float3 blo = make_float3(warp_min(active ? th.x : 1e30f), warp_min(active ? th.y : 1e30f),
+                                   warp_min(active ? th.z : 1e30f));
+    const float3 bhi = make_float3(warp_max(active ? th.x : -1e30f),
+                                   warp_max(active ? th.y : -1e30f),
+                                   warp_max(active ? th.z : -1e30f));
+    const int nseg = build_segments(a, c, ws, lane, blo, bhi, 0.5f, kc.rcm);
     const int total = ws.seg_pref[nseg];
     // tile t holds the stream elements t, t + ntiles, t + 2 ntiles, ...: each
     // tile samples the whole neighbourhood, so the lanes' in-range counts per
@@ -379,16 +469,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
             const int k = lane + 32 * i, q = tile + k * ntile;
             if (k < n) {
                 int dx, dy, dz;
-                const int j = locate(ws, nseg, side, a.K, q, dx, dy, dz);
-                float4 p = npos[j];
-                p.x += (float)dx;  // exact: integer colleague offsets, hi on a 2^-12 lattice
-                p.y += (float)dy;
-                p.z += (float)dz;
-                sh[k] = p;
-                sl[k] = nlo[j];
-                sf[k] = nfrc[j];
+                const int j = locate(ws, nseg, q, dx, dy, dz);
+                const float4 p = npos[j], l = nlo[j], f = nfrc[j];
+                // exact: integer colleague offsets, hi on a 2^-12 lattice
+                sa[k] = make_float4(p.x + (float)dx, p.y + (float)dy, p.z + (float)dz, l.x);
+                sb[k] = make_float4(l.y, l.z, f.x, f.y);
+                sc[k] = f.z;
             } else {
-                sh[k] = make_float4(kFar, kFar, kFar, 0.f);
+                sa[k] = make_float4(kFar, kFar, kFar, 0.f);
             }
         }
         __syncwarp();
@@ -397,7 +485,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
             build_masks(
                 kc.rc2_loose,
                 [&](int k) {
-                    float4 s = sh[k];
+                    const float4 s = sa[k];
                     float hx = th.x - s.x, hy = th.y - s.y, hz = th.z - s.z;
                     return fmaf(hx, hx, fmaf(hy, hy, hz * hz));
                 },
@@ -406,9 +494,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
             typename std::conditional<KAHAN, KSum, float>::type px{}, py{}, pz{};
             while (m0 | m1) {
                 const int k = next_bit(m0, m1);
-                const float4 s = sh[k];
-                pair_f32<KAHAN>(th.x - s.x, th.y - s.y, th.z - s.z, tl, sl[k], sf[k], kc, px, py,
-                                pz);
+                const float4 s = sa[k], b = sb[k];
+                // d = (hi diff, exact) + (lo diff)
+                pair_f32<KAHAN>((th.x - s.x) + (tl.x - s.w), (th.y - s.y) + (tl.y - b.x),
+                                (th.z - s.z) + (tl.z - b.y), make_float3(b.z, b.w, sc[k]), kc,
+                                px, py, pz);
             }
             if constexpr (KAHAN) {
                 ux += (double)px.s + (double)px.c * -1.0;
@@ -436,7 +526,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
     __shared__ WsF64 wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WsF64 &ws = wsm[warp];
-    dvec4 *sp = ws.arr[0], *sf = ws.arr[1];
+    dvec4 *sp = ws.tile.sp, *sf = ws.tile.sf;
     int c, tb, te;
     if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
         return;
@@ -449,8 +539,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
     const double rc2 = a.rc * a.rc, xi = a.xi, xi2 = a.xi * a.xi;
     const double c2 = 2.0 * a.xi / sqrt(3.14159265358979323846), selfc = 2.0 * c2;
     const float rc2f = (float)(rc2 * (1.0 + 1e-4));
-    const int nseg = build_segments(a, c, ws, lane);
-    const int side = 2 * a.K + 1;
+    const float3 blo = make_float3(warp_min(active ? (float)xt.x : 1e30f),
+                                   warp_min(active ? (float)xt.y : 1e30f),
+                                   warp_min(active ? (float)xt.z : 1e30f));
+    const float3 bhi = make_float3(warp_max(active ? (float)xt.x : -1e30f),
+                                   warp_max(active ? (float)xt.y : -1e30f),
+                                   warp_max(active ? (float)xt.z : -1e30f));
+    const int nseg = build_segments(a, c, ws, lane, blo, bhi, (float)(0.5 * a.cell),
+                                    (float)(a.rc + 1e-3 * a.cell));
     const int total = ws.seg_pref[nseg];
     const int ntile = (total + kTile - 1) / kTile;  // strided tiles, as in k_p2p_f32
     double ux = 0.0, uy = 0.0, uz = 0.0;
@@ -461,7 +557,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
             const int k = lane + 32 * i, q = tile + k * ntile;
             if (k < n) {
                 int dx, dy, dz;
-                const int j = locate(ws, nseg, side, a.K, q, dx, dy, dz);
+                const int j = locate(ws, nseg, q, dx, dy, dz);
                 dvec4 p = npos[j];
                 p.x += dx * a.cell;
                 p.y += dy * a.cell;
@@ -570,6 +666,7 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
         kc.rc2 = (float)(rcc * rcc);
         kc.rc2_loose = (float)(rcc * rcc * (1.0 + 2e-3));
+        kc.rcm = (float)(rcc + 1e-3);  // sub-cell culling reach: |lo| <= 2^-13 fits the margin
         kc.xi = (float)xic;
         const double c = -xic * xic * 1.4426950408889634;  // -xi^2 log2(e), cell units
         kc.nxi2log2e = (float)c;

@@ -76,7 +76,7 @@ void free_plan(ewald_plan_s *p)
     if (!p)
         return;
     void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
-                    p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc,
+                    p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec,
                     p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
                     p->err, p->hx, p->hf, p->hu};
     for (void *b : bufs)
@@ -141,9 +141,12 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_CUDA(dalloc(p, &p->startt, 4 * ((size_t)g.ntiles + 1)));
     EW_CUDA(dalloc(p, &p->items, 4 * ((size_t)g.ncells + 1)));
     EW_CUDA(dalloc(p, &p->item_off, 4 * ((size_t)g.ncells + 1)));
-    EW_CUDA(dalloc(p, &p->npos, r4 * N));
-    EW_CUDA(dalloc(p, &p->nfrc, r4 * N));
-    EW_CUDA(dalloc(p, &p->nlo, p->near64 ? 16 : 16 * N));
+    if (p->near64) {
+        EW_CUDA(dalloc(p, &p->npos, r4 * N));
+        EW_CUDA(dalloc(p, &p->nfrc, r4 * N));
+    } else {
+        EW_CUDA(dalloc(p, &p->nrec, 32 * N));
+    }
     EW_CUDA(dalloc(p, &p->tdat, r4 * N));
     EW_CUDA(dalloc(p, &p->tfrc, r4 * N));
     EW_CUDA(dalloc(p, &p->un, 3 * rs * N));

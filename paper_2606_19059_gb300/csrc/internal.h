@@ -66,7 +66,8 @@ struct ewald_plan_s {
     int32_t *items = nullptr, *item_off = nullptr;  // P2P work items per cell (ncells + 1)
     int32_t *permn = nullptr, *permt = nullptr;   // sorted slot -> user index
     void *npos = nullptr, *nfrc = nullptr;        // near-sorted positions (cell-local) / forces
-    void *nlo = nullptr;                          // FP32: low parts of the near-sorted positions
+    void *nlo = nullptr;                          // (unused since the FP32 records)
+    void *nrec = nullptr;                         // FP32: near-sorted 32-byte source records
     void *tdat = nullptr, *tfrc = nullptr;        // tile-sorted window data / forces
     void *un = nullptr, *uf = nullptr;            // near / far results, user order
     void *grid = nullptr;                         // 3 M^3 real

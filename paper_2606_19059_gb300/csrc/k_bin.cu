@@ -23,7 +23,7 @@ struct KeyArgs {
     int nc, M, T, nt, ceilP2;
     int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
     const int32_t *startn, *startt;
-    void *npos, *nlo, *nfrc, *tdat, *tfrc;
+    void *npos, *nfrc, *nrec, *tdat, *tfrc;
     int *err;
 };
 
@@ -97,31 +97,38 @@ __global__ void k_bin_scatter(KeyArgs k)
     Bin b = compute_bin(k, i);
     int pn = k.startn[k.keyn[i]] + k.slotn[i];
     int pt = k.startt[k.keyt[i]] + k.slott[i];
-    R4 *npos = (R4 *)k.npos, *nfrc = (R4 *)k.nfrc, *tdat = (R4 *)k.tdat, *tfrc = (R4 *)k.tfrc;
-    R4 pos;
+    R4 *tdat = (R4 *)k.tdat, *tfrc = (R4 *)k.tfrc;
     if constexpr (sizeof(R) == 4) {
-        // cell-local position in cell units, split hi + lo with hi on a 2^-12
-        // lattice (exact in FP32, exact differences) and |lo| <= 2^-13
-        R4 lo;
-        double X[3];
+        // FP32 near record (32 bytes): cell-local position in cell units split
+        // hi + lo, hi on a 2^-12 lattice stored as integers (exact in FP32,
+        // exact differences), |lo| <= 2^-13, and the force:
+        //   (lo.x, lo.y, lo.z, f.x) (f.y, f.z, hi.x | hi.y << 16, hi.z)
+        float lo[3];
+        int hq[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double q = b.xw[d] * k.inv_cell - b.c[d];
-            X[d] = rint(q * 4096.0) * (1.0 / 4096.0);
-            ((R *)&lo)[d] = (R)(q - X[d]);
+            const double q = b.xw[d] * k.inv_cell - b.c[d];
+            const double X = rint(q * 4096.0);
+            hq[d] = (int)X;  // 0 .. 4096
+            lo[d] = (float)(q - X * (1.0 / 4096.0));
         }
-        pos.x = (R)X[0];
-        pos.y = (R)X[1];
-        pos.z = (R)X[2];
-        lo.w = (R)0;
-        ((R4 *)k.nlo)[pn] = lo;
+        float fx = 0.f, fy = 0.f, fz = 0.f;  // set_positions: forces come later
+        if (k.f) {
+            fx = (float)k.f[3 * i];
+            fy = (float)k.f[3 * i + 1];
+            fz = (float)k.f[3 * i + 2];
+        }
+        float4 *rec = (float4 *)k.nrec + 2 * (int64_t)pn;
+        rec[0] = make_float4(lo[0], lo[1], lo[2], fx);
+        rec[1] = make_float4(fy, fz, __int_as_float(hq[0] | (hq[1] << 16)), __int_as_float(hq[2]));
     } else {
+        R4 pos;
         pos.x = (R)(b.xw[0] - b.c[0] * k.cell);
         pos.y = (R)(b.xw[1] - b.c[1] * k.cell);
         pos.z = (R)(b.xw[2] - b.c[2] * k.cell);
+        pos.w = (R)0;
+        ((R4 *)k.npos)[pn] = pos;
     }
-    pos.w = (R)0;
-    npos[pn] = pos;
     k.permn[pn] = (int32_t)i;
     int packed = (b.a[0] - b.tl[0] * k.T) | ((b.a[1] - b.tl[1] * k.T) << 4) |
                  ((b.a[2] - b.tl[2] * k.T) << 8);
@@ -138,29 +145,40 @@ __global__ void k_bin_scatter(KeyArgs k)
         fv.y = (R)k.f[3 * i + 1];
         fv.z = (R)k.f[3 * i + 2];
         fv.w = (R)0;
-        nfrc[pn] = fv;
+        if constexpr (sizeof(R) == 8)
+            ((R4 *)k.nfrc)[pn] = fv;
         tfrc[pt] = fv;
     }
 }
 
+// Forces into both sorted orders: FP64 near forces as 4-vectors, FP32 into
+// the force slots of the near records (floats 3, 4, 5 of each 8).
 template <typename R, typename R4>
 __global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__restrict__ permn,
-                                const int32_t *__restrict__ permt, R4 *nfrc, R4 *tfrc, int64_t N)
+                                const int32_t *__restrict__ permt, void *near, R4 *tfrc, int64_t N)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N)
         return;
     int in = permn[p], it = permt[p];
-    R4 a, b;
-    a.x = (R)f[3 * in];
-    a.y = (R)f[3 * in + 1];
-    a.z = (R)f[3 * in + 2];
-    a.w = (R)0;
+    if constexpr (sizeof(R) == 8) {
+        R4 a;
+        a.x = f[3 * in];
+        a.y = f[3 * in + 1];
+        a.z = f[3 * in + 2];
+        a.w = 0.0;
+        ((R4 *)near)[p] = a;
+    } else {
+        float *r = (float *)near + 8 * p;
+        r[3] = (float)f[3 * in];
+        r[4] = (float)f[3 * in + 1];
+        r[5] = (float)f[3 * in + 2];
+    }
+    R4 b;
     b.x = (R)f[3 * it];
     b.y = (R)f[3 * it + 1];
     b.z = (R)f[3 * it + 2];
     b.w = (R)0;
-    nfrc[p] = a;
     tfrc[p] = b;
 }
 
@@ -275,8 +293,8 @@ KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
     k.startn = p->startn;
     k.startt = p->startt;
     k.npos = p->npos;
-    k.nlo = p->nlo;
     k.nfrc = p->nfrc;
+    k.nrec = p->nrec;
     k.tdat = p->tdat;
     k.tfrc = p->tfrc;
     k.err = p->err;
@@ -314,10 +332,10 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
 {
     if (p->near64)
         k_gather_forces<double, dvec4><<<blocks_for(p->N, 256), 256, 0, s>>>(
-            f, p->permn, p->permt, (dvec4 *)p->nfrc, (dvec4 *)p->tfrc, p->N);
+            f, p->permn, p->permt, p->nfrc, (dvec4 *)p->tfrc, p->N);
     else
         k_gather_forces<float, float4><<<blocks_for(p->N, 256), 256, 0, s>>>(
-            f, p->permn, p->permt, (float4 *)p->nfrc, (float4 *)p->tfrc, p->N);
+            f, p->permn, p->permt, p->nrec, (float4 *)p->tfrc, p->N);
     return cudaGetLastError();
 }
 

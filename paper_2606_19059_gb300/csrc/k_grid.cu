@@ -24,6 +24,8 @@
 // shuffle reduction at the end.
 #include <math.h>
 
+#include <utility>
+
 #include "internal.h"
 
 namespace ewg {
@@ -485,12 +487,14 @@ __host__ __device__ constexpr int g2p_stride(int P)
     return best;
 }
 
+constexpr int kG2PPlanarThreads = 512;  // 16 warps: two blocks fill an SM's 64 warps by half
+
 template <int PC>
 struct G2PPlanar {
     static constexpr int T = 8, RR = T + PC - 1, S = g2p_stride(PC), NR = g2p_rounds(PC, S);
     static constexpr int NCH = (RR + 3) / 4;  // 16-byte chunks per staged row
     static constexpr int PS = (PC + 3) & ~3;
-    static constexpr int NW = kG2PThreads / 32;
+    static constexpr int NW = kG2PPlanarThreads / 32;
     static constexpr size_t grid_bytes = sizeof(float) * 3 * RR * RR * S;
     static size_t smem(int deg)
     {
@@ -498,12 +502,44 @@ struct G2PPlanar {
     }
 };
 
+// Shared-memory loads by 32-bit shared address, the offset an immediate.
+template <int OFF>
+__device__ __forceinline__ float lds_imm(unsigned addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+__device__ __forceinline__ float lds_reg(unsigned addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
+// s_c += sum_k wz[k] v_c[z0 + k] down one staged column, two partial sums
+// per component (even and odd k) for instruction-level parallelism.
+template <int PLANE, int VOL, int... K>
+__device__ __forceinline__ void column_sum(unsigned a, const float *wz, float (&e)[3],
+                                           float (&o)[3], std::integer_sequence<int, K...>)
+{
+    ((K % 2 == 0
+          ? (e[0] = fmaf(wz[K], lds_imm<4 * K * PLANE>(a), e[0]),
+             e[1] = fmaf(wz[K], lds_imm<4 * (VOL + K * PLANE)>(a), e[1]),
+             e[2] = fmaf(wz[K], lds_imm<4 * (2 * VOL + K * PLANE)>(a), e[2]))
+          : (o[0] = fmaf(wz[K], lds_imm<4 * K * PLANE>(a), o[0]),
+             o[1] = fmaf(wz[K], lds_imm<4 * (VOL + K * PLANE)>(a), o[1]),
+             o[2] = fmaf(wz[K], lds_imm<4 * (2 * VOL + K * PLANE)>(a), o[2]))),
+     ...);
+}
+
 template <int PC>
-__global__ void __launch_bounds__(kG2PThreads) k_g2p_planar(GridArgs a)
+__global__ void __launch_bounds__(kG2PPlanarThreads, 2) k_g2p_planar(GridArgs a)
 {
     using G = G2PPlanar<PC>;
     constexpr int T = G::T, RR = G::RR, S = G::S, NR = G::NR, NCH = G::NCH, PS = G::PS;
     constexpr int PLANE = RR * S, VOL = RR * PLANE;
+    constexpr int NIT = (RR * NCH + 31) / 32;  // staging: lane iterations per plane
     const int tile = blockIdx.x;
     const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
     if (s0 == s1)
@@ -513,25 +549,40 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_planar(GridArgs a)
     int *tab = (int *)(smem + G::grid_bytes);                   // [NR][32]
     float *wsm = (float *)(tab + NR * 32);                      // per warp [3][PS]
     float *coef = wsm + G::NW * 3 * PS;                         // [deg+1][PS]
+    const unsigned vs_a = (unsigned)__cvta_generic_to_shared(vs);
     const int nt = a.nt, M = a.M, nd = a.deg + 1;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // stage: 16-byte copies, M a multiple of 8 keeps every chunk on one side of
-    // the periodic wrap and M >= P keeps one wrap enough
-    const float *grid = (const float *)a.grid;
-    const int64_t M3 = (int64_t)M * M * M;
-    for (int i = threadIdx.x; i < 3 * RR * RR * NCH; i += kG2PThreads) {
-        const int ch = i % NCH, row = i / NCH;
-        const int y = row % RR, z = (row / RR) % RR, c = row / (RR * RR);
-        int gx = tx * T + 4 * ch, gy = ty * T + y, gz = tz * T + z;
-        gx -= gx >= M ? M : 0;
-        gy -= gy >= M ? M : 0;
-        gz -= gz >= M ? M : 0;
-        const float *src = grid + c * M3 + ((int64_t)gz * M + gy) * M + gx;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(vs + (c * RR + z) * PLANE + y * S + 4 * ch);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+    // stage: one warp per (component, z) plane, lanes over (row, 16-byte
+    // chunk); M a multiple of 8 keeps every chunk on one side of the periodic
+    // wrap and M >= P keeps one wrap enough
+    {
+        int rowoff[NIT], dstoff[NIT];
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+            const int t = lane + 32 * it, y = t / NCH, ch = t - y * NCH;
+            int gx = tx * T + 4 * ch, gy = ty * T + y;
+            gx -= gx >= M ? M : 0;
+            gy -= gy >= M ? M : 0;
+            rowoff[it] = t < RR * NCH ? gy * M + gx : -1;
+            dstoff[it] = 4 * (y * S + 4 * ch);
+        }
+        const float *grid = (const float *)a.grid;
+        const int64_t M2 = (int64_t)M * M, M3 = M2 * M;
+        for (int cz = warp; cz < 3 * RR; cz += G::NW) {
+            const int c = cz / RR, z = cz - c * RR;
+            int gz = tz * T + z;
+            gz -= gz >= M ? M : 0;
+            const float *plane = grid + c * M3 + gz * M2;
+            const unsigned dplane = vs_a + 4 * cz * PLANE;
+#pragma unroll
+            for (int it = 0; it < NIT; ++it)
+                if (rowoff[it] >= 0)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dplane + dstoff[it]),
+                                 "l"(plane + rowoff[it]));
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
     }
-    asm volatile("cp.async.commit_group;\n" ::);
     // bank-dealt (y, x) pairs: lane b, round r -> the r-th row yy whose pair
     // on bank b exists, packed yy << 8 | xx, -1 past the last
     if (threadIdx.x < 32) {
@@ -544,13 +595,30 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_planar(GridArgs a)
         for (; r < NR; ++r)
             tab[r * 32 + lane] = -1;
     }
-    for (int i = threadIdx.x; i < nd * PS; i += kG2PThreads) {
+    for (int i = threadIdx.x; i < nd * PS; i += kG2PPlanarThreads) {
         const int j = i / PS, l = i - j * PS;
         coef[i] = l < PC ? ((const float *)a.wcoef)[l * nd + j] : 0.f;
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     float *w = wsm + warp * 3 * PS;
+    const unsigned w_a = (unsigned)__cvta_generic_to_shared(w);
+    // this lane's pairs, block-invariant: column byte offset and weight addresses
+    int roff[NR];
+    unsigned wy_a[NR], wx_a[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int e = tab[r * 32 + lane];
+        const int yy = e >> 8, xx = e & 255;
+        roff[r] = e >= 0 ? 4 * (yy * S + xx) : -1;
+        wy_a[r] = w_a + 4 * (PS + (e >= 0 ? yy : 0));
+        wx_a[r] = w_a + 4 * (e >= 0 ? xx : 0);
+    }
+    // window-weight lanes: (d, l) = lane and lane + 32 over 3 axes x P bins
+    const int q0 = lane, q1 = lane + 32;
+    const int d0 = q0 / PC, l0 = q0 - d0 * PC, d1 = q1 / PC, l1 = q1 - d1 * PC;
+    const bool ok0 = q0 < 3 * PC, ok1 = q1 < 3 * PC;
+    const int c0 = ok0 ? l0 : 0, c1 = ok1 ? l1 : 0;
     const float4 *tdat = (const float4 *)a.tdat;
     float *uf = (float *)a.uf;
     for (int p = s0 + warp; p < s1; p += G::NW) {
@@ -558,14 +626,9 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_planar(GridArgs a)
         const int packed = (int)td.w;
         const int ox = packed & 15, oy = (packed >> 4) & 15, oz = (packed >> 8) & 15;
         __syncwarp();
-        // window weights: lane (d, l) and (d', l') = lane + 32, shared z per axis
         {
-            const int q0 = lane, q1 = lane + 32;
-            const int d0 = q0 / PC, l0 = q0 - d0 * PC, d1 = q1 / PC, l1 = q1 - d1 * PC;
-            const bool ok0 = q0 < 3 * PC, ok1 = q1 < 3 * PC;
             const float z0 = 2.f * (d0 == 0 ? td.x : (d0 == 1 ? td.y : td.z)) - 1.f;
             const float z1 = 2.f * (d1 == 0 ? td.x : (d1 == 1 ? td.y : td.z)) - 1.f;
-            const int c0 = ok0 ? l0 : 0, c1 = ok1 ? l1 : 0;
             float v0 = coef[(nd - 1) * PS + c0], v1 = coef[(nd - 1) * PS + c1];
             for (int j = nd - 2; j >= 0; --j) {
                 v0 = fmaf(v0, z0, coef[j * PS + c0]);
@@ -581,25 +644,17 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p_planar(GridArgs a)
 #pragma unroll
         for (int k = 0; k < PC; ++k)
             wz[k] = w[2 * PS + k];
-        const float *vb = vs + (oz * RR + oy) * S + ox;
+        const unsigned vb = vs_a + 4 * ((oz * RR + oy) * S + ox);
         float u0 = 0.f, u1 = 0.f, u2 = 0.f;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const int e = tab[r * 32 + lane];
-            if (e >= 0) {
-                const int yy = e >> 8, xx = e & 255;
-                const float wyx = w[PS + yy] * w[xx];
-                const float *v = vb + yy * S + xx;
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll
-                for (int k = 0; k < PC; ++k) {
-                    a0 = fmaf(wz[k], v[k * PLANE], a0);
-                    a1 = fmaf(wz[k], v[VOL + k * PLANE], a1);
-                    a2 = fmaf(wz[k], v[2 * VOL + k * PLANE], a2);
-                }
-                u0 = fmaf(wyx, a0, u0);
-                u1 = fmaf(wyx, a1, u1);
-                u2 = fmaf(wyx, a2, u2);
+            if (roff[r] >= 0) {
+                const float wyx = lds_reg(wy_a[r]) * lds_reg(wx_a[r]);
+                float e[3] = {0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f};
+                column_sum<PLANE, VOL>(vb + roff[r], wz, e, o, std::make_integer_sequence<int, PC>{});
+                u0 = fmaf(wyx, e[0] + o[0], u0);
+                u1 = fmaf(wyx, e[1] + o[1], u1);
+                u2 = fmaf(wyx, e[2] + o[2], u2);
             }
         }
 #pragma unroll
@@ -691,7 +746,7 @@ cudaError_t run_g2p_planar(const GridArgs &a, cudaStream_t s)
         cudaFuncSetAttribute(k_g2p_planar<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess)
         return e;
-    k_g2p_planar<PC><<<a.nt * a.nt * a.nt, kG2PThreads, sm, s>>>(a);
+    k_g2p_planar<PC><<<a.nt * a.nt * a.nt, kG2PPlanarThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -16,11 +16,12 @@
 // (for K = 1: those of their half-cell sub-cells that come within rc of the
 // warp's target bounding box, about half the colleague volume) are
 // concatenated into one stream that goes through the warp's own shared-memory
-// tile of 128.  Per tile a lane first tests all 128 candidates and records the
-// in-range ones in a 128-bit mask (phase 1, uniform across the warp), then
-// walks its own set bits (phase 2).  Only in-range pairs are evaluated: about
-// one candidate in four is in range, so a warp evaluating every candidate for
-// all lanes would idle most lanes in the expensive branch.
+// tiles (FP32: a ring of two 64-source tiles; FP64: one tile of 128).  Per
+// tile a lane first tests every candidate and records the in-range ones in a
+// bit mask (phase 1, uniform across the warp; FP32 tests in FP16x2 with a
+// safety margin), then walks its own set bits (phase 2).  Only in-range pairs
+// are evaluated: about one candidate in five is in range, so a warp evaluating
+// every candidate for all lanes would idle most lanes in the expensive branch.
 //
 // FP32 coordinates are cell-local in cell units and split hi + lo, hi on a
 // 2^-12 lattice: colleague offsets are integers, so hi differences are exact
@@ -29,8 +30,11 @@
 // cell-local coordinates in length units.
 //
 // erfc: FP64 uses the paper's rational erf(x)/x (Sec. 4) with erfc(x)/x =
-// 1/x - erf(x)/x.  FP32 uses that form with a polynomial erf(x)/x below x = 1
-// and a rational erfcx times e^{-x^2} above (see fit_erf.py).
+// 1/x - erf(x)/x.  FP32 uses erfcx(x) = e^{x^2} erfc(x) as a polynomial in
+// t = 1/(1 + x/2) times the e^{-x^2} the Gaussian term needs anyway (see
+// fit_erf.py); the tight-tolerance form keeps the paper's form with a
+// polynomial erf(x)/x below x = 1, where 1/r dominates.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <type_traits>
@@ -49,7 +53,8 @@ __constant__ double c_erfq64[ERF_RAT_F64_N];
 constexpr int kTile = 128;  // sources per staged tile = bits of the two masks
 
 struct P2PArgs {
-    const void *npos, *nlo, *nfrc;
+    const void *npos, *nfrc;  // FP64: cell-local positions, forces (4-vectors)
+    const void *nrec;         // FP32: 32-byte records (lo.xyz, f.xyz, hi lattice)
     const int32_t *startn, *item_off, *permn;
     void *un;
     int nc, K, ncells;
@@ -70,7 +75,7 @@ __device__ __forceinline__ float fast_ex2(float x)
 }
 
 struct F32Const {
-    float rc2, rc2_loose, rcm, xi, nxi2log2e, nxi2log2e_lo, c2, selfc;
+    float rc2, rc2_half, rcm, xi, nxi2log2e, nxi2log2e_lo, c2, selfc;
 };
 
 __constant__ float c_exp2f32[EXP2_F32_N];
@@ -156,7 +161,9 @@ __device__ __forceinline__ void pair_f32(float dx, float dy, float dz, const flo
     else
         E = fast_ex2(r2 * k.nxi2log2e);
     float A;                               // erfc(xi r) / r
-    if (x < (float)ERFX_SMALL_X32) {
+    // the tight form keeps 1/r exact for close pairs (small-x branch); the
+    // bulk form takes erfcx on all of [0, 6], ~3e-7 relative in FP32
+    if (KAHAN && x < (float)ERFX_SMALL_X32) {
         float t = x * x;
         float p = c_erfxs32[ERFX_SMALL_N - 1];
 #pragma unroll
@@ -187,6 +194,34 @@ __device__ __forceinline__ void pair_f32(float dx, float dy, float dz, const flo
         ay = fmaf(amb, f.y, fmaf(co, dy, ay));
         az = fmaf(amb, f.z, fmaf(co, dz, az));
     }
+}
+
+// Bulk form without branches, for two pairs in flight per lane: every
+// candidate runs the same instructions and the result is selected -- in range
+// (0 < r2 <= rc2): the kernel term; r2 = 0: the removed far part of the skipped
+// pair; beyond rc: nothing.  Returns the contribution.
+__device__ __forceinline__ float3 pair_f32_bulk(float dx, float dy, float dz, const float3 &f,
+                                                const F32Const &k)
+{
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool in = r2 <= k.rc2 && r2 > 0.0f;
+    const float r2s = in ? r2 : 1.0f;  // keeps the arithmetic finite off range
+    const float rinv = rsqrtf(r2s);
+    const float x = k.xi * (r2s * rinv);
+    const float E = fast_ex2(r2s * k.nxi2log2e);
+    const float tt = fast_rcp(fmaf((float)ERFCX_C32, x, 1.0f));
+    float p = c_erfcx32[ERFCX_F32_N - 1];
+#pragma unroll
+    for (int q = ERFCX_F32_N - 2; q >= 0; --q)
+        p = fmaf(p, tt, c_erfcx32[q]);
+    const float A = (E * (tt * p)) * rinv;  // e^{-x^2} erfcx(x) / r
+    const float B = k.c2 * E;
+    const float amb = A - B, apb = A + B;
+    const float rf = fmaf(dx, f.x, fmaf(dy, f.y, dz * f.z));
+    const float co = apb * rf * (rinv * rinv);
+    const float sc = r2 == 0.0f ? -k.selfc : 0.0f;
+    return make_float3(in ? fmaf(amb, f.x, co * dx) : sc * f.x, in ? fmaf(amb, f.y, co * dy) : sc * f.y,
+                       in ? fmaf(amb, f.z, co * dz) : sc * f.z);
 }
 
 // One FP64 in-range candidate (length units) with the paper's erf(x)/x.
@@ -360,9 +395,9 @@ __device__ __forceinline__ int build_segments(const P2PArgs &a, int c, WS &ws, i
     return kept;
 }
 
-// Source q of the stream: its index in the sorted arrays and colleague offset.
+// Segment of stream element q (binary search over the prefix offsets).
 template <typename WS>
-__device__ __forceinline__ int locate(const WS &ws, int nseg, int q, int &dx, int &dy, int &dz)
+__device__ __forceinline__ int seg_of(const WS &ws, int nseg, int q)
 {
     int lo = 0, hi = nseg;  // seg_pref[lo] <= q < seg_pref[hi]
     while (hi - lo > 1) {
@@ -372,11 +407,26 @@ __device__ __forceinline__ int locate(const WS &ws, int nseg, int q, int &dx, in
         else
             hi = mid;
     }
-    const int off = ws.seg_off[lo];
+    return lo;
+}
+
+// Stream element q of segment sg: its index in the sorted arrays and the
+// colleague cell offset.
+template <typename WS>
+__device__ __forceinline__ int seg_element(const WS &ws, int sg, int q, int &dx, int &dy, int &dz)
+{
+    const int off = ws.seg_off[sg];
     dx = (off & 15) - 2;
     dy = ((off >> 4) & 15) - 2;
     dz = ((off >> 8) & 15) - 2;
-    return ws.seg_start[lo] + (q - ws.seg_pref[lo]);
+    return ws.seg_start[sg] + (q - ws.seg_pref[sg]);
+}
+
+// Source q of the stream: its index in the sorted arrays and colleague offset.
+template <typename WS>
+__device__ __forceinline__ int locate(const WS &ws, int nseg, int q, int &dx, int &dy, int &dz)
+{
+    return seg_element(ws, seg_of(ws, nseg, q), q, dx, dy, dz);
 }
 
 // Phase 1 over a staged tile: bit k of (m0, m1) set when source k may be in
@@ -400,6 +450,42 @@ __device__ __forceinline__ void build_masks(float rc2, Test test, unsigned long 
 }
 
 constexpr float kFar = 1.0e9f;  // dummy source position: never within rc
+constexpr float kFarHalf = 64.0f;  // FP16 dummy: r^2 ~ 1e4, finite and never within rc
+
+// FP32 kernel: tiles of 64 sources, two staged at once (a ring of two slots),
+// so a lane may run up to one tile ahead of the slowest lane of its warp: the
+// warp's pair iterations then follow the busiest lane's total over the whole
+// stream instead of the sum over tiles of each tile's busiest lane (about a
+// fifth fewer for Poisson-like in-range counts of ~11 per lane and tile).
+constexpr int kT32 = 64;
+
+// FP16x2 phase 1 over one 64-source tile: each shared load brings sources k
+// and k + 32, one FP16x2 distance test covers both, and one AND-OR files the
+// two results.  Word w of the mask holds slot pairs 16 w .. 16 w + 15: bit b < 16
+// is source 16 w + b, bit 16 + b is source 32 + 16 w + b (half_slot inverts
+// this).  Coordinates are cell-local with |value| <= 3, so FP16 keeps their
+// differences to ~2^-10.
+__device__ __forceinline__ unsigned long long phase1_half(const uint4 *sh, __half2 tx, __half2 ty,
+                                                          __half2 tz, __half2 lim)
+{
+    unsigned acc[2] = {0u, 0u};
+#pragma unroll
+    for (int k = 0; k < kT32 / 2; ++k) {
+        const uint4 v = sh[k];
+        const __half2 dx = __hsub2(tx, *(const __half2 *)&v.x);
+        const __half2 dy = __hsub2(ty, *(const __half2 *)&v.y);
+        const __half2 dz = __hsub2(tz, *(const __half2 *)&v.z);
+        const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
+        acc[k >> 4] |= __hle2_mask(r2, lim) & ((1u << (k & 15)) | (1u << (16 + (k & 15))));
+    }
+    return ((unsigned long long)acc[1] << 32) | acc[0];
+}
+
+// Tile slot of bit position p (0..63) of a phase1_half mask.
+__device__ __forceinline__ int half_slot(int p)
+{
+    return ((p >> 5) << 4) + (p & 15) + ((p & 16) << 1);
+}
 
 // Next set bit of the 128-bit mask (m0 first), without divergent branches.
 __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long long &m1)
@@ -413,12 +499,14 @@ __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long lo
     return k;
 }
 
-// FP32 tile of 128 sources: sa = (hi + colleague offset, lo.x), sb = (lo.y,
-// lo.z, f.x, f.y), sc = f.z -- 36 bytes a source, phase 1 reading sa only.
+// FP32 ring: per slot, sa = (hi + colleague offset, lo.x), sb = (lo.y, lo.z,
+// f.x, f.y), sc = f.z -- 36 bytes a source, read by phase 2 -- and the FP16
+// copy of the positions read by phase 1.
 struct TileF32 {
-    float4 sa[kTile];
-    float4 sb[kTile];
-    float sc[kTile];
+    float4 sa[2][kT32];
+    float4 sb[2][kT32];
+    float sc[2][kT32];
+    uint4 sh[2][kT32 / 2];
 };
 struct TileF64 {
     dvec4 sp[kTile];
@@ -427,7 +515,57 @@ struct TileF64 {
 using WsF32 = WarpSmem<TileF32>;
 using WsF64 = WarpSmem<TileF64>;
 
-// KAHAN: compensated per-tile sums and FP64 accumulation across tiles.
+// FP32 record -> hi (lattice integers times 2^-12), lo and force.
+__device__ __forceinline__ void unpack_rec(const float4 &A, const float4 &B, float3 &hi, float3 &lo,
+                                           float3 &f)
+{
+    const unsigned hxy = __float_as_uint(B.z);
+    hi = make_float3((float)(int)(hxy & 0xffffu) * (1.f / 4096.f), (float)(int)(hxy >> 16) * (1.f / 4096.f),
+                     (float)__float_as_int(B.w) * (1.f / 4096.f));
+    lo = make_float3(A.x, A.y, A.z);
+    f = make_float3(A.w, B.x, B.y);
+}
+
+// Stage tile `tile` of the warp's stream (strided: elements tile, tile +
+// ntile, ...) into ring slot `slot`; each lane stages sources lane and
+// lane + 32 and packs their FP16 copy.  Tiles are staged in order, so a lane's
+// element q is its previous one plus 1: sg[h] follows its segment with at most
+// one step (segments are never empty), the binary search only for tile 0.
+__device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg, int slot,
+                                          int tile, int ntile, int total, int lane, int (&sg)[2])
+{
+    const float4 *rec = (const float4 *)a.nrec;
+    float3 hp[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h, q = tile + k * ntile;
+        if (q < total) {
+            if (tile == 0)
+                sg[h] = seg_of(ws, nseg, q);
+            else if (ws.seg_pref[sg[h] + 1] <= q)
+                ++sg[h];
+            int dx, dy, dz;
+            const int j = seg_element(ws, sg[h], q, dx, dy, dz);
+            const float4 A = rec[2 * j], B = rec[2 * j + 1];
+            float3 hi, lo, f;
+            unpack_rec(A, B, hi, lo, f);
+            // exact: integer colleague offsets, hi on a 2^-12 lattice
+            hp[h] = make_float3(hi.x + (float)dx, hi.y + (float)dy, hi.z + (float)dz);
+            ws.tile.sa[slot][k] = make_float4(hp[h].x, hp[h].y, hp[h].z, lo.x);
+            ws.tile.sb[slot][k] = make_float4(lo.y, lo.z, f.x, f.y);
+            ws.tile.sc[slot][k] = f.z;
+        } else {
+            hp[h] = make_float3(kFarHalf, kFarHalf, kFarHalf);
+        }
+    }
+    const __half2 hx = __floats2half2_rn(hp[0].x, hp[1].x);
+    const __half2 hy = __floats2half2_rn(hp[0].y, hp[1].y);
+    const __half2 hz = __floats2half2_rn(hp[0].z, hp[1].z);
+    ws.tile.sh[slot][lane] = make_uint4(*(const unsigned *)&hx, *(const unsigned *)&hy,
+                                        *(const unsigned *)&hz, 0u);
+}
+
+// KAHAN: compensated partial sums, flushed into FP64 totals at every ring step.
 template <bool KAHAN>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)
 {
@@ -435,19 +573,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
     __shared__ WsF32 wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WsF32 &ws = wsm[warp];
-    float4 *sa = ws.tile.sa, *sb = ws.tile.sb;
-    float *sc = ws.tile.sc;
     int c, tb, te;
     if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
         return;  // whole warp: no block-wide barrier follows
-    const float4 *npos = (const float4 *)a.npos, *nlo = (const float4 *)a.nlo;
-    const float4 *nfrc = (const float4 *)a.nfrc;
     const int t = tb + lane;
     const bool active = t < te;
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
     if (active) {
-        th = npos[t];
-        tl = nlo[t];
+        const float4 *rec = (const float4 *)a.nrec;
+        float3 hi, lo, f;
+        unpack_rec(rec[2 * t], rec[2 * t + 1], hi, lo, f);
+        th = make_float4(hi.x, hi.y, hi.z, 0.f);
+        tl = make_float4(lo.x, lo.y, lo.z, 0.f);
     }
     // the warp's target bounding box (hi parts; the margin covers lo)
     const float3 blo = make_float3(warp_min(active ? th.x : 1e30f), warp_min(active ? th.y : 1e30f),
@@ -459,58 +596,85 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
     const int total = ws.seg_pref[nseg];
     // tile t holds the stream elements t, t + ntiles, t + 2 ntiles, ...: each
     // tile samples the whole neighbourhood, so the lanes' in-range counts per
-    // tile are even and phase 2 wastes few iterations
-    const int ntile = (total + kTile - 1) / kTile;
+    // tile are even
+    const int ntile = (total + kT32 - 1) / kT32;
+    const __half2 tx = __float2half2_rn(th.x), ty = __float2half2_rn(th.y),
+                  tz = __float2half2_rn(th.z), lim = __float2half2_rn(kc.rc2_half);
+    // ring: mA = this lane's remaining in-range bits of tile o (slot o & 1),
+    // mB those of tile o + 1 (slot (o + 1) & 1); inactive lanes keep both 0
+    unsigned long long mA = 0ull, mB = 0ull;
+    int sg[2] = {0, 0};
+    for (int tt = 0; tt < 2 && tt < ntile; ++tt)
+        stage_f32(a, ws, nseg, tt, tt, ntile, total, lane, sg);
+    __syncwarp();
+    if (active) {
+        if (ntile > 0)
+            mA = phase1_half(ws.tile.sh[0], tx, ty, tz, lim);
+        if (ntile > 1)
+            mB = phase1_half(ws.tile.sh[1], tx, ty, tz, lim);
+    }
     Tot ux = 0, uy = 0, uz = 0;
-    for (int tile = 0; tile < ntile; ++tile) {
-        const int n = (total - tile + ntile - 1) / ntile;  // elements q < total with q % ntile == tile
+    for (int o = 0; o < ntile; ++o) {
+        typename std::conditional<KAHAN, KSum, float>::type px{}, py{}, pz{};
+        // until every lane has finished tile o; a lane done with it goes on
+        // with tile o + 1, a lane done with both waits
+        if constexpr (KAHAN) {
+            while (__any_sync(0xffffffffu, mA != 0ull)) {
+                if (mA | mB) {
+                    const int p = next_bit(mA, mB);
+                    const int slot = (o + (p >> 6)) & 1, k = half_slot(p & 63);
+                    const float4 s = ws.tile.sa[slot][k], b = ws.tile.sb[slot][k];
+                    // d = (hi diff, exact) + (lo diff)
+                    pair_f32<KAHAN>((th.x - s.x) + (tl.x - s.w), (th.y - s.y) + (tl.y - b.x),
+                                    (th.z - s.z) + (tl.z - b.y),
+                                    make_float3(b.z, b.w, ws.tile.sc[slot][k]), kc, px, py, pz);
+                }
+            }
+        } else {
+            // two pairs per iteration: independent chains for the scheduler;
+            // a lane with one pair left evaluates a far dummy as its second
+            while (__any_sync(0xffffffffu, mA != 0ull)) {
+                float3 d[2], fv[2];
 #pragma unroll
-        for (int i = 0; i < kTile / 32; ++i) {
-            const int k = lane + 32 * i, q = tile + k * ntile;
-            if (k < n) {
-                int dx, dy, dz;
-                const int j = locate(ws, nseg, q, dx, dy, dz);
-                const float4 p = npos[j], l = nlo[j], f = nfrc[j];
-                // exact: integer colleague offsets, hi on a 2^-12 lattice
-                sa[k] = make_float4(p.x + (float)dx, p.y + (float)dy, p.z + (float)dz, l.x);
-                sb[k] = make_float4(l.y, l.z, f.x, f.y);
-                sc[k] = f.z;
-            } else {
-                sa[k] = make_float4(kFar, kFar, kFar, 0.f);
+                for (int u = 0; u < 2; ++u) {
+                    d[u] = make_float3(1e3f, 0.f, 0.f);
+                    fv[u] = make_float3(0.f, 0.f, 0.f);
+                    if (mA | mB) {
+                        const int p = next_bit(mA, mB);
+                        const int slot = (o + (p >> 6)) & 1, k = half_slot(p & 63);
+                        const float4 s = ws.tile.sa[slot][k], b = ws.tile.sb[slot][k];
+                        // d = (hi diff, exact) + (lo diff)
+                        d[u] = make_float3((th.x - s.x) + (tl.x - s.w), (th.y - s.y) + (tl.y - b.x),
+                                           (th.z - s.z) + (tl.z - b.y));
+                        fv[u] = make_float3(b.z, b.w, ws.tile.sc[slot][k]);
+                    }
+                }
+                const float3 c0 = pair_f32_bulk(d[0].x, d[0].y, d[0].z, fv[0], kc);
+                const float3 c1 = pair_f32_bulk(d[1].x, d[1].y, d[1].z, fv[1], kc);
+                px += c0.x + c1.x;
+                py += c0.y + c1.y;
+                pz += c0.z + c1.z;
             }
         }
-        __syncwarp();
-        if (active) {
-            unsigned long long m0, m1;
-            build_masks(
-                kc.rc2_loose,
-                [&](int k) {
-                    const float4 s = sa[k];
-                    float hx = th.x - s.x, hy = th.y - s.y, hz = th.z - s.z;
-                    return fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-                },
-                m0, m1);
-            // per-tile partial sums
-            typename std::conditional<KAHAN, KSum, float>::type px{}, py{}, pz{};
-            while (m0 | m1) {
-                const int k = next_bit(m0, m1);
-                const float4 s = sa[k], b = sb[k];
-                // d = (hi diff, exact) + (lo diff)
-                pair_f32<KAHAN>((th.x - s.x) + (tl.x - s.w), (th.y - s.y) + (tl.y - b.x),
-                                (th.z - s.z) + (tl.z - b.y), make_float3(b.z, b.w, sc[k]), kc,
-                                px, py, pz);
-            }
-            if constexpr (KAHAN) {
-                ux += (double)px.s + (double)px.c * -1.0;
-                uy += (double)py.s + (double)py.c * -1.0;
-                uz += (double)pz.s + (double)pz.c * -1.0;
-            } else {
-                ux += px;
-                uy += py;
-                uz += pz;
-            }
+        if constexpr (KAHAN) {
+            ux += (double)px.s + (double)px.c * -1.0;
+            uy += (double)py.s + (double)py.c * -1.0;
+            uz += (double)pz.s + (double)pz.c * -1.0;
+        } else {
+            ux += px;
+            uy += py;
+            uz += pz;
         }
-        __syncwarp();
+        // slot o & 1 is free: stage tile o + 2 there
+        mA = mB;
+        mB = 0ull;
+        if (o + 2 < ntile) {
+            __syncwarp();
+            stage_f32(a, ws, nseg, o & 1, o + 2, ntile, total, lane, sg);
+            __syncwarp();
+            if (active)
+                mB = phase1_half(ws.tile.sh[o & 1], tx, ty, tz, lim);
+        }
     }
     if (active) {
         const int i = a.permn[t];
@@ -643,8 +807,8 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         return e;
     P2PArgs a;
     a.npos = p->npos;
-    a.nlo = p->nlo;
     a.nfrc = p->nfrc;
+    a.nrec = p->nrec;
     a.startn = p->startn;
     a.item_off = p->item_off;
     a.permn = p->permn;
@@ -665,7 +829,9 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         F32Const kc;
         const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
         kc.rc2 = (float)(rcc * rcc);
-        kc.rc2_loose = (float)(rcc * rcc * (1.0 + 2e-3));
+        // phase 1 runs in FP16: coordinates within 3 cells carry <= 2^-10 each,
+        // so |r^2 error| < 0.03 rc^2 + 0.005 below the cutoff (K <= 2)
+        kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
         kc.rcm = (float)(rcc + 1e-3);  // sub-cell culling reach: |lo| <= 2^-13 fits the margin
         kc.xi = (float)xic;
         const double c = -xic * xic * 1.4426950408889634;  // -xi^2 log2(e), cell units

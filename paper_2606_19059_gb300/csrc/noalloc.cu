@@ -147,6 +147,7 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
     pl.npos = base + kOffNpos;
     pl.nlo = base + kOffNlo;
     pl.nfrc = base + kOffNfrc;
+    pl.nrec = base + kOffNpos;  // FP32 records (32 bytes a point) take the position area
     pl.tdat = base + kOffTdat;
     pl.tfrc = base + kOffTfrc;
     pl.un = base + kOffUn;

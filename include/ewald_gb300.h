@@ -62,7 +62,7 @@ typedef enum {
     EWALD_F32_BULK = 1
 } ewald_dtype;
 
-/* Method parameters (Sec. 2.3).  ewald_get_params() fills every field.  As an
+/* Method parameters (Sec. 2.4).  ewald_get_params() fills every field.  As an
  * override for ewald_plan_ex(), a field <= 0 means "choose it": the library
  * then picks it from the error estimate eq. (ese) as described at ewald_plan. */
 typedef struct {
@@ -95,7 +95,7 @@ typedef struct {
 const char *ewald_status_string(ewald_status s);
 
 /* Choose the method parameters for N points in a box of side L at relative
- * tolerance tol, without touching any GPU.  Rule (Sec. 2.3): each term of the
+ * tolerance tol, without touching any GPU.  Rule (Sec. 2.4): each term of the
  * eq. (ese) estimate is held below tol/10 (the paper uses tol/3 for an rms
  * error; the max-norm error runs about 3x the rms one).  With M and P given:
  * xi is the largest value with E^F <= tol/10, then rc the smallest with
@@ -186,6 +186,68 @@ ewald_status ewald_sync_status(ewald_plan_t plan, void *stream);
 /* Number of kernel launches (this library's own kernels, cuFFT excluded) that
  * one ewald_apply() issues with this plan, and the number of cuFFT executions. */
 ewald_status ewald_launch_counts(ewald_plan_t plan, int32_t *kernels, int32_t *ffts);
+
+/* ---- Measured parameter choice and batches of boxes ----------------------
+ * Sec. 2.4 leaves one free parameter once every term of eq. (ese) is held
+ * below the tolerance, and picks it by minimising the modelled run time
+ * T(rc) (with the GPU performance models of Sec. 5 as the better T).  Here
+ * the free choice is the grid size M -- xi, rc and n_c then follow from the
+ * planner's error bounds -- together with the P2G/G2P grid tile T, and T(M)
+ * is measured on the device.  Every candidate meets the same error bound. */
+enum { EWALD_TUNE_MODEL = 0, EWALD_TUNE_MEASURE = 1 };
+
+/* The candidates the autotuner times for (N, L, tol, dtype), host only (no
+ * GPU): first the planner's cost-model choice (= ewald_choose_params with no
+ * override), then cuFFT-friendly multiples of 8 for M between 0.6x and 1.7x
+ * that choice (at most 6 of them, spread over the range) with grid tile T = 8,
+ * and the model's M with the other tile (T = 4), each only where the kernels
+ * accept it; P fixed at the planner's.  At most `cap` entries go to `cands`
+ * (host array), their number to *n.
+ * Errors: EINVAL for NULL pointers, cap < 1 or bad N, L, tol. */
+ewald_status ewald_autotune_candidates(int64_t N, double L, double tol, ewald_dtype dtype,
+                                       int32_t cap, ewald_params *cands, int32_t *n);
+
+/* Choose the parameters for (N, L, tol, dtype).  EWALD_TUNE_MODEL: the first
+ * candidate, nothing timed.  EWALD_TUNE_MEASURE: every candidate is planned
+ * on the current device and timed (uniform random points of this N, one
+ * warm-up apply, median of three event-timed applies); the fastest is
+ * returned in *out and its median time (ms) in *ms (if ms != NULL; -1 for
+ * MODEL).  Measured results are cached per (N, L, tol, dtype) for the life of
+ * the process (ewald_autotune_clear empties the cache).  Candidates that do
+ * not fit in memory are skipped.  Synchronises the device; not for use
+ * inside stream capture.  Errors: EINVAL, ENOMEM (no candidate fits), ECUDA,
+ * ECUFFT. */
+ewald_status ewald_autotune(int64_t N, double L, double tol, ewald_dtype dtype, int32_t mode,
+                            ewald_params *out, double *ms);
+void ewald_autotune_clear(void);
+
+/* A batch of independent boxes (own N, L, tol each; one dtype) applied with
+ * one call.  Each box gets a plan with the autotuned parameters of
+ * ewald_autotune(tune_mode), looked up at the half-octave representative
+ * of its N (round(2^(round(2 log2 N) / 2))), so boxes of similar size share a
+ * tuning.  The batch owns device buffers for every box's x, f (read) and u
+ * (written), N x 3 FP64 each, reached through ewald_batch_buffers(); the
+ * caller fills x and f there (any stream, ordered before the apply).
+ * `nstreams` (1..64) streams carry the boxes concurrently.  Errors: EINVAL
+ * for nbox < 1, NULL arrays, a bad N/L/tol entry, nstreams out of range;
+ * then as ewald_plan_ex / ewald_autotune.  Nothing is left allocated on
+ * failure. */
+typedef struct ewald_batch_s *ewald_batch_t;
+ewald_status ewald_batch_create(int32_t nbox, const int64_t *N, const double *L, const double *tol,
+                                ewald_dtype dtype, int32_t tune_mode, int32_t nstreams,
+                                ewald_batch_t *out);
+/* Device pointers of box `box`'s x, f, u buffers (any of the outputs may be NULL). */
+ewald_status ewald_batch_buffers(ewald_batch_t b, int32_t box, double **x, double **f, double **u);
+ewald_status ewald_batch_get_params(ewald_batch_t b, int32_t box, ewald_params *out);
+/* The plan of one box (owned by the batch; valid until ewald_batch_destroy). */
+ewald_status ewald_batch_plan(ewald_batch_t b, int32_t box, ewald_plan_t *out);
+/* Apply every box: u = apply(x, f) per box, as ewald_apply would give with
+ * the box's plan.  The first call records all the boxes' applies into one
+ * CUDA graph (boxes by decreasing N dealt round-robin over the streams);
+ * every call launches that graph on `stream`, asynchronously.  Calls on one
+ * batch must not overlap in time. */
+ewald_status ewald_batch_apply(ewald_batch_t b, void *stream);
+void ewald_batch_destroy(ewald_batch_t b);
 
 /* Host-only helpers, usable without a GPU (tests, tooling).
  * ewald_window_eval: the plan-time piecewise-polynomial fit of the Kaiser-

@@ -92,6 +92,20 @@ _SIGS = [
                                          ctypes.POINTER(ctypes.c_double)]),
     ("ewald_window_hat", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _P, _P]),
     ("ewald_near_field_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ewald_params), _P, _P, _P, _P]),
+    ("ewald_autotune_candidates", ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                 ctypes.c_int32, ctypes.POINTER(ewald_params),
+                                                 ctypes.POINTER(ctypes.c_int32)]),
+    ("ewald_autotune", ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int32,
+                                      ctypes.POINTER(ewald_params), ctypes.POINTER(ctypes.c_double)]),
+    ("ewald_autotune_clear", None, []),
+    ("ewald_batch_create", ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(_P)]),
+    ("ewald_batch_buffers", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                           ctypes.POINTER(_P)]),
+    ("ewald_batch_get_params", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ewald_params)]),
+    ("ewald_batch_plan", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    ("ewald_batch_apply", ctypes.c_int, [_P, _P]),
+    ("ewald_batch_destroy", None, [_P]),
 ]
 EXPORTED = [name for name, _, _ in _SIGS]
 
@@ -240,6 +254,104 @@ def ewald_near_field_noalloc(N: int, params: ewald_params, x_ptr, f_ptr, u_ptr, 
     for callers that cannot allocate device memory themselves."""
     _check(load().ewald_near_field_noalloc(int(N), ctypes.byref(params), x_ptr, f_ptr, u_ptr, stream),
            "ewald_near_field_noalloc")
+
+
+EWALD_TUNE_MODEL, EWALD_TUNE_MEASURE = 0, 1
+
+
+def ewald_autotune_candidates(N: int, L: float, tol: float, dtype: int = EWALD_F32_BULK, cap: int = 32):
+    arr = (ewald_params * int(cap))()
+    n = ctypes.c_int32(0)
+    _check(load().ewald_autotune_candidates(int(N), float(L), float(tol), int(dtype), int(cap), arr,
+                                            ctypes.byref(n)), "ewald_autotune_candidates")
+    return [arr[i] for i in range(n.value)]
+
+
+def ewald_autotune(N: int, L: float, tol: float, dtype: int = EWALD_F32_BULK, mode: int = EWALD_TUNE_MEASURE):
+    out = ewald_params()
+    ms = ctypes.c_double(0.0)
+    _check(load().ewald_autotune(int(N), float(L), float(tol), int(dtype), int(mode), ctypes.byref(out),
+                                 ctypes.byref(ms)), "ewald_autotune")
+    return out, ms.value
+
+
+def ewald_autotune_clear():
+    load().ewald_autotune_clear()
+
+
+class Batch:
+    """Owner of one ewald_batch_t: many independent boxes applied with one
+    graph launch.  Per box, x/f/u are views (torch, CUDA, float64, N x 3) of
+    the batch's own device buffers (marshalling only)."""
+
+    def __init__(self, N, L, tol, dtype: int = EWALD_F32_BULK, tune: int = EWALD_TUNE_MEASURE, nstreams: int = 16):
+        import numpy as np
+
+        self.N = np.ascontiguousarray(N, dtype=np.int64)
+        Ls = np.ascontiguousarray(np.broadcast_to(np.asarray(L, dtype=np.float64), self.N.shape))
+        tols = np.ascontiguousarray(np.broadcast_to(np.asarray(tol, dtype=np.float64), self.N.shape))
+        h = _P()
+        _check(load().ewald_batch_create(len(self.N), self.N.ctypes.data, Ls.ctypes.data, tols.ctypes.data,
+                                         int(dtype), int(tune), int(nstreams), ctypes.byref(h)),
+               "ewald_batch_create")
+        self.handle = h.value
+        self._views = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ewald_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.N)
+
+    def params(self, box: int) -> ewald_params:
+        out = ewald_params()
+        _check(load().ewald_batch_get_params(self.handle, int(box), ctypes.byref(out)), "ewald_batch_get_params")
+        return out
+
+    def buffers(self, box: int):
+        """(x, f, u) torch views of box `box`'s device buffers."""
+        import torch
+
+        if self._views is None:
+            self._views = {}
+        if box not in self._views:
+            px, pf, pu = _P(), _P(), _P()
+            _check(load().ewald_batch_buffers(self.handle, int(box), ctypes.byref(px), ctypes.byref(pf),
+                                              ctypes.byref(pu)), "ewald_batch_buffers")
+            n = int(self.N[box])
+            self._views[box] = tuple(_device_view(p.value, (n, 3)) for p in (px, pf, pu))
+        return self._views[box]
+
+    def apply(self, stream=None):
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(load().ewald_batch_apply(self.handle, s.cuda_stream), "ewald_batch_apply")
+
+
+def _device_view(ptr: int, shape):
+    """A torch float64 CUDA tensor over memory the library owns (no copy)."""
+    import torch
+
+    n = 1
+    for d in shape:
+        n *= d
+
+    class _Arr:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+
+    t = torch.as_tensor(_Arr(), device="cuda")
+    assert t.data_ptr() == ptr and t.numel() == n
+    return t
 
 
 class Plan:

@@ -57,3 +57,23 @@ WORKLOADS = {
     "uniform_1e5_tol1e-6_M128_P12": ("uniform", 100_000, 1.0, 1e-6, 128, 12, 1002),
     "clustered_2e6_tol1e-7_M256_P14": ("clustered", 2_000_000, 1.0, 1e-7, 256, 14, 1003),
 }
+
+
+# Many independent boxes: N = round(10^U(log10 n_lo, log10 n_hi)) per box,
+# tol drawn uniformly from `tols`, uniform points in the unit box and
+# zero-mean forces.  Box b's own points come from seed (seed, b).
+BATCH_TOLS = (1e-4, 1e-6, 1e-8)
+
+
+def batch_boxes(nbox: int, seed: int, n_lo: float = 1e3, n_hi: float = 1e5, tols=BATCH_TOLS):
+    """Sizes and tolerances of `nbox` boxes: (N array int64, tol array)."""
+    rng = np.random.default_rng(seed)
+    N = np.rint(10.0 ** rng.uniform(np.log10(n_lo), np.log10(n_hi), nbox)).astype(np.int64)
+    tol = np.asarray(tols, dtype=np.float64)[rng.integers(0, len(tols), nbox)]
+    return N, tol
+
+
+def batch_box(seed: int, b: int, n: int, L: float = 1.0):
+    """(x, f) of box b of a batch drawn with `seed`: uniform points, forces."""
+    rng = np.random.default_rng([seed, b])
+    return uniform(rng, n, L), forces(rng, n)

@@ -249,6 +249,70 @@ ewald_status ewald_batch_plan(ewald_batch_t b, int32_t box, ewald_plan_t *out);
 ewald_status ewald_batch_apply(ewald_batch_t b, void *stream);
 void ewald_batch_destroy(ewald_batch_t b);
 
+/* ---- Serving: a continuous-batching request loop -------------------------
+ * No counterpart in the paper (it applies one suspension at a time).  A
+ * request is one suspension that issues `napplies` successive applies, as
+ * an iterative solve would: its positions are binned once and stay on the
+ * device with the cell lists and grid order for all of them; apply t >= 1
+ * uses f_t = f_{t-1} + perturb * n_t re-centred to zero mean, n_t ~ N(0, 1)
+ * per component from Philox4x32-10 (Salmon et al., SC 2011) with counter
+ * (i mod 2^32, i div 2^32, t, 0) for point i and key (seed mod 2^32,
+ * seed div 2^32), u1, u2 from outputs 0, 1 and n_z from outputs 2, 3 as
+ * (x + 1) / 2^32, Box-Muller n_x, n_y = sqrt(-2 ln u1) (cos, sin)(2 pi u2),
+ * n_z = sqrt(-2 ln u3) cos(2 pi u4).  Only the last apply's velocities are
+ * returned.  A scheduler thread admits queued requests first come first
+ * served while the summed device footprint of the running ones (planner
+ * estimate plus request buffers) stays within the budget and one of
+ * `max_active` slots is free; each runs on its own stream, so requests
+ * overlap on the GPU, and finished ones free their room at once. */
+typedef struct ewald_server_s *ewald_server_t;
+
+typedef struct {
+    int64_t N;             /* points */
+    double L, tol;         /* box side, tolerance (as ewald_plan) */
+    int32_t dtype;         /* ewald_dtype */
+    int32_t napplies;      /* >= 1 */
+    double perturb;        /* >= 0: force perturbation scale between applies */
+    uint64_t seed;         /* Philox key of this request */
+    const double *x_host;  /* HOST N x 3 positions; read until the request starts */
+    const double *f_host;  /* HOST N x 3 forces of the first apply; read until it starts */
+    double *u_host;        /* HOST N x 3: the last apply's u, written when it completes */
+} ewald_request;
+
+typedef struct {
+    int64_t submitted, completed, failed, cancelled, queued, active;
+    int64_t peak_footprint_bytes;  /* largest summed footprint of running requests */
+    double particle_applies;       /* sum over completed requests of N * napplies */
+    double p50_ms, p99_ms, mean_ms; /* arrival (submit) to completion, completed requests */
+    double throughput;             /* particle_applies / (last completion - first arrival), per s */
+} ewald_server_summary;
+
+enum { EWALD_REQ_QUEUED = 0, EWALD_REQ_RUNNING = 1, EWALD_REQ_DONE = 2, EWALD_REQ_FAILED = 3,
+       EWALD_REQ_CANCELLED = 4 };
+
+/* Create a server on the current device.  hbm_budget_bytes > 0;
+ * 1 <= max_active <= 256; start_paused != 0 admits nothing until
+ * ewald_server_resume().  Errors: EINVAL, ENOMEM, ECUDA. */
+ewald_status ewald_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t start_paused,
+                                 ewald_server_t *out);
+/* Queue a request (copied; the host arrays it points to are not).  Returns at
+ * once with a ticket.  Errors: EINVAL (NULL or bad fields, as ewald_plan for
+ * N, L, tol), ENOMEM when the request alone exceeds the budget (never
+ * admissible; nothing is queued). */
+ewald_status ewald_server_submit(ewald_server_t s, const ewald_request *r, int64_t *ticket);
+/* State (EWALD_REQ_*) and arrival-to-completion latency (ms; -1 until done).
+ * Returns the request's failure status for a failed request. */
+ewald_status ewald_server_poll(ewald_server_t s, int64_t ticket, int32_t *state, double *latency_ms);
+/* Wait up to timeout_s seconds for the request to finish: EWALD_ETIMEOUT if it
+ * has not (the request goes on), its failure status if it failed. */
+ewald_status ewald_server_wait(ewald_server_t s, int64_t ticket, double timeout_s);
+/* Cancel a request that is still queued (EINVAL once it has started). */
+ewald_status ewald_server_cancel(ewald_server_t s, int64_t ticket);
+ewald_status ewald_server_resume(ewald_server_t s);
+ewald_status ewald_server_stats(ewald_server_t s, ewald_server_summary *out);
+/* Drop the queued requests, let the running ones finish, release everything. */
+void ewald_server_destroy(ewald_server_t s);
+
 /* Host-only helpers, usable without a GPU (tests, tooling).
  * ewald_window_eval: the plan-time piecewise-polynomial fit of the Kaiser-
  *   Bessel window w_0 for support P and polynomial degree nu (Sec. 2.2 and

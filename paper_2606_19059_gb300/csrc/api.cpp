@@ -6,6 +6,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -60,34 +62,81 @@ struct DeviceGuard {
     }
 };
 
+// Plan workspaces come from one stream-ordered memory pool per device (kept
+// reserved: release threshold at its maximum), allocated and freed on the
+// plan's own stream: destroying a plan then never waits for the rest of the
+// device, as cudaFree would -- a server tearing down one request's plan leaves
+// the others running.  Without pool support, plain cudaMalloc/cudaFree.
+cudaMemPool_t plan_pool(int dev)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    static bool tried[64] = {};
+    if (dev < 0 || dev >= 64)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried[dev]) {
+        tried[dev] = true;
+        int ok = 0;
+        if (cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess && ok) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t pool = nullptr;
+            if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+                uint64_t thr = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+                pools[dev] = pool;
+            }
+        }
+        cudaGetLastError();
+    }
+    return pools[dev];
+}
+
 template <typename T>
 cudaError_t dalloc(ewald_plan_s *p, T **ptr, size_t bytes)
 {
     if (bytes == 0)
         bytes = 16;
-    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    cudaError_t e;
+    if (p->pooled)
+        e = cudaMallocFromPoolAsync((void **)ptr, bytes, plan_pool(p->device), p->s2);
+    else
+        e = cudaMalloc((void **)ptr, bytes);
     if (e == cudaSuccess)
         p->footprint += (int64_t)bytes;
     return e;
+}
+
+void dfree(ewald_plan_s *p, void *b)
+{
+    if (!b)
+        return;
+    if (p->pooled)
+        cudaFreeAsync(b, p->s2);
+    else
+        cudaFree(b);
 }
 
 void free_plan(ewald_plan_s *p)
 {
     if (!p)
         return;
-    void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
-                    p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec,
-                    p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
-                    p->err, p->hx, p->hf, p->hu};
-    for (void *b : bufs)
-        if (b)
-            cudaFree(b);
-    if (p->own_grid_g2p && p->grid_g2p)
-        cudaFree(p->grid_g2p);
     if (p->have_fwd)
         cufftDestroy(p->fwd);
     if (p->have_inv)
         cufftDestroy(p->inv);
+    void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
+                    p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec,
+                    p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
+                    p->err, p->hx, p->hf, p->hu, p->fftwork};
+    for (void *b : bufs)
+        dfree(p, b);
+    if (p->own_grid_g2p && p->grid_g2p)
+        dfree(p, p->grid_g2p);
     if (p->s2)
         cudaStreamDestroy(p->s2);
     if (p->ev_fork)
@@ -127,6 +176,10 @@ ewald_status make_plan(ewald_plan_s *p)
     double werr = 0;
     EW_ST(fit_window(g.P, q.poly_deg, &p->wpoly, &werr));
 
+    // the plan's own stream first: workspaces are allocated on it
+    EW_CUDA(cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking));
+    p->pooled = plan_pool(p->device) != nullptr;
+
     const int64_t N = p->N;
     const size_t r4 = p->near64 ? 32 : 16, rs = p->near64 ? 8 : 4, fs = p->fft64 ? 8 : 4;
     EW_CUDA(dalloc(p, &p->keyn, 4 * N));
@@ -164,8 +217,9 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_CUDA(dalloc(p, &p->tab, fs * (size_t)g.M));
     EW_CUDA(dalloc(p, &p->wcoef_dev, rs * p->wpoly.coef.size()));
     EW_CUDA(dalloc(p, &p->err, sizeof(int)));
-    EW_CUDA(cudaMemset(p->err, 0, sizeof(int)));
-    EW_CUDA(cudaMemset(p->items, 0, 4 * ((size_t)g.ncells + 1)));
+    EW_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->s2));
+    EW_CUDA(cudaMemsetAsync(p->items, 0, 4 * ((size_t)g.ncells + 1), p->s2));
+    EW_CUDA(cudaStreamSynchronize(p->s2));  // workspaces ready for any stream
 
     // window polynomial coefficients in the kernels' precision
     if (p->near64) {
@@ -197,19 +251,23 @@ ewald_status make_plan(ewald_plan_s *p)
     // cuFFT: 3 batched real <-> half-complex transforms of M^3
     int n3[3] = {g.M, g.M, g.M};
     int inembed_r[3] = {g.M, g.M, g.M}, inembed_c[3] = {g.M, g.M, g.Mh};
-    size_t ws = 0;
+    // (one work area of our own for both: they never run at the same time)
+    size_t wsf = 0, wsi = 0;
     EW_FFT(cufftCreate(&p->fwd));
     p->have_fwd = true;
+    EW_FFT(cufftSetAutoAllocation(p->fwd, 0));
     EW_FFT(cufftMakePlanMany(p->fwd, 3, n3, inembed_r, 1, (int)g.nreal, inembed_c, 1,
-                             (int)g.ncplx, p->fft64 ? CUFFT_D2Z : CUFFT_R2C, 3, &ws));
-    p->footprint += (int64_t)ws;
+                             (int)g.ncplx, p->fft64 ? CUFFT_D2Z : CUFFT_R2C, 3, &wsf));
     EW_FFT(cufftCreate(&p->inv));
     p->have_inv = true;
+    EW_FFT(cufftSetAutoAllocation(p->inv, 0));
     EW_FFT(cufftMakePlanMany(p->inv, 3, n3, inembed_c, 1, (int)g.ncplx, inembed_r, 1,
-                             (int)g.nreal, p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3, &ws));
-    p->footprint += (int64_t)ws;
+                             (int)g.nreal, p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3, &wsi));
+    EW_CUDA(dalloc(p, &p->fftwork, std::max(wsf, wsi)));
+    EW_CUDA(cudaStreamSynchronize(p->s2));
+    EW_FFT(cufftSetWorkArea(p->fwd, p->fftwork));
+    EW_FFT(cufftSetWorkArea(p->inv, p->fftwork));
 
-    EW_CUDA(cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking));
     EW_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     EW_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     for (auto &e : p->ev)
@@ -442,6 +500,7 @@ ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const dou
         EW_CUDA(dalloc(plan, &plan->hx, bytes));
         EW_CUDA(dalloc(plan, &plan->hf, bytes));
         EW_CUDA(dalloc(plan, &plan->hu, bytes));
+        EW_CUDA(cudaStreamSynchronize(plan->s2));  // pool allocations ready for `s`
     }
     EW_CUDA(cudaMemcpyAsync(plan->hx, x_host, bytes, cudaMemcpyHostToDevice, s));
     EW_CUDA(cudaMemcpyAsync(plan->hf, f_host, bytes, cudaMemcpyHostToDevice, s));

@@ -82,6 +82,8 @@ struct ewald_plan_s {
 
     cufftHandle fwd = 0, inv = 0;
     bool have_fwd = false, have_inv = false;
+    void *fftwork = nullptr;                      // shared cuFFT work area (both plans)
+    bool pooled = false;                          // workspaces from the stream-ordered pool
     cudaStream_t s2 = nullptr;                    // second stream: P2P alongside the far field
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev[ewg::kNumEvents] = {};
@@ -124,6 +126,10 @@ cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStre
 cudaError_t load_p2p_constants();
 cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s);
 cudaError_t launch_copy_out(const void *src, bool src_f64, double *dst, int64_t n, cudaStream_t s);
+// Served requests: f <- f + a n (Philox4x32-10 normals for (point, step,
+// seed)), then f <- f - mean(f); `sums` is 3 doubles of device scratch.
+cudaError_t launch_perturb_forces(double *f, int64_t N, double a, uint32_t step, uint64_t seed,
+                                  double *sums, cudaStream_t s);
 cudaError_t launch_grid_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t n,
                                 cudaStream_t s);
 

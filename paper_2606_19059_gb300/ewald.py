@@ -106,6 +106,15 @@ _SIGS = [
     ("ewald_batch_plan", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     ("ewald_batch_apply", ctypes.c_int, [_P, _P]),
     ("ewald_batch_destroy", None, [_P]),
+    ("ewald_server_create", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
+    ("ewald_server_submit", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    ("ewald_server_poll", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    ("ewald_server_wait", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
+    ("ewald_server_cancel", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("ewald_server_resume", ctypes.c_int, [_P]),
+    ("ewald_server_stats", ctypes.c_int, [_P, _P]),
+    ("ewald_server_destroy", None, [_P]),
 ]
 EXPORTED = [name for name, _, _ in _SIGS]
 
@@ -352,6 +361,93 @@ def _device_view(ptr: int, shape):
     t = torch.as_tensor(_Arr(), device="cuda")
     assert t.data_ptr() == ptr and t.numel() == n
     return t
+
+
+class ewald_request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("L", ctypes.c_double), ("tol", ctypes.c_double),
+                ("dtype", ctypes.c_int32), ("napplies", ctypes.c_int32), ("perturb", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("x_host", _P), ("f_host", _P), ("u_host", _P)]
+
+
+class ewald_server_summary(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("queued", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("peak_footprint_bytes", ctypes.c_int64), ("particle_applies", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("throughput", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+EWALD_REQ_QUEUED, EWALD_REQ_RUNNING, EWALD_REQ_DONE, EWALD_REQ_FAILED, EWALD_REQ_CANCELLED = range(5)
+
+
+class Server:
+    """Owner of one ewald_server_t (marshalling only).  submit() takes host
+    numpy arrays and returns a ticket; the arrays are kept alive here until
+    the request is finished and result(ticket) hands back u."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, start_paused: bool = False):
+        h = _P()
+        _check(load().ewald_server_create(int(hbm_budget_bytes), int(max_active), int(bool(start_paused)),
+                                          ctypes.byref(h)), "ewald_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, x, f, tol: float, L: float = 1.0, dtype: int = EWALD_F32_BULK, napplies: int = 20,
+               perturb: float = 0.1, seed: int = 0) -> int:
+        import numpy as np
+
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if x.ndim != 2 or x.shape[1] != 3 or f.shape != x.shape:
+            raise ValueError("x and f must be N x 3")
+        u = np.empty_like(x)
+        r = ewald_request(N=x.shape[0], L=float(L), tol=float(tol), dtype=int(dtype), napplies=int(napplies),
+                          perturb=float(perturb), seed=int(seed), x_host=x.ctypes.data, f_host=f.ctypes.data,
+                          u_host=u.ctypes.data)
+        t = ctypes.c_int64(0)
+        _check(load().ewald_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "ewald_server_submit")
+        self._keep[t.value] = (x, f, u)
+        return t.value
+
+    def poll(self, ticket: int):
+        st = ctypes.c_int32(0)
+        lat = ctypes.c_double(0.0)
+        code = load().ewald_server_poll(self.handle, int(ticket), ctypes.byref(st), ctypes.byref(lat))
+        return st.value, lat.value, code
+
+    def wait(self, ticket: int, timeout_s: float = 3600.0) -> int:
+        """Status code: EWALD_OK, EWALD_ETIMEOUT, or the request's failure."""
+        return load().ewald_server_wait(self.handle, int(ticket), float(timeout_s))
+
+    def result(self, ticket: int):
+        _check(self.wait(ticket), "ewald_server_wait")
+        return self._keep.pop(ticket)[2]
+
+    def cancel(self, ticket: int) -> int:
+        return load().ewald_server_cancel(self.handle, int(ticket))
+
+    def resume(self):
+        _check(load().ewald_server_resume(self.handle), "ewald_server_resume")
+
+    def stats(self) -> dict:
+        out = ewald_server_summary()
+        _check(load().ewald_server_stats(self.handle, ctypes.byref(out)), "ewald_server_stats")
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ewald_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

@@ -1,0 +1,96 @@
+"""Serving on the GPU: each result the same alone and in the mix, the device
+force updates equal to the input generator's, footprint admission, bounded
+waits.
+
+A request binned in the mix may see its points placed within a cell in a
+different order than alone (atomic slot counters), so "the same" means equal
+to rounding in the request's precision.  The last apply's velocities are
+checked against the oracle with the forces the published generator gives on
+the host (workloads.served_forces): this pins the device-side Philox too.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2606_19059_gb300 import ewald, workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+F32, F64 = ewald.EWALD_F32_BULK, ewald.EWALD_F64
+BUDGET = 40 << 30
+
+REQS = [("uniform", 3000, 1e-6, 11), ("clustered", 12000, 1e-4, 12), ("uniform", 20000, 1e-6, 13),
+        ("clustered", 6000, 1e-8, 14), ("uniform", 9000, 1e-4, 15)]
+
+
+def run(server, reqs, napplies=5):
+    tickets = []
+    for kind, n, tol, seed in reqs:
+        x, f = workloads.served_box(kind, n, seed)
+        tickets.append(server.submit(x, f, tol, napplies=napplies, perturb=0.1, seed=seed))
+    return [server.result(t) for t in tickets]
+
+
+def close(u, v, tol):
+    bound = 2e-6 if tol >= 1e-7 else 1e-11   # FP32 bulk above 1e-7, FP64 kernels below
+    return np.abs(u - v).max() / np.abs(v).max() <= bound
+
+
+def test_same_result_alone_and_in_the_mix():
+    alone = []
+    s1 = ewald.Server(BUDGET, max_active=1)
+    for r in REQS:  # one at a time: each waits for the previous one
+        alone += run(s1, [r])
+    s1.close()
+    s4 = ewald.Server(BUDGET, max_active=4)
+    mixed = run(s4, REQS)  # all queued at once, up to four on the GPU together
+    st = s4.stats()
+    s4.close()
+    assert st["completed"] == len(REQS) and st["failed"] == 0
+    for (kind, n, tol, seed), a, m in zip(REQS, alone, mixed):
+        assert close(m, a, tol), (kind, n, tol)
+
+
+def test_served_result_matches_oracle():
+    kind, n, tol, seed = "uniform", 3000, 1e-6, 21
+    s = ewald.Server(BUDGET, max_active=2)
+    x, f0 = workloads.served_box(kind, n, seed)
+    u = s.result(s.submit(x, f0, tol, napplies=4, perturb=0.1, seed=seed))
+    s.close()
+    f_last = workloads.served_forces(f0, 4, 0.1, seed)
+    tg = np.sort(np.random.default_rng(1).choice(n, 64, replace=False))
+    ref = oracle.ewald(x, f_last, 1.0, targets=tg)
+    d = u[tg] - ref
+    assert np.linalg.norm(d) / np.linalg.norm(ref) <= tol
+    assert np.abs(d).max() / np.abs(ref).max() <= tol
+
+
+def test_admission_respects_the_footprint_budget():
+    n = 30000
+    prm = ewald.ewald_choose_params(n, 1.0, 1e-6, F32)
+    one = prm.footprint_bytes + 8 * (9 * n + 3)
+    budget = int(1.5 * one)  # room for one request at a time
+    s = ewald.Server(budget, max_active=4)
+    reqs = [("uniform", n, 1e-6, 30 + i) for i in range(4)]
+    out = run(s, reqs, napplies=3)
+    st = s.stats()
+    s.close()
+    assert st["completed"] == 4 and st["peak_footprint_bytes"] <= budget
+    assert st["peak_footprint_bytes"] == one
+    assert all(np.isfinite(u).all() for u in out)
+
+
+def test_bounded_wait_times_out_then_completes():
+    s = ewald.Server(BUDGET, max_active=2)
+    x, f = workloads.served_box("uniform", 200_000, 41)
+    t = s.submit(x, f, 1e-6, napplies=20, perturb=0.1, seed=41)
+    assert s.wait(t, 1e-4) == ewald.EWALD_ETIMEOUT
+    assert s.wait(t, 600.0) == ewald.EWALD_OK
+    st, lat, code = s.poll(t)
+    assert st == ewald.EWALD_REQ_DONE and lat > 0 and code == ewald.EWALD_OK
+    s.close()

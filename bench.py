@@ -430,6 +430,20 @@ def main():
         }
         for k in ("scale", "fft", "ifft"):
             stage_roof[k]["frac"] = stage_roof[k]["achieved"] / hbm
+        # P2G / G2P: intensity far above the HBM ridge, so the binding fraction
+        # is the FP32 pipe; the algorithmic HBM rate is reported beside it.
+        # P2G per source: 3 P nu Horner FMAs, P^2 + P^3 weight products,
+        # 3 P^3 force FMAs; bytes 24 N (FP32 x, f) + 12 M^3 (grid write).
+        # G2P per target: P^2 + P^3 products and 3 P^3 FMAs; bytes 12 N + 12 N
+        # + 12 M^3.
+        nu = prm["poly_deg"]
+        p2g_flops = N * (6 * P * nu + P * P + 7 * P ** 3)
+        g2p_flops = N * (6 * P * nu + P * P + 7 * P ** 3)
+        for k, fl, by in (("p2g", p2g_flops, 24 * N + 12 * M ** 3), ("g2p", g2p_flops, 24 * N + 12 * M ** 3)):
+            t = st[k + "_ms"] * 1e-3
+            stage_roof[k] = {"bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": fl / t / 1e12 / fp32_peak, "hbm_gbs": by / t / 1e9,
+                             "hbm_frac": by / t / 1e9 / hbm, "flops_per_launch": fl, "bytes_per_launch": by}
         # dominant kernel: the longest stage
         order = sorted(((st[k + "_ms"], k) for k in ("p2p", "p2g", "fft", "scale", "ifft", "g2p", "bin")),
                        reverse=True)

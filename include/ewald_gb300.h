@@ -58,7 +58,9 @@ typedef enum {
     EWALD_F64 = 0,
     /* P2P, P2G and G2P in FP32 with FP32 accumulation; FFT, CNV and the final
      * near + far sum in FP64 when tol < 1e-6, else FP32 FFT/CNV and FP64 sum.
-     * Callers still pass and receive FP64 arrays. */
+     * Below tol 1e-7, where single precision cannot reach: P2P in
+     * double-single FP32 arithmetic (down to tol 1e-9; FP64 below) and P2G/G2P
+     * in FP64.  Callers still pass and receive FP64 arrays. */
     EWALD_F32_BULK = 1
 } ewald_dtype;
 
@@ -82,6 +84,11 @@ typedef struct {
     int32_t near_f64;      /* 1: P2P/P2G/G2P in FP64, 0: FP32 */
     int32_t fft_f64;       /* 1: FFT/CNV in FP64, 0: FP32 */
     int64_t footprint_bytes; /* device memory owned by the plan */
+    int32_t near_ds;       /* 1: P2P in double-single arithmetic (pairs of FP32 values,
+                              ~44 bits) with P2G/G2P in FP64 -- EWALD_F32_BULK at
+                              1e-9 <= tol < 1e-7; 0 otherwise.  Read-only (not an
+                              override). */
+    int32_t reserved_;     /* zero */
 } ewald_params;
 
 /* Per-stage device times (ms) of the most recent apply with timing enabled

@@ -130,7 +130,7 @@ void free_plan(ewald_plan_s *p)
     if (p->have_inv)
         cufftDestroy(p->inv);
     void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
-                    p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec,
+                    p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec, p->nflo,
                     p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
                     p->err, p->hx, p->hf, p->hu, p->fftwork};
     for (void *b : bufs)
@@ -171,6 +171,7 @@ ewald_status make_plan(ewald_plan_s *p)
     g.nreal = (int64_t)g.M * g.M * g.M;
     g.ncplx = (int64_t)g.M * g.M * g.Mh;
     p->near64 = q.near_f64 != 0;
+    p->near_ds = q.near_ds != 0;
     p->fft64 = q.fft_f64 != 0;
 
     double werr = 0;
@@ -194,11 +195,13 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_CUDA(dalloc(p, &p->startt, 4 * ((size_t)g.ntiles + 1)));
     EW_CUDA(dalloc(p, &p->items, 4 * ((size_t)g.ncells + 1)));
     EW_CUDA(dalloc(p, &p->item_off, 4 * ((size_t)g.ncells + 1)));
-    if (p->near64) {
+    if (p->near64 && !p->near_ds) {
         EW_CUDA(dalloc(p, &p->npos, r4 * N));
         EW_CUDA(dalloc(p, &p->nfrc, r4 * N));
     } else {
         EW_CUDA(dalloc(p, &p->nrec, 32 * N));
+        if (p->near_ds)
+            EW_CUDA(dalloc(p, &p->nflo, 16 * N));
     }
     EW_CUDA(dalloc(p, &p->tdat, r4 * N));
     EW_CUDA(dalloc(p, &p->tfrc, r4 * N));

@@ -68,6 +68,8 @@ struct ewald_plan_s {
     void *npos = nullptr, *nfrc = nullptr;        // near-sorted positions (cell-local) / forces
     void *nlo = nullptr;                          // (unused since the FP32 records)
     void *nrec = nullptr;                         // FP32: near-sorted 32-byte source records
+    void *nflo = nullptr;                         // double-single: force low parts (float4)
+    bool near_ds = false;                         // P2P in double-single arithmetic
     void *tdat = nullptr, *tfrc = nullptr;        // tile-sorted window data / forces
     void *un = nullptr, *uf = nullptr;            // near / far results, user order
     void *grid = nullptr;                         // 3 M^3 real

@@ -23,7 +23,7 @@ struct KeyArgs {
     int nc, M, T, nt, ceilP2;
     int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
     const int32_t *startn, *startt;
-    void *npos, *nfrc, *nrec, *tdat, *tfrc;
+    void *npos, *nfrc, *nrec, *nflo, *tdat, *tfrc;
     int *err;
 };
 
@@ -98,20 +98,24 @@ __global__ void k_bin_scatter(KeyArgs k)
     int pn = k.startn[k.keyn[i]] + k.slotn[i];
     int pt = k.startt[k.keyt[i]] + k.slott[i];
     R4 *tdat = (R4 *)k.tdat, *tfrc = (R4 *)k.tfrc;
-    if constexpr (sizeof(R) == 4) {
+    if (k.nrec) {
         // FP32 near record (32 bytes): cell-local position in cell units split
-        // hi + lo, hi on a 2^-12 lattice stored as integers (exact in FP32,
-        // exact differences), |lo| <= 2^-13, and the force:
-        //   (lo.x, lo.y, lo.z, f.x) (f.y, f.z, hi.x | hi.y << 16, hi.z)
+        // hi + lo, hi on a 2^-20 lattice stored as three 21-bit integers
+        // (exact in FP32 together with an integer colleague offset, so hi
+        // differences are exact), |lo| <= 2^-21 (FP32: 2^-45 absolute), and
+        // the force:
+        //   (lo.x, lo.y, lo.z, f.x) (f.y, f.z, bits 0..31, bits 32..63 of
+        //   hi.x | hi.y << 21 | hi.z << 42)
         float lo[3];
-        int hq[3];
+        uint64_t hq[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double q = b.xw[d] * k.inv_cell - b.c[d];
-            const double X = rint(q * 4096.0);
-            hq[d] = (int)X;  // 0 .. 4096
-            lo[d] = (float)(q - X * (1.0 / 4096.0));
+            const double X = rint(q * 1048576.0);
+            hq[d] = (uint64_t)X;  // 0 .. 2^20
+            lo[d] = (float)(q - X * (1.0 / 1048576.0));
         }
+        const uint64_t packed = hq[0] | (hq[1] << 21) | (hq[2] << 42);
         float fx = 0.f, fy = 0.f, fz = 0.f;  // set_positions: forces come later
         if (k.f) {
             fx = (float)k.f[3 * i];
@@ -120,7 +124,14 @@ __global__ void k_bin_scatter(KeyArgs k)
         }
         float4 *rec = (float4 *)k.nrec + 2 * (int64_t)pn;
         rec[0] = make_float4(lo[0], lo[1], lo[2], fx);
-        rec[1] = make_float4(fy, fz, __int_as_float(hq[0] | (hq[1] << 16)), __int_as_float(hq[2]));
+        rec[1] = make_float4(fy, fz, __uint_as_float((unsigned)packed), __uint_as_float((unsigned)(packed >> 32)));
+        if (k.nflo) {  // double-single P2P: the forces' FP32 rounding errors
+            float4 fl = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k.f)
+                fl = make_float4((float)(k.f[3 * i] - (double)fx), (float)(k.f[3 * i + 1] - (double)fy),
+                                 (float)(k.f[3 * i + 2] - (double)fz), 0.f);
+            ((float4 *)k.nflo)[pn] = fl;
+        }
     } else {
         R4 pos;
         pos.x = (R)(b.xw[0] - b.c[0] * k.cell);
@@ -145,34 +156,40 @@ __global__ void k_bin_scatter(KeyArgs k)
         fv.y = (R)k.f[3 * i + 1];
         fv.z = (R)k.f[3 * i + 2];
         fv.w = (R)0;
-        if constexpr (sizeof(R) == 8)
+        if (!k.nrec)
             ((R4 *)k.nfrc)[pn] = fv;
         tfrc[pt] = fv;
     }
 }
 
-// Forces into both sorted orders: FP64 near forces as 4-vectors, FP32 into
-// the force slots of the near records (floats 3, 4, 5 of each 8).
+// Forces into both sorted orders: FP64 near forces as 4-vectors (nfrc), or
+// into the force slots of the FP32 near records (floats 3, 4, 5 of each 8)
+// with their FP32 rounding errors in nflo for the double-single P2P.
 template <typename R, typename R4>
 __global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__restrict__ permn,
-                                const int32_t *__restrict__ permt, void *near, R4 *tfrc, int64_t N)
+                                const int32_t *__restrict__ permt, dvec4 *nfrc, float *nrec,
+                                float4 *nflo, R4 *tfrc, int64_t N)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N)
         return;
     int in = permn[p], it = permt[p];
-    if constexpr (sizeof(R) == 8) {
-        R4 a;
+    if (nrec) {
+        float *r = nrec + 8 * p;
+        const float fx = (float)f[3 * in], fy = (float)f[3 * in + 1], fz = (float)f[3 * in + 2];
+        r[3] = fx;
+        r[4] = fy;
+        r[5] = fz;
+        if (nflo)
+            nflo[p] = make_float4((float)(f[3 * in] - (double)fx), (float)(f[3 * in + 1] - (double)fy),
+                                  (float)(f[3 * in + 2] - (double)fz), 0.f);
+    } else {
+        dvec4 a;
         a.x = f[3 * in];
         a.y = f[3 * in + 1];
         a.z = f[3 * in + 2];
         a.w = 0.0;
-        ((R4 *)near)[p] = a;
-    } else {
-        float *r = (float *)near + 8 * p;
-        r[3] = (float)f[3 * in];
-        r[4] = (float)f[3 * in + 1];
-        r[5] = (float)f[3 * in + 2];
+        nfrc[p] = a;
     }
     R4 b;
     b.x = (R)f[3 * it];
@@ -295,6 +312,7 @@ KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
     k.npos = p->npos;
     k.nfrc = p->nfrc;
     k.nrec = p->nrec;
+    k.nflo = p->nflo;
     k.tdat = p->tdat;
     k.tfrc = p->tfrc;
     k.err = p->err;
@@ -332,10 +350,11 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
 {
     if (p->near64)
         k_gather_forces<double, dvec4><<<blocks_for(p->N, 256), 256, 0, s>>>(
-            f, p->permn, p->permt, p->nfrc, (dvec4 *)p->tfrc, p->N);
+            f, p->permn, p->permt, (dvec4 *)p->nfrc, (float *)p->nrec, (float4 *)p->nflo,
+            (dvec4 *)p->tfrc, p->N);
     else
         k_gather_forces<float, float4><<<blocks_for(p->N, 256), 256, 0, s>>>(
-            f, p->permn, p->permt, p->nrec, (float4 *)p->tfrc, p->N);
+            f, p->permn, p->permt, nullptr, (float *)p->nrec, nullptr, (float4 *)p->tfrc, p->N);
     return cudaGetLastError();
 }
 

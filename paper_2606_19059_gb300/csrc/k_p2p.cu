@@ -24,7 +24,7 @@
 // every candidate for all lanes would idle most lanes in the expensive branch.
 //
 // FP32 coordinates are cell-local in cell units and split hi + lo, hi on a
-// 2^-12 lattice: colleague offsets are integers, so hi differences are exact
+// 2^-20 lattice: colleague offsets are integers, so hi differences are exact
 // and r = (hi_t - hi_s) + (lo_t - lo_s) keeps close pairs accurate to a few
 // ulp of |r| (a plain FP32 coordinate would carry eps * cell).  FP64 uses
 // cell-local coordinates in length units.
@@ -37,6 +37,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "erf_rational.h"
@@ -55,6 +56,7 @@ constexpr int kTile = 128;  // sources per staged tile = bits of the two masks
 struct P2PArgs {
     const void *npos, *nfrc;  // FP64: cell-local positions, forces (4-vectors)
     const void *nrec;         // FP32: 32-byte records (lo.xyz, f.xyz, hi lattice)
+    const void *nflo;         // double-single: the forces' FP32 rounding errors (float4)
     const int32_t *startn, *item_off, *permn;
     void *un;
     int nc, K, ncells;
@@ -79,6 +81,8 @@ struct F32Const {
 };
 
 __constant__ float c_exp2f32[EXP2_F32_N];
+__constant__ float c_erfcx_ds_hi[ERFCX_DS_N], c_erfcx_ds_lo[ERFCX_DS_SPLIT];
+__constant__ float c_exp_ds_hi[EXP_DS_N], c_exp_ds_lo[6];
 
 // e^{-xi^2 r^2} = 2^y, y = (r2 + r2lo) * (chi + clo) kept as y_hi + y_lo (the
 // product's rounding recovered by an FMA), reduced to 2^f, |f| <= 1/2, by a minimax
@@ -222,44 +226,6 @@ __device__ __forceinline__ float3 pair_f32_bulk(float dx, float dy, float dz, co
     const float sc = r2 == 0.0f ? -k.selfc : 0.0f;
     return make_float3(in ? fmaf(amb, f.x, co * dx) : sc * f.x, in ? fmaf(amb, f.y, co * dy) : sc * f.y,
                        in ? fmaf(amb, f.z, co * dz) : sc * f.z);
-}
-
-// One FP64 in-range candidate (length units) with the paper's erf(x)/x.
-__device__ __forceinline__ void pair_f64(double dx, double dy, double dz, const dvec4 &f,
-                                         double rc2, double xi, double xi2, double c2, double selfc,
-                                         double &ax, double &ay, double &az)
-{
-    double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-    if (r2 > rc2)
-        return;
-    if (r2 == 0.0) {
-        ax = fma(-selfc, f.x, ax);
-        ay = fma(-selfc, f.y, ay);
-        az = fma(-selfc, f.z, az);
-        return;
-    }
-    double rinv = rsqrt(r2);
-    double x = xi * (r2 * rinv);
-    double A;
-    if (x < ERF_RAT_X64) {
-        double z = fma(x, 2.0 / ERF_RAT_X64, -1.0);
-        double P = c_erfp64[ERF_RAT_F64_N - 1], Q = c_erfq64[ERF_RAT_F64_N - 1];
-#pragma unroll
-        for (int q = ERF_RAT_F64_N - 2; q >= 0; --q) {
-            P = fma(P, z, c_erfp64[q]);
-            Q = fma(Q, z, c_erfq64[q]);
-        }
-        A = rinv - xi * (P / Q);           // (1/x - erf(x)/x) xi
-    } else {
-        A = 0.0;                           // erfc(7) ~ 4e-23
-    }
-    double B = c2 * exp(-xi2 * r2);
-    double amb = A - B, apb = A + B;
-    double rf = fma(dx, f.x, fma(dy, f.y, dz * f.z));
-    double co = apb * rf * (rinv * rinv);
-    ax = fma(amb, f.x, fma(co, dx, ax));
-    ay = fma(amb, f.y, fma(co, dy, ay));
-    az = fma(amb, f.z, fma(co, dz, az));
 }
 
 __device__ __forceinline__ int wrap(int i, int n)
@@ -429,28 +395,7 @@ __device__ __forceinline__ int locate(const WS &ws, int nseg, int q, int &dx, in
     return seg_element(ws, seg_of(ws, nseg, q), q, dx, dy, dz);
 }
 
-// Phase 1 over a staged tile: bit k of (m0, m1) set when source k may be in
-// range.  `test(k)` returns the candidate's squared distance estimate.  Slots
-// past the tile's end hold a far-away dummy, so the loop is always complete
-// and fully unrolled (every shift is a constant).
-template <typename Test>
-__device__ __forceinline__ void build_masks(float rc2, Test test, unsigned long long &m0,
-                                            unsigned long long &m1)
-{
-    m0 = 0ull;
-    m1 = 0ull;
-#pragma unroll
-    for (int k = 0; k < 64; ++k)
-        if (test(k) <= rc2)
-            m0 |= 1ull << k;
-#pragma unroll
-    for (int k = 0; k < 64; ++k)
-        if (test(64 + k) <= rc2)
-            m1 |= 1ull << k;
-}
-
-constexpr float kFar = 1.0e9f;  // dummy source position: never within rc
-constexpr float kFarHalf = 64.0f;  // FP16 dummy: r^2 ~ 1e4, finite and never within rc
+constexpr float kFarHalf = 64.0f;  // FP16 dummy source: r^2 ~ 1e4, finite and never within rc
 
 // FP32 kernel: tiles of 64 sources, two staged at once (a ring of two slots),
 // so a lane may run up to one tile ahead of the slowest lane of its warp: the
@@ -508,20 +453,82 @@ struct TileF32 {
     float sc[2][kT32];
     uint4 sh[2][kT32 / 2];
 };
+// FP64 tile of 128 sources: positions (hi + colleague offset, length units)
+// and forces as packed double triples, and the FP16 copy of the positions in
+// cell units for phase 1 (sources k and k + 64 per entry).
 struct TileF64 {
-    dvec4 sp[kTile];
-    dvec4 sf[kTile];
+    double3 sp[kTile];
+    double3 sf[kTile];
+    uint4 sh[kTile / 2];
 };
+// FP16x2 phase 1 over one 128-source tile (FP64 kernel): entry k holds
+// sources k and k + 64; word w of the result holds entries 16 w .. 16 w + 15,
+// bit b < 16 source 16 w + b, bit 16 + b source 64 + 16 w + b (half_slot_128
+// inverts this).  Same coordinates (cell units, |value| <= 3) and threshold as
+// the FP32 kernel.
+__device__ __forceinline__ void phase1_half_128(const uint4 *sh, __half2 tx, __half2 ty, __half2 tz,
+                                                __half2 lim, unsigned long long &m0,
+                                                unsigned long long &m1)
+{
+    unsigned acc[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < kTile / 2; ++k) {
+        const uint4 v = sh[k];
+        const __half2 dx = __hsub2(tx, *(const __half2 *)&v.x);
+        const __half2 dy = __hsub2(ty, *(const __half2 *)&v.y);
+        const __half2 dz = __hsub2(tz, *(const __half2 *)&v.z);
+        const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
+        acc[k >> 4] |= __hle2_mask(r2, lim) & ((1u << (k & 15)) | (1u << (16 + (k & 15))));
+    }
+    m0 = ((unsigned long long)acc[1] << 32) | acc[0];
+    m1 = ((unsigned long long)acc[3] << 32) | acc[2];
+}
+
+__device__ __forceinline__ int half_slot_128(int p)
+{
+    return ((p >> 5) << 4) + (p & 15) + ((p & 16) << 2);
+}
+
+// FP64 pair without branches (two in flight per lane): in range (0 < r2 <=
+// rc2) the kernel term, r2 = 0 the removed far part, else nothing.  The
+// paper's erf(x)/x rational; erfc(x) is taken as 0 past x = 7 (4e-23).
+__device__ __forceinline__ double3 pair_f64_bulk(double dx, double dy, double dz, const double3 &f,
+                                                 double rc2, double xi, double xi2, double c2,
+                                                 double selfc)
+{
+    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const bool in = r2 <= rc2 && r2 > 0.0;
+    const double r2s = in ? r2 : 1.0;
+    const double rinv = rsqrt(r2s);
+    const double x = xi * (r2s * rinv);
+    const double z = fma(fmin(x, ERF_RAT_X64), 2.0 / ERF_RAT_X64, -1.0);
+    double P = c_erfp64[ERF_RAT_F64_N - 1], Q = c_erfq64[ERF_RAT_F64_N - 1];
+#pragma unroll
+    for (int q = ERF_RAT_F64_N - 2; q >= 0; --q) {
+        P = fma(P, z, c_erfp64[q]);
+        Q = fma(Q, z, c_erfq64[q]);
+    }
+    const double A = x < ERF_RAT_X64 ? rinv - xi * (P / Q) : 0.0;  // erfc(x)/r
+    const double B = c2 * exp(-xi2 * r2s);
+    const double amb = A - B, apb = A + B;
+    const double rf = fma(dx, f.x, fma(dy, f.y, dz * f.z));
+    const double co = apb * rf * (rinv * rinv);
+    const double sc = r2 == 0.0 ? -selfc : 0.0;
+    return make_double3(in ? fma(amb, f.x, co * dx) : sc * f.x, in ? fma(amb, f.y, co * dy) : sc * f.y,
+                        in ? fma(amb, f.z, co * dz) : sc * f.z);
+}
+
 using WsF32 = WarpSmem<TileF32>;
 using WsF64 = WarpSmem<TileF64>;
 
-// FP32 record -> hi (lattice integers times 2^-12), lo and force.
+// FP32 record -> hi (21-bit lattice integers times 2^-20), lo and force.
 __device__ __forceinline__ void unpack_rec(const float4 &A, const float4 &B, float3 &hi, float3 &lo,
                                            float3 &f)
 {
-    const unsigned hxy = __float_as_uint(B.z);
-    hi = make_float3((float)(int)(hxy & 0xffffu) * (1.f / 4096.f), (float)(int)(hxy >> 16) * (1.f / 4096.f),
-                     (float)__float_as_int(B.w) * (1.f / 4096.f));
+    const unsigned w0 = __float_as_uint(B.z), w1 = __float_as_uint(B.w);
+    const unsigned qx = w0 & 0x1FFFFFu, qy = (w0 >> 21) | ((w1 & 0x3FFu) << 11), qz = w1 >> 10;
+    hi = make_float3((float)(int)qx * (1.f / 1048576.f), (float)(int)qy * (1.f / 1048576.f),
+                     (float)(int)qz * (1.f / 1048576.f));
     lo = make_float3(A.x, A.y, A.z);
     f = make_float3(A.w, B.x, B.y);
 }
@@ -549,7 +556,7 @@ __device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg,
             const float4 A = rec[2 * j], B = rec[2 * j + 1];
             float3 hi, lo, f;
             unpack_rec(A, B, hi, lo, f);
-            // exact: integer colleague offsets, hi on a 2^-12 lattice
+            // exact: integer colleague offsets, hi on a 2^-20 lattice
             hp[h] = make_float3(hi.x + (float)dx, hi.y + (float)dy, hi.z + (float)dz);
             ws.tile.sa[slot][k] = make_float4(hp[h].x, hp[h].y, hp[h].z, lo.x);
             ws.tile.sb[slot][k] = make_float4(lo.y, lo.z, f.x, f.y);
@@ -685,12 +692,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
     }
 }
 
-__global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
+__global__ void __launch_bounds__(kWarps * 32, 5) k_p2p_f64(P2PArgs a)
 {
     __shared__ WsF64 wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WsF64 &ws = wsm[warp];
-    dvec4 *sp = ws.tile.sp, *sf = ws.tile.sf;
+    double3 *sp = ws.tile.sp, *sf = ws.tile.sf;
+    uint4 *sh = ws.tile.sh;
     int c, tb, te;
     if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
         return;
@@ -702,7 +710,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
         xt = npos[t];
     const double rc2 = a.rc * a.rc, xi = a.xi, xi2 = a.xi * a.xi;
     const double c2 = 2.0 * a.xi / sqrt(3.14159265358979323846), selfc = 2.0 * c2;
-    const float rc2f = (float)(rc2 * (1.0 + 1e-4));
+    const double inv_cell = 1.0 / a.cell, rcc = a.rc * inv_cell;
     const float3 blo = make_float3(warp_min(active ? (float)xt.x : 1e30f),
                                    warp_min(active ? (float)xt.y : 1e30f),
                                    warp_min(active ? (float)xt.z : 1e30f));
@@ -713,47 +721,66 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
                                     (float)(a.rc + 1e-3 * a.cell));
     const int total = ws.seg_pref[nseg];
     const int ntile = (total + kTile - 1) / kTile;  // strided tiles, as in k_p2p_f32
+    // phase 1 in FP16 on cell-unit coordinates (the FP32 kernel's bound)
+    const __half2 tx = __float2half2_rn((float)(xt.x * inv_cell)), ty = __float2half2_rn((float)(xt.y * inv_cell)),
+                  tz = __float2half2_rn((float)(xt.z * inv_cell)),
+                  lim = __float2half2_rn((float)(rcc * rcc * 1.03 + 0.01));
     double ux = 0.0, uy = 0.0, uz = 0.0;
     for (int tile = 0; tile < ntile; ++tile) {
         const int n = (total - tile + ntile - 1) / ntile;
 #pragma unroll
-        for (int i = 0; i < kTile / 32; ++i) {
-            const int k = lane + 32 * i, q = tile + k * ntile;
-            if (k < n) {
-                int dx, dy, dz;
-                const int j = locate(ws, nseg, q, dx, dy, dz);
-                dvec4 p = npos[j];
-                p.x += dx * a.cell;
-                p.y += dy * a.cell;
-                p.z += dz * a.cell;
-                sp[k] = p;
-                sf[k] = nfrc[j];
-            } else {
-                sp[k] = dvec4{kFar, kFar, kFar, 0.0};
+        for (int i = 0; i < kTile / 64; ++i) {
+            float3 hp[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = lane + 32 * i + 64 * h, q = tile + k * ntile;
+                if (k < n) {
+                    int dx, dy, dz;
+                    const int j = locate(ws, nseg, q, dx, dy, dz);
+                    const dvec4 p = npos[j], f = nfrc[j];
+                    const double3 pp = make_double3(p.x + dx * a.cell, p.y + dy * a.cell, p.z + dz * a.cell);
+                    sp[k] = pp;
+                    sf[k] = make_double3(f.x, f.y, f.z);
+                    hp[h] = make_float3((float)(pp.x * inv_cell), (float)(pp.y * inv_cell),
+                                        (float)(pp.z * inv_cell));
+                } else {
+                    hp[h] = make_float3(kFarHalf, kFarHalf, kFarHalf);
+                }
             }
+            const __half2 hx = __floats2half2_rn(hp[0].x, hp[1].x);
+            const __half2 hy = __floats2half2_rn(hp[0].y, hp[1].y);
+            const __half2 hz = __floats2half2_rn(hp[0].z, hp[1].z);
+            sh[lane + 32 * i] = make_uint4(*(const unsigned *)&hx, *(const unsigned *)&hy,
+                                           *(const unsigned *)&hz, 0u);
         }
         __syncwarp();
-        if (active) {
-            unsigned long long m0, m1;
-            build_masks(
-                rc2f,
-                [&](int k) {
-                    const dvec4 &s = sp[k];
-                    double hx = xt.x - s.x, hy = xt.y - s.y, hz = xt.z - s.z;
-                    return (float)fma(hx, hx, fma(hy, hy, hz * hz));
-                },
-                m0, m1);
-            double px = 0.0, py = 0.0, pz = 0.0;
-            while (m0 | m1) {
-                const int k = next_bit(m0, m1);
-                const dvec4 &s = sp[k];
-                pair_f64(xt.x - s.x, xt.y - s.y, xt.z - s.z, sf[k], rc2, xi, xi2, c2, selfc, px,
-                         py, pz);
+        unsigned long long m0 = 0ull, m1 = 0ull;
+        if (active)
+            phase1_half_128(sh, tx, ty, tz, lim, m0, m1);
+        // two pairs per iteration: independent FP64 chains for the scheduler
+        double px = 0.0, py = 0.0, pz = 0.0;
+        while (__any_sync(0xffffffffu, (m0 | m1) != 0ull)) {
+            double3 d[2], fv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                d[u] = make_double3(1e3, 0.0, 0.0);
+                fv[u] = make_double3(0.0, 0.0, 0.0);
+                if (m0 | m1) {
+                    const int k = half_slot_128(next_bit(m0, m1));
+                    const double3 s = sp[k];
+                    d[u] = make_double3(xt.x - s.x, xt.y - s.y, xt.z - s.z);
+                    fv[u] = sf[k];
+                }
             }
-            ux += px;
-            uy += py;
-            uz += pz;
+            const double3 c0 = pair_f64_bulk(d[0].x, d[0].y, d[0].z, fv[0], rc2, xi, xi2, c2, selfc);
+            const double3 c1 = pair_f64_bulk(d[1].x, d[1].y, d[1].z, fv[1], rc2, xi, xi2, c2, selfc);
+            px += c0.x + c1.x;
+            py += c0.y + c1.y;
+            pz += c0.z + c1.z;
         }
+        ux += px;
+        uy += py;
+        uz += pz;
         __syncwarp();
     }
     if (active) {
@@ -762,6 +789,233 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f64(P2PArgs a)
         un[3 * i] = ux;
         un[3 * i + 1] = uy;
         un[3 * i + 2] = uz;
+    }
+}
+
+// ---- double-single near field ---------------------------------------------
+// Values carried as unevaluated sums h + l of two FP32 numbers (|l| <= ulp(h)/2,
+// ~44 significant bits): the FP32 pipe does ~64x the FP64 work per clock on
+// this GPU, so FP32 pairs beat native FP64 for the tol 1e-8 near field.  The
+// error-free transformations are the standard ones (Knuth's two-sum, Dekker's
+// fast two-sum, the FMA two-product); the _rn intrinsics keep the compiler
+// from contracting them into FMAs, which would break their exactness.
+struct dsf {
+    float h, l;
+};
+
+__device__ __forceinline__ dsf two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), v = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
+}
+__device__ __forceinline__ dsf quick_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dsf two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ dsf ds_add(dsf x, dsf y)
+{
+    const dsf s = two_sum(x.h, y.h);
+    return quick_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ dsf ds_add_f(dsf x, float y)
+{
+    const dsf s = two_sum(x.h, y);
+    return quick_two_sum(s.h, __fadd_rn(s.l, x.l));
+}
+__device__ __forceinline__ dsf ds_neg(dsf x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ dsf ds_mul(dsf x, dsf y)
+{
+    const float p = __fmul_rn(x.h, y.h);
+    const float e = fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p)));
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ dsf ds_scale2(dsf x, float pow2) { return {x.h * pow2, x.l * pow2}; }
+
+struct DSConst {
+    float rc2;              // cutoff^2 (cell units), compared on the high part
+    float rc2_half;         // FP16 phase-1 threshold, as the FP32 kernel
+    float rcm;              // sub-cell culling reach
+    dsf xi, xi2, c2, selfc; // xi, xi^2, 2 xi / sqrt(pi), 4 xi / sqrt(pi) (cell units)
+};
+
+// e^{-y} for 0 <= y <= ~60: y = n ln2 - s with |s| <= ln2/2 (ln2 split so that
+// n ln2_hi is exact and n ln2_mid is carried exactly by two_prod), e^s by its
+// Taylor series to s^13 (terms from s^6 on in FP32: they are below 3e-6), then
+// the exact scaling by 2^-n.
+__device__ __forceinline__ dsf exp_neg_ds(dsf y)
+{
+    const float kLn2Hi = 0.693145751953125f;          // 45426 * 2^-16
+    const float kLn2Mid = 1.428606765330187e-06f;     // ln2 - kLn2Hi, rounded
+    const float kLn2Lo = 5.497923148104107e-14f;      // ln2 - kLn2Hi - kLn2Mid, rounded
+    const float n = rintf(y.h * 1.44269504088896341f);
+    const float a = fmaf(n, kLn2Hi, -y.h);  // exact: both sides multiples of 2^-25, |a| < 1
+    const dsf m = two_prod(n, kLn2Mid);
+    dsf s = two_sum(a, m.h);
+    s = quick_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(m.l, fmaf(n, kLn2Lo, -y.l))));
+    float q = c_exp_ds_hi[EXP_DS_N - 1];
+#pragma unroll
+    for (int k = EXP_DS_N - 2; k >= 6; --k)
+        q = fmaf(q, s.h, c_exp_ds_hi[k]);
+    dsf p = {q, 0.f};
+#pragma unroll
+    for (int k = 5; k >= 3; --k)
+        p = ds_add(ds_mul(p, s), {c_exp_ds_hi[k], c_exp_ds_lo[k]});
+#pragma unroll
+    for (int k = 2; k >= 0; --k)
+        p = ds_add_f(ds_mul(p, s), c_exp_ds_hi[k]);
+    return ds_scale2(p, __int_as_float((127 - (int)n) << 23));
+}
+
+// erfcx(x) = t g(u), t = 1/(1 + x/2), u = (8t - 5)/3 (fit_erf.py: 1.2e-13
+// relative on [0, 6]); g's coefficients from k = ERFCX_DS_SPLIT on are below
+// 7e-6 and summed in FP32.
+__device__ __forceinline__ dsf erfcx_ds(dsf x)
+{
+    const dsf den = ds_add_f(ds_scale2(x, 0.5f), 1.0f);
+    const float t0 = __frcp_rn(den.h);
+    const dsf pr = ds_mul({den.h, den.l}, {t0, 0.f});
+    dsf t = quick_two_sum(t0, t0 * __fsub_rn(__fsub_rn(1.0f, pr.h), pr.l));
+    if (t.h < 0.25f)  // past the fit (x > 6): never for an in-range pair
+        t = {0.25f, 0.f};
+    const dsf u = ds_mul(ds_add_f(ds_scale2(t, 8.0f), -5.0f), {0.3333333432674408f, -9.934107758624577e-09f});
+    float q = c_erfcx_ds_hi[ERFCX_DS_N - 1];
+#pragma unroll
+    for (int k = ERFCX_DS_N - 2; k >= ERFCX_DS_SPLIT; --k)
+        q = fmaf(q, u.h, c_erfcx_ds_hi[k]);
+    dsf g = {q, 0.f};
+#pragma unroll
+    for (int k = ERFCX_DS_SPLIT - 1; k >= 0; --k)
+        g = ds_add(ds_mul(g, u), {c_erfcx_ds_hi[k], c_erfcx_ds_lo[k]});
+    return ds_mul(t, g);
+}
+
+// One double-single candidate (cell units): d = (hi diff, exact) + (lo diff),
+// force fh + fl; adds the pair's term (or the removed far part at r = 0) to acc.
+__device__ __forceinline__ void pair_ds(float dhx, float dhy, float dhz, float dlx, float dly,
+                                        float dlz, const float3 &fh, const float3 &fl,
+                                        const DSConst &k, dsf (&acc)[3])
+{
+    const dsf d[3] = {two_sum(dhx, dlx), two_sum(dhy, dly), two_sum(dhz, dlz)};
+    const dsf r2 = ds_add(ds_add(ds_mul(d[0], d[0]), ds_mul(d[1], d[1])), ds_mul(d[2], d[2]));
+    const dsf f[3] = {{fh.x, fl.x}, {fh.y, fl.y}, {fh.z, fl.z}};
+    if (r2.h > k.rc2)
+        return;
+    if (r2.h == 0.0f) {  // self or coincident point: the pair's far part comes out
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            acc[c] = ds_add(acc[c], ds_neg(ds_mul(k.selfc, f[c])));
+        return;
+    }
+    // 1/r: FP32 estimate and one Newton step carried in double-single
+    const float y0 = rsqrtf(r2.h);
+    const dsf t = ds_mul(r2, two_prod(y0, y0));
+    const dsf rinv = quick_two_sum(y0, 0.5f * y0 * __fsub_rn(__fsub_rn(1.0f, t.h), t.l));
+    const dsf x = ds_mul(k.xi, ds_mul(r2, rinv));
+    const dsf E = exp_neg_ds(ds_mul(k.xi2, r2));                       // e^{-xi^2 r^2}
+    const dsf A = ds_mul(ds_mul(E, erfcx_ds(x)), rinv);                // erfc(xi r) / r
+    const dsf B = ds_mul(k.c2, E);
+    const dsf amb = ds_add(A, ds_neg(B)), apb = ds_add(A, B);
+    const dsf rf = ds_add(ds_add(ds_mul(d[0], f[0]), ds_mul(d[1], f[1])), ds_mul(d[2], f[2]));
+    const dsf co = ds_mul(ds_mul(apb, rf), ds_mul(rinv, rinv));
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        acc[c] = ds_add(acc[c], ds_add(ds_mul(amb, f[c]), ds_mul(co, d[c])));
+}
+
+// Double-single tile of 128 sources: sa = (hi + colleague offset, lo.x),
+// sb = (lo.y, lo.z, fh.x, fh.y), sc = (fh.z, fl.x, fl.y, fl.z); FP16 copy for
+// phase 1 as the FP64 kernel.
+struct TileDS {
+    float4 sa[kTile];
+    float4 sb[kTile];
+    float4 sc[kTile];
+    uint4 sh[kTile / 2];
+};
+using WsDS = WarpSmem<TileDS>;
+constexpr int kDSBlocksPerSM = 6;  // shared-memory limited (4 warps x 9.2 KB)
+
+// The warps stride over the work items (the grid holds as many blocks as fit
+// at once): the heavier double-single pairs make a partial second wave costly.
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_ds(P2PArgs a, DSConst kc, int items)
+{
+    __shared__ WsDS wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WsDS &ws = wsm[warp];
+    const float4 *rec = (const float4 *)a.nrec, *flo = (const float4 *)a.nflo;
+    for (int item = blockIdx.x * kWarps + warp; item < items; item += gridDim.x * kWarps) {
+        int c, tb, te;
+        if (!find_item(a, item, c, tb, te))
+            break;  // items past the last real one: the same for the whole warp
+        const int t = tb + lane;
+        const bool active = t < te;
+        float3 th = make_float3(0.f, 0.f, 0.f), tl = th, fdum;
+        if (active)
+            unpack_rec(rec[2 * t], rec[2 * t + 1], th, tl, fdum);
+        const float3 blo = make_float3(warp_min(active ? th.x : 1e30f), warp_min(active ? th.y : 1e30f),
+                                       warp_min(active ? th.z : 1e30f));
+        const float3 bhi = make_float3(warp_max(active ? th.x : -1e30f),
+                                       warp_max(active ? th.y : -1e30f),
+                                       warp_max(active ? th.z : -1e30f));
+        const int nseg = build_segments(a, c, ws, lane, blo, bhi, 0.5f, kc.rcm);
+        const int total = ws.seg_pref[nseg];
+        const int ntile = (total + kTile - 1) / kTile;
+        const __half2 tx = __float2half2_rn(th.x), ty = __float2half2_rn(th.y),
+                      tz = __float2half2_rn(th.z), lim = __float2half2_rn(kc.rc2_half);
+        dsf acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (int tile = 0; tile < ntile; ++tile) {
+#pragma unroll
+            for (int i = 0; i < kTile / 64; ++i) {
+                float3 hp[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * i + 64 * h, q = tile + k * ntile;
+                    if (q < total) {
+                        int dx, dy, dz;
+                        const int j = locate(ws, nseg, q, dx, dy, dz);
+                        float3 hi, lo, f;
+                        unpack_rec(rec[2 * j], rec[2 * j + 1], hi, lo, f);
+                        const float4 fl = flo[j];
+                        hp[h] = make_float3(hi.x + (float)dx, hi.y + (float)dy, hi.z + (float)dz);
+                        ws.tile.sa[k] = make_float4(hp[h].x, hp[h].y, hp[h].z, lo.x);
+                        ws.tile.sb[k] = make_float4(lo.y, lo.z, f.x, f.y);
+                        ws.tile.sc[k] = make_float4(f.z, fl.x, fl.y, fl.z);
+                    } else {
+                        hp[h] = make_float3(kFarHalf, kFarHalf, kFarHalf);
+                    }
+                }
+                const __half2 hx = __floats2half2_rn(hp[0].x, hp[1].x);
+                const __half2 hy = __floats2half2_rn(hp[0].y, hp[1].y);
+                const __half2 hz = __floats2half2_rn(hp[0].z, hp[1].z);
+                ws.tile.sh[lane + 32 * i] = make_uint4(*(const unsigned *)&hx, *(const unsigned *)&hy,
+                                                       *(const unsigned *)&hz, 0u);
+            }
+            __syncwarp();
+            unsigned long long m0 = 0ull, m1 = 0ull;
+            if (active)
+                phase1_half_128(ws.tile.sh, tx, ty, tz, lim, m0, m1);
+            while (m0 | m1) {
+                const int k = half_slot_128(next_bit(m0, m1));
+                const float4 sa = ws.tile.sa[k], sb = ws.tile.sb[k], sc = ws.tile.sc[k];
+                pair_ds(th.x - sa.x, th.y - sa.y, th.z - sa.z, tl.x - sa.w, tl.y - sb.x, tl.z - sb.y,
+                        make_float3(sb.z, sb.w, sc.x), make_float3(sc.y, sc.z, sc.w), kc, acc);
+            }
+            __syncwarp();
+        }
+        if (active) {
+            const int i = a.permn[t];
+            double *un = (double *)a.un;
+            const double inv_cell = 1.0 / a.cell;
+            un[3 * i] = ((double)acc[0].h + (double)acc[0].l) * inv_cell;
+            un[3 * i + 1] = ((double)acc[1].h + (double)acc[1].l) * inv_cell;
+            un[3 * i + 2] = ((double)acc[2].h + (double)acc[2].l) * inv_cell;
+        }
+        __syncwarp();
     }
 }
 
@@ -795,6 +1049,14 @@ cudaError_t load_p2p_constants()
         e = cudaMemcpyToSymbol(c_erfp64, erf_rat_f64_p, sizeof(erf_rat_f64_p));
     if (e == cudaSuccess)
         e = cudaMemcpyToSymbol(c_erfq64, erf_rat_f64_q, sizeof(erf_rat_f64_q));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_erfcx_ds_hi, erfcx_ds_hi, sizeof(erfcx_ds_hi));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_erfcx_ds_lo, erfcx_ds_lo, sizeof(erfcx_ds_lo));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_exp_ds_hi, exp_ds_hi, sizeof(exp_ds_hi));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_exp_ds_lo, exp_ds_lo, sizeof(exp_ds_lo));
     if (e == cudaSuccess && dev >= 0 && dev < 64)
         g_const_loaded[dev] = true;
     return e;
@@ -809,6 +1071,7 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
     a.npos = p->npos;
     a.nfrc = p->nfrc;
     a.nrec = p->nrec;
+    a.nflo = p->nflo;
     a.startn = p->startn;
     a.item_off = p->item_off;
     a.permn = p->permn;
@@ -822,7 +1085,29 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
     // upper bound on work items: every cell contributes at most count/32 + 1
     const int64_t items = (int64_t)p->g.ncells + (p->N + kP2PChunk - 1) / kP2PChunk + 1;
     const unsigned grid = (unsigned)((items + kWarps - 1) / kWarps);
-    if (p->near64) {
+    if (p->near_ds) {
+        // cell units, every constant as a double-single pair
+        auto split = [](double v) {
+            dsf r;
+            r.h = (float)v;
+            r.l = (float)(v - (double)r.h);
+            return r;
+        };
+        DSConst kc;
+        const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
+        kc.rc2 = (float)(rcc * rcc);
+        kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
+        kc.rcm = (float)(rcc + 1e-3);
+        kc.xi = split(xic);
+        kc.xi2 = split(xic * xic);
+        kc.c2 = split(2.0 * xic / sqrt(3.14159265358979323846));
+        kc.selfc = split(4.0 * xic / sqrt(3.14159265358979323846));
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned cap = (unsigned)std::max(1, sms * kDSBlocksPerSM);
+        k_p2p_ds<<<std::min(grid, cap), kWarps * 32, 0, s>>>(a, kc, (int)(items));
+    } else if (p->near64) {
         k_p2p_f64<<<grid, kWarps * 32, 0, s>>>(a);
     } else {
         // cell units: lengths / cell, xi * cell
@@ -832,7 +1117,7 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         // phase 1 runs in FP16: coordinates within 3 cells carry <= 2^-10 each,
         // so |r^2 error| < 0.03 rc^2 + 0.005 below the cutoff (K <= 2)
         kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
-        kc.rcm = (float)(rcc + 1e-3);  // sub-cell culling reach: |lo| <= 2^-13 fits the margin
+        kc.rcm = (float)(rcc + 1e-3);  // sub-cell culling reach: |lo| <= 2^-21 fits the margin
         kc.xi = (float)xic;
         const double c = -xic * xic * 1.4426950408889634;  // -xi^2 log2(e), cell units
         kc.nxi2log2e = (float)c;

@@ -147,7 +147,8 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
     pl.npos = base + kOffNpos;
     pl.nlo = base + kOffNlo;
     pl.nfrc = base + kOffNfrc;
-    pl.nrec = base + kOffNpos;  // FP32 records (32 bytes a point) take the position area
+    // FP32 records (32 bytes a point) take the position area; FP64 uses npos
+    pl.nrec = pl.near64 ? nullptr : base + kOffNpos;
     pl.tdat = base + kOffTdat;
     pl.tfrc = base + kOffTfrc;
     pl.un = base + kOffUn;

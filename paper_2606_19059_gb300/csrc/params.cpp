@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "erf_rational.h"
 #include "internal.h"
 
 namespace ewg {
@@ -191,6 +192,9 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
     p.tol = tol;
     // FP32 bulk stops at tol 1e-7: below it P2P/P2G/G2P fall back to FP64
     p.near_f64 = (dtype == EWALD_F64 || tol < 1e-7) ? 1 : 0;
+    // below 1e-7 the FP32-bulk P2P runs in double-single arithmetic (the FP64
+    // pipe is 1/64 of the FP32 one on this GPU), down to 1e-9
+    p.near_ds = (dtype == EWALD_F32_BULK && tol < 1e-7 && tol >= 1e-9) ? 1 : 0;
     p.fft_f64 = (dtype == EWALD_F64 || tol < 1e-6) ? 1 : 0;
     // each estimated term held to tol/10: the estimate is an rms for unit
     // sum |f|^2, and the max-norm error runs about 3x the rms one (measured)
@@ -231,9 +235,17 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
             double cand = (double)N * (double)N * 27.0 * cellv;       // P2P candidates
             double inr = (double)N * (double)N * 4.18879 * r * r * r;  // in-range pairs
             double m3 = (double)m * m * m;
-            double cost = 10.0 * cand + 50.0 * inr                     // P2P
-                          + 2.0 * 8.0 * (double)N * P * P * P          // P2G + G2P
-                          + 2.0 * 30.0 * m3 * log2(m3) / 10.0;          // FFTs (memory bound)
+            // stage weights calibrated on a GB300 (N = 1e5, M = 128, P = 12:
+            // P2P 0.45, P2G + G2P 0.35, FFTs 0.084 ms in FP32); FP64 kernels
+            // cost 36x (P2P), 15x (P2G, G2P) and 16x (FFT) their FP32 time --
+            // the FP64 pipe is 1/64 of the FP32 one -- so FP64 plans move work
+            // from the near field to the grid
+            const double wn = p.near_ds ? 8.0 : (p.near_f64 ? 36.0 : 1.0);
+            const double wg = p.near_f64 ? 15.0 : 1.0;
+            const double wf = p.fft_f64 ? 16.0 : 1.0;
+            double cost = wn * (10.0 * cand + 50.0 * inr)              // P2P
+                          + wg * 28.0 * (double)N * P * P * P          // P2G + G2P
+                          + wf * 27.0 * m3 * log2(m3);                 // FFTs
             if (cost < best) {
                 best = cost;
                 M = m;
@@ -260,6 +272,8 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
     p.h = L / M;
     p.P = P;
     p.est_err = est_near(xi, rc) + est_far(1.0 / M, xi) + est_window(P);
+    if (p.near_ds && xi * rc > ERFCX_DS_X)  // beyond the double-single erfcx fit
+        p.near_ds = 0;
 
     // window polynomial degree: max error <= tol/20 (and the FP32 floor)
     double wtarget = std::max(tol / 30.0, p.near_f64 ? 1e-15 : 2e-8);
@@ -313,6 +327,7 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
     fb += N * 4 * 6;                                   // keys, slots, perms
     fb += (nkeys + 1) * 8 + (ntl + 1) * 8 + ((int64_t)nc * nc * nc + 1) * 8;
     fb += N * 2 * (p.near_f64 ? 32 : 16) * 2;          // sorted near / tile data
+    fb += p.near_ds ? N * 16 : 0;                      // double-single force low parts
     fb += N * 3 * (p.near_f64 ? 8 : 4) * 2;            // un, uf
     fb += 3 * m3 * (p.fft_f64 ? 8 : 4);                // real grid
     fb += 3 * mc * (p.fft_f64 ? 16 : 8);               // half spectrum

@@ -46,6 +46,8 @@ class ewald_params(ctypes.Structure):
         ("near_f64", ctypes.c_int32),
         ("fft_f64", ctypes.c_int32),
         ("footprint_bytes", ctypes.c_int64),
+        ("near_ds", ctypes.c_int32),
+        ("reserved_", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -47,6 +47,14 @@ DEG64 = 13
 XS32 = 1.0          # FP32 small-x branch: erf(x)/x as a polynomial in x^2 on [0, XS32]
 DEGS32 = 8
 DEGX2 = 6           # FP32 2^f on [-1/2, 1/2] (tight-tolerance exponential)
+# Double-single (pairs of FP32) near field, tol down to 1e-9: erfcx(x) = t g(u)
+# on x in [0, XDS], t = 1 / (1 + x/2) in [1/4, 1], u = (8 t - 5) / 3 in [-1, 1],
+# g a degree-DEGDS polynomial (Chebyshev interpolation, monomial form); terms
+# below DSSPLIT carry two-float coefficients, the rest one float.
+XDS = 6.0
+DEGDS = 16
+DSSPLIT = 9
+EXPDS_N = 13        # e^s, |s| <= ln2 / 2: Taylor terms 0..13; two-float for 3..5
 
 
 def erf_over_x(x):
@@ -202,6 +210,41 @@ def max_rel_error_f32(c, n_check: int = 20001) -> float:
     return float(m)
 
 
+def _g_ds(u):
+    t = (3 * mp.mpf(u) + 5) / 8
+    x = (1 / t - 1) * 2
+    return erfcx(x) / t
+
+
+def fit_erfcx_ds(deg: int):
+    """Monomial coefficients in u of the degree-`deg` Chebyshev interpolant of g."""
+    nodes = [mp.cos(mp.pi * (k + mp.mpf(1) / 2) / (deg + 1)) for k in range(deg + 1)]
+    V = mp.matrix([[u ** j for j in range(deg + 1)] for u in nodes])
+    c = mp.lu_solve(V, mp.matrix([_g_ds(u) for u in nodes]))
+    return [c[i] for i in range(deg + 1)]
+
+
+def max_rel_error_ds(c, n_check: int = 4001) -> float:
+    """max |t g(u) - erfcx(x)| / erfcx(x) over x in [0, XDS] (exact arithmetic,
+    coefficients as stored: two floats below DSSPLIT, one float above)."""
+    cs = []
+    for k, v in enumerate(c):
+        hi = float(np.float32(float(v)))
+        lo = float(np.float32(float(v - hi))) if k < DSSPLIT else 0.0
+        cs.append(mp.mpf(hi) + mp.mpf(lo))
+    m = mp.mpf(0)
+    for i in range(n_check):
+        u = -1 + 2 * mp.mpf(i) / (n_check - 1)
+        m = max(m, abs(_horner(cs, u) - _g_ds(u)) / _g_ds(u))
+    return float(m)
+
+
+def two_float(v):
+    hi = np.float32(float(v))
+    lo = np.float32(float(mp.mpf(v) - mp.mpf(float(hi))))
+    return float(hi), float(lo)
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     out = os.path.join(here, "csrc", "erf_rational.h")
@@ -216,6 +259,9 @@ def main():
     x2 = fit_exp2(DEGX2)
     ex2 = max_rel_error_exp2(x2)
     print("f32 2^f poly", DEGX2, "max rel error", ex2)
+    cds = fit_erfcx_ds(DEGDS)
+    eds = max_rel_error_ds(cds)
+    print("double-single erfcx g(u)", DEGDS, "max rel error", eds)
     print("f64 erf(x)/x  P/Q", DEG64, "max abs error", e64)
     print("f32 erfcx  t p(t)", DEG32, "max rel error", e32)
     L = [
@@ -256,6 +302,25 @@ def main():
           f"#define EXP2_F32_MAXERR {ex2:.3e}  /* relative, on 2^f, |f| <= 1/2 */",
           f"static const double exp2_f32_c[{DEGX2 + 1}] = {{"]
     L += [f"    {v!r}," for v in x2]
+    L += ["};", "",
+          "/* Double-single near field: erfcx(x) = t g(u), t = 1/(1 + x/2), u = (8t - 5)/3,",
+          " * x in [0, ERFCX_DS_X]; g_k = hi + lo for k < ERFCX_DS_SPLIT, hi alone above. */",
+          f"#define ERFCX_DS_X {XDS!r}",
+          f"#define ERFCX_DS_N {DEGDS + 1}",
+          f"#define ERFCX_DS_SPLIT {DSSPLIT}",
+          f"#define ERFCX_DS_MAXERR {eds:.3e}  /* relative, on erfcx(x), coefficients as stored */",
+          f"static const float erfcx_ds_hi[{DEGDS + 1}] = {{"]
+    L += [f"    {two_float(v)[0]!r}f," for v in cds]
+    L += ["};", f"static const float erfcx_ds_lo[{DSSPLIT}] = {{"]
+    L += [f"    {two_float(v)[1]!r}f," for v in cds[:DSSPLIT]]
+    L += ["};", "",
+          "/* e^s for |s| <= ln2/2: Taylor coefficients 1/k!, k = 0..EXP_DS_N - 1; two floats",
+          " * (hi, lo) for the inexact ones among k <= 5. */",
+          f"#define EXP_DS_N {EXPDS_N + 1}",
+          f"static const float exp_ds_hi[{EXPDS_N + 1}] = {{"]
+    L += [f"    {two_float(1 / mp.factorial(k))[0]!r}f," for k in range(EXPDS_N + 1)]
+    L += ["};", "static const float exp_ds_lo[6] = {"]
+    L += [f"    {two_float(1 / mp.factorial(k))[1]!r}f," for k in range(6)]
     L += ["};", ""]
     with open(out, "w") as fh:
         fh.write("\n".join(L))

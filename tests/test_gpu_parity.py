@@ -321,3 +321,29 @@ def test_stage_times_reported():
         assert t["total_ms"] > 0 and t["p2p_ms"] > 0 and t["p2g_ms"] > 0 and t["g2p_ms"] > 0
     k, nfft = ewald.ewald_launch_counts(p.handle)
     assert k >= 10 and nfft == 2
+
+
+# ------------------------------------------------- double-single near field --
+
+def test_near_field_double_single_matches_oracle():
+    # FP32 bulk below tol 1e-7: P2P in pairs of FP32 values (~44 bits); the
+    # positions' low parts are FP32 (2^-37 cell), so close pairs bound it
+    x, f = workloads.make("uniform", 3000, seed=103)
+    p = plan(3000, 1.0, 1e-8, F32, M=32, P=8)
+    assert p.params.near_ds == 1 and p.params.near_f64 == 1
+    u = host(p.near_field(dev(x), dev(f)))
+    ref = oracle.near_field(x, f, 1.0, p.params.xi, p.params.rc)
+    l2, mx = errs(u, ref)
+    assert l2 <= 1e-10 and mx <= 5e-10, (l2, mx)
+
+
+@pytest.mark.parametrize("kind,N,tol", [("uniform", 20000, 1e-8), ("clustered", 12000, 1e-9)])
+def test_f32_bulk_double_single_full_apply(kind, N, tol):
+    x, f = workloads.make(kind, N, seed=104)
+    p = plan(N, 1.0, tol, F32)
+    assert p.params.near_ds == 1
+    u = host(p.apply(dev(x), dev(f)))
+    idx = np.sort(np.random.default_rng(5).choice(N, 256, replace=False))
+    ref = oracle.ewald(x, f, 1.0, targets=idx)
+    l2, mx = errs(u[idx], ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)

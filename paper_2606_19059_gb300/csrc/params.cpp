@@ -238,9 +238,9 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
             // stage weights calibrated on a GB300 (N = 1e5, M = 128, P = 12:
             // P2P 0.45, P2G + G2P 0.35, FFTs 0.084 ms in FP32); FP64 kernels
             // cost 36x (P2P), 15x (P2G, G2P) and 16x (FFT) their FP32 time --
-            // the FP64 pipe is 1/64 of the FP32 one -- so FP64 plans move work
-            // from the near field to the grid
-            const double wn = p.near_ds ? 8.0 : (p.near_f64 ? 36.0 : 1.0);
+            // the FP64 pipe is 1/64 of the FP32 one -- and the double-single
+            // P2P ~12x, so FP64 plans move work from the near field to the grid
+            const double wn = p.near_ds ? 12.0 : (p.near_f64 ? 36.0 : 1.0);
             const double wg = p.near_f64 ? 15.0 : 1.0;
             const double wf = p.fft_f64 ? 16.0 : 1.0;
             double cost = wn * (10.0 * cand + 50.0 * inr)              // P2P

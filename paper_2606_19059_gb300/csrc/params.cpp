@@ -243,8 +243,10 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
             const double wn = p.near_ds ? 12.0 : (p.near_f64 ? 36.0 : 1.0);
             const double wg = p.near_f64 ? 15.0 : 1.0;
             const double wf = p.fft_f64 ? 16.0 : 1.0;
+            const double halo = pow((8.0 + P - 1.0) / 8.0, 3);      // staged block / tile
             double cost = wn * (10.0 * cand + 50.0 * inr)              // P2P
-                          + wg * 28.0 * (double)N * P * P * P          // P2G + G2P
+                          + wg * 28.0 * (double)N * P * P * P          // P2G + G2P per point
+                          + wg * 65.0 * m3 * halo                      // P2G + G2P per tile
                           + wf * 27.0 * m3 * log2(m3);                 // FFTs
             if (cost < best) {
                 best = cost;

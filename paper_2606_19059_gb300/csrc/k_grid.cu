@@ -673,6 +673,112 @@ __global__ void __launch_bounds__(kG2PPlanarThreads, 2) k_g2p_planar(GridArgs a)
     }
 }
 
+// FP64 G2P without staging.  An FP64 grid block of (T+P-1)^3 points x 3
+// components does not fit shared memory at T = 8 from P = 13 on, and smaller
+// tiles multiply the staged volume; the grid itself (3 M^3 doubles, e.g. 41 MB
+// at M = 120) stays in L2, so each warp reads its point's support directly:
+// lanes over the P x P (y, x) pairs (consecutive x on consecutive lanes: the
+// loads of a row coalesce), z walked per lane with s_c = sum_z wz v_c, then
+// u_c += wy wx s_c.  One block per tile of anchors (empty tiles exit), warps
+// over the tile's points; P is a compile-time constant.
+constexpr int kG2PDirectThreads = 256;
+
+template <int T, int PC>
+__global__ void __launch_bounds__(kG2PDirectThreads, 2) k_g2p_direct64(GridArgs a)
+{
+    constexpr int NW = kG2PDirectThreads / 32, NR = (PC * PC + 31) / 32;
+    const int tile = blockIdx.x;
+    const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
+    if (s0 == s1)
+        return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *coef = (double *)smem;               // [P][nd]
+    double *wsm = coef + PC * (a.deg + 1);       // per warp [3][PC]
+    const int nt = a.nt, M = a.M, nd = a.deg + 1;
+    const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
+    for (int i = threadIdx.x; i < PC * nd; i += kG2PDirectThreads)
+        coef[i] = ((const double *)a.wcoef)[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *w = wsm + warp * 3 * PC;
+    const double *grid = (const double *)a.grid;
+    const int64_t M2 = (int64_t)M * M, M3 = M2 * M;
+    const dvec4 *tdat = (const dvec4 *)a.tdat;
+    double *uf = (double *)a.uf;
+    for (int p = s0 + warp; p < s1; p += NW) {
+        const dvec4 td = tdat[p];
+        const int packed = (int)td.w;
+        const int ax = tx * T + (packed & 15), ay = ty * T + ((packed >> 4) & 15),
+                  az = tz * T + ((packed >> 8) & 15);
+        __syncwarp();
+        for (int q = lane; q < 3 * PC; q += 32) {
+            const int d = q / PC, l = q - d * PC;
+            const double z = 2.0 * (d == 0 ? td.x : (d == 1 ? td.y : td.z)) - 1.0;
+            w[d * PC + l] = horner(coef + l * nd, a.deg, z);
+        }
+        __syncwarp();
+        double wz[PC];
+        int64_t zoff[PC];
+#pragma unroll
+        for (int k = 0; k < PC; ++k) {
+            wz[k] = w[2 * PC + k];
+            int gz = az + k;
+            gz -= gz >= M ? M : 0;
+            zoff[k] = gz * M2;
+        }
+        double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int q = lane + 32 * r;
+            if (q < PC * PC) {
+                const int yy = q / PC, xx = q - yy * PC;
+                int gy = ay + yy, gx = ax + xx;
+                gy -= gy >= M ? M : 0;
+                gx -= gx >= M ? M : 0;
+                const double *v = grid + (int64_t)gy * M + gx;
+                double s0c = 0.0, s1c = 0.0, s2c = 0.0;
+#pragma unroll
+                for (int k = 0; k < PC; ++k) {
+                    const double *vk = v + zoff[k];
+                    s0c = fma(wz[k], __ldg(vk), s0c);
+                    s1c = fma(wz[k], __ldg(vk + M3), s1c);
+                    s2c = fma(wz[k], __ldg(vk + 2 * M3), s2c);
+                }
+                const double wyx = w[PC + yy] * w[xx];
+                u0 = fma(wyx, s0c, u0);
+                u1 = fma(wyx, s1c, u1);
+                u2 = fma(wyx, s2c, u2);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            u0 += __shfl_xor_sync(0xffffffffu, u0, o);
+            u1 += __shfl_xor_sync(0xffffffffu, u1, o);
+            u2 += __shfl_xor_sync(0xffffffffu, u2, o);
+        }
+        if (lane == 0) {
+            const int i = a.permt[p];
+            uf[3 * i] = u0 * a.scale;
+            uf[3 * i + 1] = u1 * a.scale;
+            uf[3 * i + 2] = u2 * a.scale;
+        }
+    }
+}
+
+template <int T, int PC>
+cudaError_t run_g2p_direct64(const GridArgs &a, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (a.P != PC)
+            return run_g2p_direct64<T, PC + 1>(a, s);
+        const size_t sm = sizeof(double) * ((size_t)PC * (a.deg + 1) + (kG2PDirectThreads / 32) * 3 * PC);
+        k_g2p_direct64<T, PC><<<a.nt * a.nt * a.nt, kG2PDirectThreads, sm, s>>>(a);
+        return cudaGetLastError();
+    }
+}
+
 GridArgs grid_args(ewald_plan_s *p)
 {
     GridArgs a;
@@ -709,16 +815,16 @@ cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// FP32 (grid G), T = 8: a compile-time-P kernel for every supported P
-template <typename G, int PC>
-cudaError_t run_p2g_f32_fixed(const GridArgs &a, cudaStream_t s)
+// T = 8: a compile-time-P kernel for every supported P (accumulation R, grid G)
+template <typename R, typename G, int PC>
+cudaError_t run_p2g_fixed(const GridArgs &a, cudaStream_t s)
 {
     if constexpr (PC > kMaxP) {
-        return run_p2g<8, float, G, 0>(a, s);
+        return run_p2g<8, R, G, 0>(a, s);
     } else {
         if (a.P == PC)
-            return run_p2g<8, float, G, PC>(a, s);
-        return run_p2g_f32_fixed<G, PC + 1>(a, s);
+            return run_p2g<8, R, G, PC>(a, s);
+        return run_p2g_fixed<R, G, PC + 1>(a, s);
     }
 }
 
@@ -766,13 +872,16 @@ cudaError_t run_g2p_f32_fixed(const GridArgs &a, cudaStream_t s)
 template <int T>
 cudaError_t dispatch_p2g(ewald_plan_s *p, const GridArgs &a, cudaStream_t s)
 {
-    if (p->near64)
-        return run_p2g<T, double, double, 0>(a, s);
     if constexpr (T == 8) {
+        // FP64: the run-time-P kernel (the compile-time one spills, measured slower)
+        if (p->near64)
+            return run_p2g<8, double, double, 0>(a, s);
         if (p->fft64)
-            return run_p2g_f32_fixed<double, 2>(a, s);
-        return run_p2g_f32_fixed<float, 2>(a, s);
+            return run_p2g_fixed<float, double, 2>(a, s);
+        return run_p2g_fixed<float, float, 2>(a, s);
     } else {
+        if (p->near64)
+            return run_p2g<T, double, double, 0>(a, s);
         if (p->fft64)
             return run_p2g<T, float, double, 0>(a, s);
         return run_p2g<T, float, float, 0>(a, s);
@@ -794,7 +903,7 @@ cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStre
     a.grid = const_cast<void *>(grid);
     a.scale = scale;
     if (p->near64)
-        return p->g.T == 8 ? run_g2p<8, double, 0>(a, s) : run_g2p<4, double, 0>(a, s);
+        return p->g.T == 8 ? run_g2p_direct64<8, 2>(a, s) : run_g2p_direct64<4, 2>(a, s);
     return p->g.T == 8 ? run_g2p_f32_fixed<2>(a, s) : run_g2p<4, float, 0>(a, s);
 }
 

@@ -294,11 +294,11 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
     }
     p.poly_deg = deg;
 
-    // grid tile T: the G2P block of (T + P - 1)^3 x 3 values must fit in
-    // shared memory (<= 222 KB of the 227 KB a block may use)
-    // (G2P stages it as 4-vectors of the kernels' precision: 16 or 32 bytes
-    // per grid point)
-    const double esz = p.near_f64 ? 32.0 : 16.0;
+    // grid tile T: the FP32 G2P block of (T + P - 1)^3 x 3 values must fit in
+    // shared memory (<= 222 KB of the 227 KB a block may use; counted at 16
+    // bytes a grid point, above the planar staging's 12); FP64 plans read the
+    // grid from L2 in G2P and only need P2G's shared memory, which fits at T = 8
+    const double esz = p.near_f64 ? 0.0 : 16.0;
     int T = o.tile > 0 ? o.tile : 8;
     if (T != 4 && T != 8)
         return EWALD_EUNSUPPORTED;

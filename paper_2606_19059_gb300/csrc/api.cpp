@@ -300,8 +300,7 @@ ewald_status bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t
     EW_CUDA(cudaMemsetAsync(p->cntn, 0, 4 * (size_t)g.nkeys, s));
     EW_CUDA(cudaMemsetAsync(p->cntt, 0, 4 * (size_t)g.ntiles, s));
     EW_CUDA(launch_bin_keys(p, a, s));
-    EW_CUDA(launch_scan(p->cntn, p->startn, g.nkeys, s));
-    EW_CUDA(launch_scan(p->cntt, p->startt, g.ntiles, s));
+    EW_CUDA(launch_scan2(p->cntn, p->startn, g.nkeys, p->cntt, p->startt, g.ntiles, s));
     EW_CUDA(launch_bin_scatter(p, a, s));
     EW_CUDA(launch_cell_items(p, s));
     p->positions_valid = true;
@@ -640,8 +639,9 @@ ewald_status ewald_launch_counts(ewald_plan_t plan, int32_t *kernels, int32_t *f
 {
     if (!plan || !kernels || !ffts)
         return EWALD_EINVAL;
-    // bin_keys, 2 scans, scatter, cell_items + scan, p2p, p2g, scale, g2p, sum
-    *kernels = 11;
+    // bin_keys, both scans (one launch), scatter, cell items with their scan,
+    // p2p, p2g, scale, g2p, sum -- plus the FP32 copy of an FP64 grid
+    *kernels = 9 + (plan->own_grid_g2p ? 1 : 0);
     *ffts = 2;
     return EWALD_OK;
 }

@@ -116,6 +116,9 @@ struct BinArgs {
 };
 cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s);
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s);
+// both scans in one launch (independent arrays)
+cudaError_t launch_scan2(const int32_t *in0, int32_t *out0, int n0, const int32_t *in1, int32_t *out1,
+                         int n1, cudaStream_t s);
 cudaError_t launch_bin_scatter(ewald_plan_s *p, const BinArgs &a, cudaStream_t s);
 cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t s);
 cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s);

@@ -199,17 +199,36 @@ __global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__r
     tfrc[p] = b;
 }
 
-// Exclusive scan of n counts by one block; out[n] receives the total.
-__global__ void __launch_bounds__(1024) k_scan(const int32_t *__restrict__ in,
-                                               int32_t *__restrict__ out, int n)
+// Exclusive scans of up to two count arrays, one block each (blockIdx.x
+// picks the pair); out[n] receives the total.  With `chunk` > 0 the values
+// scanned are the P2P work items of each cell, ceil(count / chunk) with count
+// read from the sub-cell starts `in` (stride kSub3), instead of in[i].
+struct ScanJob {
+    const int32_t *in;
+    int32_t *out;
+    int n, chunk;
+};
+
+__device__ __forceinline__ int scan_value(const ScanJob &j, int i)
+{
+    if (j.chunk <= 0)
+        return j.in[i];
+    const int cnt = j.in[(i + 1) * kSub3] - j.in[i * kSub3];
+    return (cnt + j.chunk - 1) / j.chunk;
+}
+
+__global__ void __launch_bounds__(1024) k_scan(ScanJob j0, ScanJob j1)
 {
     __shared__ int32_t wsum[32];
+    const ScanJob j = blockIdx.x == 0 ? j0 : j1;
+    const int n = j.n;
+    int32_t *__restrict__ out = j.out;
     int tid = threadIdx.x, nthr = blockDim.x;
     int per = (n + nthr - 1) / nthr;
     int lo = min(tid * per, n), hi = min(lo + per, n);
     int s = 0;
     for (int i = lo; i < hi; ++i)
-        s += in[i];
+        s += scan_value(j, i);
     int lane = tid & 31, w = tid >> 5;
     int v = s;
 #pragma unroll
@@ -236,23 +255,12 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t *__restrict__ in,
     __syncthreads();
     int run = v - s + (w > 0 ? wsum[w - 1] : 0);
     for (int i = lo; i < hi; ++i) {
-        int c = in[i];
+        int c = scan_value(j, i);
         out[i] = run;
         run += c;
     }
     if (tid == nthr - 1)
         out[n] = run;
-}
-
-// Number of P2P work items (target chunks of at most `block` points) per cell.
-__global__ void k_cell_items(const int32_t *__restrict__ startn, int32_t *__restrict__ items,
-                             int ncells, int block)
-{
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncells)
-        return;
-    int cnt = startn[(c + 1) * kSub3] - startn[c * kSub3];
-    items[c] = (cnt + block - 1) / block;
 }
 
 // Step a7 (Algorithm 1, SUM): u = u^N + u^F in FP64, user order (the self
@@ -332,7 +340,15 @@ cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s)
 
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s)
 {
-    k_scan<<<1, 1024, 0, s>>>(in, out, n);
+    ScanJob j{in, out, n, 0};
+    k_scan<<<1, 1024, 0, s>>>(j, j);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan2(const int32_t *in0, int32_t *out0, int n0, const int32_t *in1, int32_t *out1,
+                         int n1, cudaStream_t s)
+{
+    k_scan<<<2, 1024, 0, s>>>(ScanJob{in0, out0, n0, 0}, ScanJob{in1, out1, n1, 0});
     return cudaGetLastError();
 }
 
@@ -358,14 +374,13 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
     return cudaGetLastError();
 }
 
+// P2P work items per cell (chunks of at most kP2PChunk targets) and their
+// prefix offsets, in one launch.
 cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s)
 {
-    k_cell_items<<<blocks_for(p->g.ncells, 256), 256, 0, s>>>(p->startn, p->items, p->g.ncells,
-                                                               kP2PChunk);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return e;
-    return launch_scan(p->items, p->item_off, p->g.ncells, s);
+    ScanJob j{p->startn, p->item_off, p->g.ncells, kP2PChunk};
+    k_scan<<<1, 1024, 0, s>>>(j, j);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s)

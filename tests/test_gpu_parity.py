@@ -320,7 +320,7 @@ def test_stage_times_reported():
         t = ewald.ewald_stage_times(p.handle)
         assert t["total_ms"] > 0 and t["p2p_ms"] > 0 and t["p2g_ms"] > 0 and t["g2p_ms"] > 0
     k, nfft = ewald.ewald_launch_counts(p.handle)
-    assert k >= 10 and nfft == 2
+    assert 9 <= k <= 10 and nfft == 2  # bin 4, P2P, P2G, CNV, G2P, SUM (+ grid copy)
 
 
 # ------------------------------------------------- double-single near field --

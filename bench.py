@@ -260,9 +260,7 @@ def run_batch(args, rank):
     torch.cuda.synchronize()
     ms = [a.elapsed_time(e) for a, e in evs]
     tuned = {(int(b.params(i).M), int(b.params(i).tile)) for i in range(len(N))}
-    kern = 0
-    for i in range(len(N)):
-        kern += ewald.ewald_launch_counts(_batch_plan(b, i))[0]
+    kern = b.launch_counts()[0]
     b.close()
     ms_med = float(np.median(ms))
     return {"boxes": int(len(N)), "particles": int(N.sum()), "ms_per_step": ms_med,
@@ -303,16 +301,6 @@ def run_serving(args, rank):
                         "50/50; tol uniform in {1e-4, 1e-6, 1e-8}; FP32 bulk; 20 applies per request with "
                         "f += 0.1 N(0,1) re-centred (Philox4x32-10); latency from submit to the last "
                         "apply's u on the host; HBM budget 200 GB, 8 slots"}
-
-
-def _batch_plan(b, i):
-    import ctypes
-
-    from paper_2606_19059_gb300 import ewald
-
-    h = ctypes.c_void_p()
-    ewald._check(ewald.load().ewald_batch_plan(b.handle, int(i), ctypes.byref(h)), "ewald_batch_plan")
-    return h.value
 
 
 def cpu_baseline(n_targets: int, seed_shift: int = 0):

@@ -249,11 +249,17 @@ ewald_status ewald_batch_get_params(ewald_batch_t b, int32_t box, ewald_params *
 /* The plan of one box (owned by the batch; valid until ewald_batch_destroy). */
 ewald_status ewald_batch_plan(ewald_batch_t b, int32_t box, ewald_plan_t *out);
 /* Apply every box: u = apply(x, f) per box, as ewald_apply would give with
- * the box's plan.  The first call records all the boxes' applies into one
- * CUDA graph (boxes by decreasing N dealt round-robin over the streams);
- * every call launches that graph on `stream`, asynchronously.  Calls on one
- * batch must not overlap in time. */
+ * the box's plan.  The first call records the batch into one CUDA graph:
+ * binning, far field and sum of each box (boxes by decreasing N dealt
+ * round-robin over the streams), and the near field of all boxes as one
+ * persistent launch per P2P variant (FP32, compensated FP32, double-single,
+ * FP64) whose warps stride over every box's work items; every call launches
+ * that graph on `stream`, asynchronously.  Calls on one batch must not
+ * overlap in time. */
 ewald_status ewald_batch_apply(ewald_batch_t b, void *stream);
+/* Kernel launches (this library's own kernels) and cuFFT executions in one
+ * ewald_batch_apply. */
+ewald_status ewald_batch_launch_counts(ewald_batch_t b, int32_t *kernels, int32_t *ffts);
 void ewald_batch_destroy(ewald_batch_t b);
 
 /* ---- Serving: a continuous-batching request loop -------------------------

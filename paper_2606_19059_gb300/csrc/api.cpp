@@ -383,6 +383,31 @@ bool bad_ptr(const void *a) { return a == nullptr; }
 
 }  // namespace
 
+// Apply phases for batches of plans (csrc/batch.cpp).
+namespace ewg {
+ewald_status plan_bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t s)
+{
+    return bin(p, x, f, s);
+}
+
+ewald_status plan_far(ewald_plan_s *p, cudaStream_t s)
+{
+    const double h3 = p->g.h * p->g.h * p->g.h;
+    EW_CUDA(launch_p2g(p, s));
+    EW_ST(fgc(p, 8.0 * kPi * h3 / (double)p->g.nreal, s));
+    if (p->own_grid_g2p)
+        EW_CUDA(launch_grid_convert(p->grid, true, p->grid_g2p, false, 3 * p->g.nreal, s));
+    EW_CUDA(launch_g2p(p, p->grid_g2p, 1.0, s));
+    return EWALD_OK;
+}
+
+ewald_status plan_sum(ewald_plan_s *p, double *u, cudaStream_t s)
+{
+    EW_CUDA(launch_sum(p, nullptr, u, s));
+    return EWALD_OK;
+}
+}  // namespace ewg
+
 extern "C" {
 
 const char *ewald_status_string(ewald_status s)

@@ -11,9 +11,10 @@
 //
 // A batch holds one plan per box (each with its own N, L, tol and tuned
 // parameters) and device buffers for the boxes' x, f and u.  The first apply
-// captures every box's apply into one CUDA graph, boxes spread over several
-// capture streams so that small boxes run side by side; later applies replay
-// the graph with one launch.
+// captures the whole batch into one CUDA graph: binning, far field and sum per
+// box over several capture streams (small boxes run side by side), and the
+// near field of all boxes as one persistent launch per P2P variant; later
+// applies replay the graph with one launch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -179,6 +180,9 @@ struct ewald_batch_s {
     cudaStream_t cap = nullptr;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> joins;
+    std::vector<cudaEvent_t> binned;  // per stream: its boxes binned
+    cudaEvent_t near_done = nullptr;  // the batched near field finished
+    P2PBoxes *near = nullptr;         // one persistent P2P launch per variant
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -207,11 +211,20 @@ void free_batch(ewald_batch_s *b)
     for (cudaEvent_t e : b->joins)
         if (e)
             cudaEventDestroy(e);
+    for (cudaEvent_t e : b->binned)
+        if (e)
+            cudaEventDestroy(e);
+    if (b->near_done)
+        cudaEventDestroy(b->near_done);
+    p2p_boxes_destroy(b->near);
     delete b;
 }
 
 // Record every box's apply into one graph: boxes by decreasing N, dealt
-// round-robin over the capture streams.
+// round-robin over the capture streams.  Each stream bins its boxes; one
+// persistent near-field launch per P2P variant then covers every box's work
+// items while the streams run their boxes' far fields; each box's sum waits
+// for both.
 ewald_status capture(ewald_batch_s *b)
 {
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess)
@@ -226,11 +239,27 @@ ewald_status capture(ewald_batch_s *b)
     for (int i = 0; i < b->nbox; ++i)
         order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->N[a] > b->N[c]; });
+    const size_t ns = b->streams.size();
     for (int r = 0; r < b->nbox && st == EWALD_OK; ++r) {
         const int i = order[r];
         double *x = b->buf + b->off[i];
-        const int64_t n3 = 3 * b->N[i];
-        st = ewald_apply(b->plans[i], x, x + n3, x + 2 * n3, b->streams[r % b->streams.size()]);
+        st = plan_bin(b->plans[i], x, x + 3 * b->N[i], b->streams[r % ns]);
+    }
+    for (size_t k = 0; k < ns && st == EWALD_OK; ++k)
+        if (cudaEventRecord(b->binned[k], b->streams[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->cap, b->binned[k], 0) != cudaSuccess)
+            st = EWALD_ECUDA;
+    if (st == EWALD_OK && (p2p_boxes_launch(b->near, b->cap) != cudaSuccess ||
+                           cudaEventRecord(b->near_done, b->cap) != cudaSuccess))
+        st = EWALD_ECUDA;
+    for (int r = 0; r < b->nbox && st == EWALD_OK; ++r)
+        st = plan_far(b->plans[order[r]], b->streams[r % ns]);
+    for (size_t k = 0; k < ns && st == EWALD_OK; ++k)
+        if (cudaStreamWaitEvent(b->streams[k], b->near_done, 0) != cudaSuccess)
+            st = EWALD_ECUDA;
+    for (int r = 0; r < b->nbox && st == EWALD_OK; ++r) {
+        const int i = order[r];
+        st = plan_sum(b->plans[i], b->buf + b->off[i] + 6 * b->N[i], b->streams[r % ns]);
     }
     for (size_t k = 0; k < b->streams.size() && st == EWALD_OK; ++k)
         if (cudaEventRecord(b->joins[k], b->streams[k]) != cudaSuccess ||
@@ -404,13 +433,20 @@ ewald_status ewald_batch_create(int32_t nbox, const int64_t *N, const double *L,
         st = EWALD_ECUDA;
     b->streams.assign(std::min(nstreams, nbox), nullptr);
     b->joins.assign(b->streams.size(), nullptr);
+    b->binned.assign(b->streams.size(), nullptr);
     for (size_t k = 0; k < b->streams.size() && st == EWALD_OK; ++k)
         if (cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->joins[k], cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&b->joins[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->binned[k], cudaEventDisableTiming) != cudaSuccess)
             st = EWALD_ECUDA;
     if (st == EWALD_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
-                           cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess))
+                           cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&b->near_done, cudaEventDisableTiming) != cudaSuccess))
         st = EWALD_ECUDA;
+    if (st == EWALD_OK && p2p_boxes_create(b->plans.data(), nbox, &b->near) != cudaSuccess) {
+        cudaGetLastError();
+        st = EWALD_ECUDA;
+    }
     if (st != EWALD_OK) {
         free_batch(b);
         return st;
@@ -465,6 +501,22 @@ ewald_status ewald_batch_apply(ewald_batch_t b, void *stream)
     if (dev != b->device && dev >= 0)
         cudaSetDevice(dev);
     return st;
+}
+
+ewald_status ewald_batch_launch_counts(ewald_batch_t b, int32_t *kernels, int32_t *ffts)
+{
+    if (!b || !kernels || !ffts)
+        return EWALD_EINVAL;
+    int32_t k = 0, f = 0;
+    for (ewald_plan_t p : b->plans) {
+        int32_t kp = 0, fp = 0;
+        ewald_launch_counts(p, &kp, &fp);
+        k += kp - 1;  // each box's own P2P launch is replaced ...
+        f += fp;
+    }
+    *kernels = k + p2p_boxes_launches(b->near);  // ... by one per variant
+    *ffts = f;
+    return EWALD_OK;
 }
 
 void ewald_batch_destroy(ewald_batch_t b) { free_batch(b); }

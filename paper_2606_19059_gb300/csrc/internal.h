@@ -129,6 +129,18 @@ cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);
 // the sum is multiplied by `scale`.
 cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s);
 cudaError_t load_p2p_constants();
+// The near field of many plans: one persistent launch per P2P variant over
+// all their work items (the plans' own buffers; they must stay alive).
+struct P2PBoxes;
+cudaError_t p2p_boxes_create(ewald_plan_s *const *plans, int n, P2PBoxes **out);
+cudaError_t p2p_boxes_launch(const P2PBoxes *b, cudaStream_t s);
+int p2p_boxes_launches(const P2PBoxes *b);
+void p2p_boxes_destroy(P2PBoxes *b);
+// Apply phases for batches: binning (positions and forces), the far field into
+// the plan's u^F, and the final sum (after the near field has run).
+ewald_status plan_bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t s);
+ewald_status plan_far(ewald_plan_s *p, cudaStream_t s);
+ewald_status plan_sum(ewald_plan_s *p, double *u, cudaStream_t s);
 cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s);
 cudaError_t launch_copy_out(const void *src, bool src_f64, double *dst, int64_t n, cudaStream_t s);
 // Served requests: f <- f + a n (Philox4x32-10 normals for (point, step,

@@ -38,7 +38,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <new>
 #include <type_traits>
+#include <vector>
 
 #include "erf_rational.h"
 #include "internal.h"
@@ -573,15 +575,14 @@ __device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg,
 }
 
 // KAHAN: compensated partial sums, flushed into FP64 totals at every ring step.
+// One work item (a chunk of <= 32 targets of one cell) by one warp.
 template <bool KAHAN>
-__global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)
+__device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &kc, float inv_cell,
+                                             int item, WsF32 &ws, int lane)
 {
     using Tot = typename std::conditional<KAHAN, double, float>::type;
-    __shared__ WsF32 wsm[kWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WsF32 &ws = wsm[warp];
     int c, tb, te;
-    if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
+    if (!find_item(a, item, c, tb, te))
         return;  // whole warp: no block-wide barrier follows
     const int t = tb + lane;
     const bool active = t < te;
@@ -692,15 +693,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc,
     }
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 5) k_p2p_f64(P2PArgs a)
+template <bool KAHAN>
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)
 {
-    __shared__ WsF64 wsm[kWarps];
+    __shared__ WsF32 wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WsF64 &ws = wsm[warp];
+    p2p_f32_item<KAHAN>(a, kc, inv_cell, blockIdx.x * kWarps + warp, wsm[warp], lane);
+}
+
+__device__ __forceinline__ void p2p_f64_item(const P2PArgs &a, int item, WsF64 &ws, int lane)
+{
     double3 *sp = ws.tile.sp, *sf = ws.tile.sf;
     uint4 *sh = ws.tile.sh;
     int c, tb, te;
-    if (!find_item(a, blockIdx.x * kWarps + warp, c, tb, te))
+    if (!find_item(a, item, c, tb, te))
         return;
     const dvec4 *npos = (const dvec4 *)a.npos, *nfrc = (const dvec4 *)a.nfrc;
     const int t = tb + lane;
@@ -790,6 +796,13 @@ __global__ void __launch_bounds__(kWarps * 32, 5) k_p2p_f64(P2PArgs a)
         un[3 * i + 1] = uy;
         un[3 * i + 2] = uz;
     }
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 5) k_p2p_f64(P2PArgs a)
+{
+    __shared__ WsF64 wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    p2p_f64_item(a, blockIdx.x * kWarps + warp, wsm[warp], lane);
 }
 
 // ---- double-single near field ---------------------------------------------
@@ -942,16 +955,14 @@ constexpr int kDSBlocksPerSM = 6;  // shared-memory limited (4 warps x 9.2 KB)
 
 // The warps stride over the work items (the grid holds as many blocks as fit
 // at once): the heavier double-single pairs make a partial second wave costly.
-__global__ void __launch_bounds__(kWarps * 32) k_p2p_ds(P2PArgs a, DSConst kc, int items)
+__device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc, int item, WsDS &ws,
+                                            int lane)
 {
-    __shared__ WsDS wsm[kWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WsDS &ws = wsm[warp];
     const float4 *rec = (const float4 *)a.nrec, *flo = (const float4 *)a.nflo;
-    for (int item = blockIdx.x * kWarps + warp; item < items; item += gridDim.x * kWarps) {
+    {
         int c, tb, te;
         if (!find_item(a, item, c, tb, te))
-            break;  // items past the last real one: the same for the whole warp
+            return;  // past the last real item: the same for the whole warp
         const int t = tb + lane;
         const bool active = t < te;
         float3 th = make_float3(0.f, 0.f, 0.f), tl = th, fdum;
@@ -1015,6 +1026,67 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_ds(P2PArgs a, DSConst kc, i
             un[3 * i + 1] = ((double)acc[1].h + (double)acc[1].l) * inv_cell;
             un[3 * i + 2] = ((double)acc[2].h + (double)acc[2].l) * inv_cell;
         }
+    }
+}
+
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_ds(P2PArgs a, DSConst kc, int items)
+{
+    __shared__ WsDS wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int item = blockIdx.x * kWarps + warp; item < items; item += gridDim.x * kWarps) {
+        p2p_ds_item(a, kc, item, wsm[warp], lane);
+        __syncwarp();
+    }
+}
+
+// ---- many boxes in one launch ---------------------------------------------
+// One persistent launch per P2P variant over the work items of every box of a
+// batch: box b owns global items [base[b], base[b + 1]) (its item upper bound,
+// cells + N / 32 + 1), a warp finds its box by binary search and runs the
+// single-box item code with that box's arguments.  The grid holds as many
+// blocks as fit at once; warps stride over the items.
+struct BoxP2P {
+    P2PArgs a;
+    F32Const k32;
+    DSConst kds;
+    float inv_cell;
+};
+
+__device__ __forceinline__ int box_of(const int *base, int nbox, int g)
+{
+    int lo = 0, hi = nbox;  // base[lo] <= g < base[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= g)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// VAR: 0 FP32, 1 FP32 tight (compensated), 2 double-single, 3 FP64
+template <int VAR>
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_boxes(const BoxP2P *__restrict__ boxes,
+                                                           const int *__restrict__ base, int nbox)
+{
+    using WS = typename std::conditional<
+        VAR <= 1, WsF32, typename std::conditional<VAR == 2, WsDS, WsF64>::type>::type;
+    __shared__ WS wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = base[nbox];
+    for (int g = blockIdx.x * kWarps + warp; g < total; g += gridDim.x * kWarps) {
+        const int b = box_of(base, nbox, g);
+        const BoxP2P &bx = boxes[b];
+        const int item = g - base[b];
+        if constexpr (VAR == 0)
+            p2p_f32_item<false>(bx.a, bx.k32, bx.inv_cell, item, wsm[warp], lane);
+        else if constexpr (VAR == 1)
+            p2p_f32_item<true>(bx.a, bx.k32, bx.inv_cell, item, wsm[warp], lane);
+        else if constexpr (VAR == 2)
+            p2p_ds_item(bx.a, bx.kds, item, wsm[warp], lane);
+        else
+            p2p_f64_item(bx.a, item, wsm[warp], lane);
         __syncwarp();
     }
 }
@@ -1062,11 +1134,10 @@ cudaError_t load_p2p_constants()
     return e;
 }
 
-cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
+namespace {
+
+P2PArgs p2p_args(const ewald_plan_s *p)
 {
-    cudaError_t e = load_p2p_constants();
-    if (e != cudaSuccess)
-        return e;
     P2PArgs a;
     a.npos = p->npos;
     a.nfrc = p->nfrc;
@@ -1082,54 +1153,196 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
     a.cell = p->g.cell;
     a.rc = p->prm.rc;
     a.xi = p->prm.xi;
-    // upper bound on work items: every cell contributes at most count/32 + 1
-    const int64_t items = (int64_t)p->g.ncells + (p->N + kP2PChunk - 1) / kP2PChunk + 1;
+    return a;
+}
+
+// upper bound on work items: every cell contributes at most count/32 + 1
+int64_t p2p_items(const ewald_plan_s *p)
+{
+    return (int64_t)p->g.ncells + (p->N + kP2PChunk - 1) / kP2PChunk + 1;
+}
+
+// cell units: lengths / cell, xi * cell
+F32Const f32_const(const ewald_plan_s *p)
+{
+    F32Const kc;
+    const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
+    kc.rc2 = (float)(rcc * rcc);
+    // phase 1 runs in FP16: coordinates within 3 cells carry <= 2^-10 each,
+    // so |r^2 error| < 0.03 rc^2 + 0.005 below the cutoff (K <= 2)
+    kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
+    kc.rcm = (float)(rcc + 1e-3);  // sub-cell culling reach: |lo| <= 2^-21 fits the margin
+    kc.xi = (float)xic;
+    const double c = -xic * xic * 1.4426950408889634;  // -xi^2 log2(e), cell units
+    kc.nxi2log2e = (float)c;
+    kc.nxi2log2e_lo = (float)(c - (double)kc.nxi2log2e);
+    kc.c2 = (float)(2.0 * xic / sqrt(3.14159265358979323846));
+    kc.selfc = (float)(4.0 * xic / sqrt(3.14159265358979323846));
+    return kc;
+}
+
+// cell units, every constant as a double-single pair
+DSConst ds_const(const ewald_plan_s *p)
+{
+    auto split = [](double v) {
+        dsf r;
+        r.h = (float)v;
+        r.l = (float)(v - (double)r.h);
+        return r;
+    };
+    DSConst kc;
+    const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
+    kc.rc2 = (float)(rcc * rcc);
+    kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
+    kc.rcm = (float)(rcc + 1e-3);
+    kc.xi = split(xic);
+    kc.xi2 = split(xic * xic);
+    kc.c2 = split(2.0 * xic / sqrt(3.14159265358979323846));
+    kc.selfc = split(4.0 * xic / sqrt(3.14159265358979323846));
+    return kc;
+}
+
+// 0 FP32, 1 FP32 tight (compensated sums below tol 1e-6), 2 double-single, 3 FP64
+int p2p_variant(const ewald_plan_s *p)
+{
+    if (p->near_ds)
+        return 2;
+    if (p->near64)
+        return 3;
+    return p->prm.tol < 1e-6 ? 1 : 0;
+}
+
+unsigned resident_blocks(const void *kernel, int dev)
+{
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kWarps * 32, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per = 1;
+    }
+    return (unsigned)std::max(1, sms * std::max(1, per));
+}
+
+}  // namespace
+
+cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
+{
+    cudaError_t e = load_p2p_constants();
+    if (e != cudaSuccess)
+        return e;
+    const P2PArgs a = p2p_args(p);
+    const int64_t items = p2p_items(p);
     const unsigned grid = (unsigned)((items + kWarps - 1) / kWarps);
-    if (p->near_ds) {
-        // cell units, every constant as a double-single pair
-        auto split = [](double v) {
-            dsf r;
-            r.h = (float)v;
-            r.l = (float)(v - (double)r.h);
-            return r;
-        };
-        DSConst kc;
-        const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
-        kc.rc2 = (float)(rcc * rcc);
-        kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
-        kc.rcm = (float)(rcc + 1e-3);
-        kc.xi = split(xic);
-        kc.xi2 = split(xic * xic);
-        kc.c2 = split(2.0 * xic / sqrt(3.14159265358979323846));
-        kc.selfc = split(4.0 * xic / sqrt(3.14159265358979323846));
-        int sms = 0, dev = 0;
+    switch (p2p_variant(p)) {
+    case 2: {
+        int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const unsigned cap = (unsigned)std::max(1, sms * kDSBlocksPerSM);
-        k_p2p_ds<<<std::min(grid, cap), kWarps * 32, 0, s>>>(a, kc, (int)(items));
-    } else if (p->near64) {
+        const unsigned cap = resident_blocks((const void *)k_p2p_ds, dev);
+        k_p2p_ds<<<std::min(grid, cap), kWarps * 32, 0, s>>>(a, ds_const(p), (int)items);
+        break;
+    }
+    case 3:
         k_p2p_f64<<<grid, kWarps * 32, 0, s>>>(a);
-    } else {
-        // cell units: lengths / cell, xi * cell
-        F32Const kc;
-        const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
-        kc.rc2 = (float)(rcc * rcc);
-        // phase 1 runs in FP16: coordinates within 3 cells carry <= 2^-10 each,
-        // so |r^2 error| < 0.03 rc^2 + 0.005 below the cutoff (K <= 2)
-        kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
-        kc.rcm = (float)(rcc + 1e-3);  // sub-cell culling reach: |lo| <= 2^-21 fits the margin
-        kc.xi = (float)xic;
-        const double c = -xic * xic * 1.4426950408889634;  // -xi^2 log2(e), cell units
-        kc.nxi2log2e = (float)c;
-        kc.nxi2log2e_lo = (float)(c - (double)kc.nxi2log2e);
-        kc.c2 = (float)(2.0 * xic / sqrt(3.14159265358979323846));
-        kc.selfc = (float)(4.0 * xic / sqrt(3.14159265358979323846));
-        if (p->prm.tol < 1e-6)  // compensated sums below tol 1e-6
-            k_p2p_f32<true><<<grid, kWarps * 32, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
-        else
-            k_p2p_f32<false><<<grid, kWarps * 32, 0, s>>>(a, kc, (float)(1.0 / p->g.cell));
+        break;
+    case 1:
+        k_p2p_f32<true><<<grid, kWarps * 32, 0, s>>>(a, f32_const(p), (float)(1.0 / p->g.cell));
+        break;
+    default:
+        k_p2p_f32<false><<<grid, kWarps * 32, 0, s>>>(a, f32_const(p), (float)(1.0 / p->g.cell));
     }
     return cudaGetLastError();
+}
+
+// ---- the near field of many plans in one launch per variant ---------------
+struct P2PBoxes {
+    int dev = 0;
+    BoxP2P *boxes[4] = {};  // device, per variant
+    int *base[4] = {};      // device, per variant: nbox + 1 prefix offsets of items
+    int nbox[4] = {};
+    unsigned grid[4] = {};
+};
+
+cudaError_t p2p_boxes_create(ewald_plan_s *const *plans, int n, P2PBoxes **out)
+{
+    cudaError_t e = load_p2p_constants();
+    if (e != cudaSuccess)
+        return e;
+    P2PBoxes *b = new (std::nothrow) P2PBoxes;
+    if (!b)
+        return cudaErrorMemoryAllocation;
+    cudaGetDevice(&b->dev);
+    std::vector<BoxP2P> hb[4];
+    std::vector<int> hbase[4];
+    for (int v = 0; v < 4; ++v)
+        hbase[v].push_back(0);
+    for (int i = 0; i < n; ++i) {
+        const ewald_plan_s *p = plans[i];
+        const int v = p2p_variant(p);
+        BoxP2P x;
+        x.a = p2p_args(p);
+        x.k32 = f32_const(p);
+        if (v == 2)
+            x.kds = ds_const(p);
+        x.inv_cell = (float)(1.0 / p->g.cell);
+        hb[v].push_back(x);
+        hbase[v].push_back(hbase[v].back() + (int)p2p_items(p));
+    }
+    const void *kern[4] = {(const void *)k_p2p_boxes<0>, (const void *)k_p2p_boxes<1>,
+                           (const void *)k_p2p_boxes<2>, (const void *)k_p2p_boxes<3>};
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+        b->nbox[v] = (int)hb[v].size();
+        if (!b->nbox[v])
+            continue;
+        e = cudaMalloc(&b->boxes[v], sizeof(BoxP2P) * hb[v].size());
+        if (e == cudaSuccess)
+            e = cudaMalloc(&b->base[v], sizeof(int) * hbase[v].size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->boxes[v], hb[v].data(), sizeof(BoxP2P) * hb[v].size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->base[v], hbase[v].data(), sizeof(int) * hbase[v].size(), cudaMemcpyHostToDevice);
+        const unsigned need = (unsigned)((hbase[v].back() + kWarps - 1) / kWarps);
+        b->grid[v] = std::min(need, resident_blocks(kern[v], b->dev));
+    }
+    if (e != cudaSuccess) {
+        p2p_boxes_destroy(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+cudaError_t p2p_boxes_launch(const P2PBoxes *b, cudaStream_t s)
+{
+    if (b->nbox[0])
+        k_p2p_boxes<0><<<b->grid[0], kWarps * 32, 0, s>>>(b->boxes[0], b->base[0], b->nbox[0]);
+    if (b->nbox[1])
+        k_p2p_boxes<1><<<b->grid[1], kWarps * 32, 0, s>>>(b->boxes[1], b->base[1], b->nbox[1]);
+    if (b->nbox[2])
+        k_p2p_boxes<2><<<b->grid[2], kWarps * 32, 0, s>>>(b->boxes[2], b->base[2], b->nbox[2]);
+    if (b->nbox[3])
+        k_p2p_boxes<3><<<b->grid[3], kWarps * 32, 0, s>>>(b->boxes[3], b->base[3], b->nbox[3]);
+    return cudaGetLastError();
+}
+
+int p2p_boxes_launches(const P2PBoxes *b)
+{
+    int k = 0;
+    for (int v = 0; v < 4; ++v)
+        k += b->nbox[v] ? 1 : 0;
+    return k;
+}
+
+void p2p_boxes_destroy(P2PBoxes *b)
+{
+    if (!b)
+        return;
+    for (int v = 0; v < 4; ++v) {
+        if (b->boxes[v])
+            cudaFree(b->boxes[v]);
+        if (b->base[v])
+            cudaFree(b->base[v]);
+    }
+    delete b;
 }
 
 }  // namespace ewg

@@ -107,6 +107,7 @@ _SIGS = [
     ("ewald_batch_get_params", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ewald_params)]),
     ("ewald_batch_plan", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     ("ewald_batch_apply", ctypes.c_int, [_P, _P]),
+    ("ewald_batch_launch_counts", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("ewald_batch_destroy", None, [_P]),
     ("ewald_server_create", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
     ("ewald_server_submit", ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
@@ -346,6 +347,12 @@ class Batch:
 
         s = stream if stream is not None else torch.cuda.current_stream()
         _check(load().ewald_batch_apply(self.handle, s.cuda_stream), "ewald_batch_apply")
+
+    def launch_counts(self):
+        k, f = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().ewald_batch_launch_counts(self.handle, ctypes.byref(k), ctypes.byref(f)),
+               "ewald_batch_launch_counts")
+        return k.value, f.value
 
 
 def _device_view(ptr: int, shape):

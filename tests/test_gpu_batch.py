@@ -113,3 +113,20 @@ def test_autotune_picks_a_candidate_and_caches():
     assert ms > 0 and q.est_err <= 0.3e-6 * (1 + 1e-12)
     q2, ms2 = ewald.ewald_autotune(8000, 1.0, 1e-6, F32)
     assert (q2.M, q2.tile, ms2) == (q.M, q.tile, ms)
+
+
+def test_batch_near_field_is_one_launch_per_variant(batch):
+    b, N, tol, data = batch
+    k, f = b.launch_counts()
+    per_box = [ewald.ewald_launch_counts(_plan(b, i)) for i in range(len(N))]
+    variants = {(b.params(i).near_ds, b.params(i).near_f64, b.params(i).tol < 1e-6) for i in range(len(N))}
+    assert f == sum(pf for _, pf in per_box)
+    assert k == sum(pk - 1 for pk, _ in per_box) + len(variants)
+
+
+def _plan(b, i):
+    import ctypes
+
+    h = ctypes.c_void_p()
+    ewald._check(ewald.load().ewald_batch_plan(b.handle, int(i), ctypes.byref(h)), "ewald_batch_plan")
+    return h.value

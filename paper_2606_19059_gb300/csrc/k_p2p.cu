@@ -202,16 +202,18 @@ __device__ __forceinline__ void pair_f32(float dx, float dy, float dz, const flo
     }
 }
 
-// Bulk form without branches, for two pairs in flight per lane: every
-// candidate runs the same instructions and the result is selected -- in range
-// (0 < r2 <= rc2): the kernel term; r2 = 0: the removed far part of the skipped
-// pair; beyond rc: nothing.  Returns the contribution.
-__device__ __forceinline__ float3 pair_f32_bulk(float dx, float dy, float dz, const float3 &f,
-                                                const F32Const &k)
+// Bulk form without branches, for two pairs in flight per lane: every source
+// the bit walk yields runs the same instructions.  Returns the pair's term.  In
+// range (0 < r2 <= rc2): the kernel term.  r2 = 0: the far part of the skipped
+// pair, -selfc f (r2 + 1e-30 keeps 1/r finite there, and d = 0 zeroes the
+// r (r.f) part).  Beyond rc (what passes the FP16 test's margin, and the dummy
+// entries): r2 is replaced by 1e30, for which e^{-xi^2 r^2}, and with it every
+// factor of the term, is exactly 0.
+__device__ __forceinline__ float3 pair_f32_bulk(float dx, float dy, float dz, float fx, float fy,
+                                                float fz, const F32Const &k)
 {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const bool in = r2 <= k.rc2 && r2 > 0.0f;
-    const float r2s = in ? r2 : 1.0f;  // keeps the arithmetic finite off range
+    const float r2s = r2 <= k.rc2 ? r2 + 1e-30f : 1e30f;
     const float rinv = rsqrtf(r2s);
     const float x = k.xi * (r2s * rinv);
     const float E = fast_ex2(r2s * k.nxi2log2e);
@@ -220,14 +222,13 @@ __device__ __forceinline__ float3 pair_f32_bulk(float dx, float dy, float dz, co
 #pragma unroll
     for (int q = ERFCX_F32_N - 2; q >= 0; --q)
         p = fmaf(p, tt, c_erfcx32[q]);
-    const float A = (E * (tt * p)) * rinv;  // e^{-x^2} erfcx(x) / r
+    const float Ar = (tt * p) * rinv;  // erfcx(x) / r: A = E Ar
     const float B = k.c2 * E;
-    const float amb = A - B, apb = A + B;
-    const float rf = fmaf(dx, f.x, fmaf(dy, f.y, dz * f.z));
-    const float co = apb * rf * (rinv * rinv);
-    const float sc = r2 == 0.0f ? -k.selfc : 0.0f;
-    return make_float3(in ? fmaf(amb, f.x, co * dx) : sc * f.x, in ? fmaf(amb, f.y, co * dy) : sc * f.y,
-                       in ? fmaf(amb, f.z, co * dz) : sc * f.z);
+    const float amb = r2 == 0.0f ? -k.selfc : fmaf(E, Ar, -B);
+    const float apb = fmaf(E, Ar, B);
+    const float rf = fmaf(dx, fx, fmaf(dy, fy, dz * fz));
+    const float co = (apb * rf) * (rinv * rinv);
+    return make_float3(fmaf(amb, fx, co * dx), fmaf(amb, fy, co * dy), fmaf(amb, fz, co * dz));
 }
 
 __device__ __forceinline__ int wrap(int i, int n)
@@ -408,12 +409,11 @@ constexpr int kT32 = 64;
 
 // FP16x2 phase 1 over one 64-source tile: each shared load brings sources k
 // and k + 32, one FP16x2 distance test covers both, and one AND-OR files the
-// two results.  Word w of the mask holds slot pairs 16 w .. 16 w + 15: bit b < 16
-// is source 16 w + b, bit 16 + b is source 32 + 16 w + b (half_slot inverts
-// this).  Coordinates are cell-local with |value| <= 3, so FP16 keeps their
-// differences to ~2^-10.
-__device__ __forceinline__ unsigned long long phase1_half(const uint4 *sh, __half2 tx, __half2 ty,
-                                                          __half2 tz, __half2 lim)
+// two results.  Word w (0, 1) gets bit b < 16 for source 16 w + b and bit
+// 16 + b for source 32 + 16 w + b.  Coordinates are cell-local with |value| <= 3,
+// so FP16 keeps their differences to ~2^-10.
+__device__ __forceinline__ void phase1_words(const uint4 *sh, __half2 tx, __half2 ty, __half2 tz,
+                                             __half2 lim, unsigned &w0, unsigned &w1)
 {
     unsigned acc[2] = {0u, 0u};
 #pragma unroll
@@ -425,14 +425,61 @@ __device__ __forceinline__ unsigned long long phase1_half(const uint4 *sh, __hal
         const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
         acc[k >> 4] |= __hle2_mask(r2, lim) & ((1u << (k & 15)) | (1u << (16 + (k & 15))));
     }
-    return ((unsigned long long)acc[1] << 32) | acc[0];
+    w0 = acc[0];
+    w1 = acc[1];
 }
 
-// Tile slot of bit position p (0..63) of a phase1_half mask.
-__device__ __forceinline__ int half_slot(int p)
+// Highest set bit of w (-1 for w = 0), and w with bit b cleared (w itself for
+// b = -1: PTX clamps the shift count, so 1 << b is then 0).
+__device__ __forceinline__ int bfind(unsigned w)
 {
-    return ((p >> 5) << 4) + (p & 15) + ((p & 16) << 1);
+    int b;
+    asm("bfind.u32 %0, %1;" : "=r"(b) : "r"(w));
+    return b;
 }
+__device__ __forceinline__ unsigned clear_bit(unsigned w, int b)
+{
+    unsigned m;
+    asm("shl.b32 %0, %1, %2;" : "=r"(m) : "r"(1u), "r"(b));
+    return w ^ m;
+}
+
+// FP32 ring layout: the two staged tiles are four groups of 33 entries, group
+// g = 2 slot + w for word w of the slot's masks: entry 33 g is a dummy source
+// (far away, zero force: its term is exactly 0), entries 33 g + 1 + b the
+// sources of bit b.
+constexpr int kGrp = 33;
+
+// A lane's in-range bits of the staged tiles as a queue of 32-bit words in pop
+// order; w0 is being popped and g is its group.  pop() shifts the queue by a
+// word when w0 is used up (a zero enters at the back), then takes w0's highest
+// bit -- or the group's dummy when w0 is empty -- so a pop costs a few selects
+// and one bit search whatever the mask.
+struct BitQueue {
+    unsigned w0, w1, w2, w3;
+    int g;
+    __device__ __forceinline__ void shift_if(bool e)
+    {
+        w0 = e ? w1 : w0;
+        w1 = e ? w2 : w1;
+        w2 = e ? w3 : w2;
+        w3 = e ? 0u : w3;
+        g = e ? ((g + 1) & 3) : g;
+    }
+    __device__ __forceinline__ int pop()
+    {
+        shift_if(w0 == 0u);
+        const int b = bfind(w0);
+        w0 = clear_bit(w0, b);
+        return kGrp * g + 1 + b;
+    }
+    // in-range sources of the cursor's tile still queued (the cursor is on the
+    // tile's first word when g is even)
+    __device__ __forceinline__ int pending() const
+    {
+        return __popc(w0) + ((g & 1) ? 0 : __popc(w1));
+    }
+};
 
 // Next set bit of the 128-bit mask (m0 first), without divergent branches.
 __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long long &m1)
@@ -446,15 +493,16 @@ __device__ __forceinline__ int next_bit(unsigned long long &m0, unsigned long lo
     return k;
 }
 
-// FP32 ring: per slot, sa = (hi + colleague offset, lo.x), sb = (lo.y, lo.z,
-// f.x, f.y), sc = f.z -- 36 bytes a source, read by phase 2 -- and the FP16
-// copy of the positions read by phase 1.
+// FP32 ring entries (groups as above): sa = (hi + colleague offset, lo.x),
+// sb = (lo.y, lo.z, f.x, f.y), sc = f.z -- 36 bytes a source, read by phase 2 --
+// and per slot the FP16 copy of the positions read by phase 1.
 struct TileF32 {
-    float4 sa[2][kT32];
-    float4 sb[2][kT32];
-    float sc[2][kT32];
+    float4 sa[4 * kGrp];
+    float4 sb[4 * kGrp];
+    float sc[4 * kGrp];
     uint4 sh[2][kT32 / 2];
 };
+
 // FP64 tile of 128 sources: positions (hi + colleague offset, length units)
 // and forces as packed double triples, and the FP16 copy of the positions in
 // cell units for phase 1 (sources k and k + 64 per entry).
@@ -537,9 +585,10 @@ __device__ __forceinline__ void unpack_rec(const float4 &A, const float4 &B, flo
 
 // Stage tile `tile` of the warp's stream (strided: elements tile, tile +
 // ntile, ...) into ring slot `slot`; each lane stages sources lane and
-// lane + 32 and packs their FP16 copy.  Tiles are staged in order, so a lane's
-// element q is its previous one plus 1: sg[h] follows its segment with at most
-// one step (segments are never empty), the binary search only for tile 0.
+// lane + 32, at the entries of their phase-1 bits, and packs their FP16 copy.
+// Tiles are staged in order, so a lane's element q is its previous one plus 1:
+// sg[h] follows its segment with at most one step (segments are never empty),
+// the binary search only for tile 0.
 __device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg, int slot,
                                           int tile, int ntile, int total, int lane, int (&sg)[2])
 {
@@ -560,9 +609,10 @@ __device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg,
             unpack_rec(A, B, hi, lo, f);
             // exact: integer colleague offsets, hi on a 2^-20 lattice
             hp[h] = make_float3(hi.x + (float)dx, hi.y + (float)dy, hi.z + (float)dz);
-            ws.tile.sa[slot][k] = make_float4(hp[h].x, hp[h].y, hp[h].z, lo.x);
-            ws.tile.sb[slot][k] = make_float4(lo.y, lo.z, f.x, f.y);
-            ws.tile.sc[slot][k] = f.z;
+            const int e = kGrp * (2 * slot + (lane >> 4)) + 1 + (lane & 15) + 16 * h;
+            ws.tile.sa[e] = make_float4(hp[h].x, hp[h].y, hp[h].z, lo.x);
+            ws.tile.sb[e] = make_float4(lo.y, lo.z, f.x, f.y);
+            ws.tile.sc[e] = f.z;
         } else {
             hp[h] = make_float3(kFarHalf, kFarHalf, kFarHalf);
         }
@@ -574,8 +624,11 @@ __device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg,
                                         *(const unsigned *)&hz, 0u);
 }
 
-// KAHAN: compensated partial sums, flushed into FP64 totals at every ring step.
-// One work item (a chunk of <= 32 targets of one cell) by one warp.
+// One work item (a chunk of <= 32 targets of one cell) by one warp.  Rounds
+// over the tiles: round o runs until every lane has evaluated its in-range
+// sources of tile o -- the busiest lane's count, known up front -- while lanes
+// done early go on into tile o + 1; then tile o + 2 takes tile o's slot.
+// KAHAN: compensated partial sums, flushed into FP64 totals every round.
 template <bool KAHAN>
 __device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &kc, float inv_cell,
                                              int item, WsF32 &ws, int lane)
@@ -608,57 +661,48 @@ __device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &k
     const int ntile = (total + kT32 - 1) / kT32;
     const __half2 tx = __float2half2_rn(th.x), ty = __float2half2_rn(th.y),
                   tz = __float2half2_rn(th.z), lim = __float2half2_rn(kc.rc2_half);
-    // ring: mA = this lane's remaining in-range bits of tile o (slot o & 1),
-    // mB those of tile o + 1 (slot (o + 1) & 1); inactive lanes keep both 0
-    unsigned long long mA = 0ull, mB = 0ull;
+    if (lane < 4) {  // the groups' dummy sources
+        ws.tile.sa[kGrp * lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+        ws.tile.sb[kGrp * lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ws.tile.sc[kGrp * lane] = 0.f;
+    }
     int sg[2] = {0, 0};
     for (int tt = 0; tt < 2 && tt < ntile; ++tt)
         stage_f32(a, ws, nseg, tt, tt, ntile, total, lane, sg);
     __syncwarp();
+    BitQueue q = {0u, 0u, 0u, 0u, 0};  // inactive lanes: empty throughout
     if (active) {
         if (ntile > 0)
-            mA = phase1_half(ws.tile.sh[0], tx, ty, tz, lim);
+            phase1_words(ws.tile.sh[0], tx, ty, tz, lim, q.w0, q.w1);
         if (ntile > 1)
-            mB = phase1_half(ws.tile.sh[1], tx, ty, tz, lim);
+            phase1_words(ws.tile.sh[1], tx, ty, tz, lim, q.w2, q.w3);
     }
     Tot ux = 0, uy = 0, uz = 0;
     for (int o = 0; o < ntile; ++o) {
+        const int need = (int)__reduce_max_sync(0xffffffffu, (unsigned)q.pending());
         typename std::conditional<KAHAN, KSum, float>::type px{}, py{}, pz{};
-        // until every lane has finished tile o; a lane done with it goes on
-        // with tile o + 1, a lane done with both waits
         if constexpr (KAHAN) {
-            while (__any_sync(0xffffffffu, mA != 0ull)) {
-                if (mA | mB) {
-                    const int p = next_bit(mA, mB);
-                    const int slot = (o + (p >> 6)) & 1, k = half_slot(p & 63);
-                    const float4 s = ws.tile.sa[slot][k], b = ws.tile.sb[slot][k];
-                    // d = (hi diff, exact) + (lo diff)
-                    pair_f32<KAHAN>((th.x - s.x) + (tl.x - s.w), (th.y - s.y) + (tl.y - b.x),
-                                    (th.z - s.z) + (tl.z - b.y),
-                                    make_float3(b.z, b.w, ws.tile.sc[slot][k]), kc, px, py, pz);
-                }
+            for (int it = 0; it < need; ++it) {
+                const int e = q.pop();
+                const float4 s = ws.tile.sa[e], b = ws.tile.sb[e];
+                // d = (hi diff, exact) + (lo diff)
+                pair_f32<KAHAN>((th.x - s.x) + (tl.x - s.w), (th.y - s.y) + (tl.y - b.x),
+                                (th.z - s.z) + (tl.z - b.y), make_float3(b.z, b.w, ws.tile.sc[e]),
+                                kc, px, py, pz);
             }
         } else {
-            // two pairs per iteration: independent chains for the scheduler;
-            // a lane with one pair left evaluates a far dummy as its second
-            while (__any_sync(0xffffffffu, mA != 0ull)) {
-                float3 d[2], fv[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    d[u] = make_float3(1e3f, 0.f, 0.f);
-                    fv[u] = make_float3(0.f, 0.f, 0.f);
-                    if (mA | mB) {
-                        const int p = next_bit(mA, mB);
-                        const int slot = (o + (p >> 6)) & 1, k = half_slot(p & 63);
-                        const float4 s = ws.tile.sa[slot][k], b = ws.tile.sb[slot][k];
-                        // d = (hi diff, exact) + (lo diff)
-                        d[u] = make_float3((th.x - s.x) + (tl.x - s.w), (th.y - s.y) + (tl.y - b.x),
-                                           (th.z - s.z) + (tl.z - b.y));
-                        fv[u] = make_float3(b.z, b.w, ws.tile.sc[slot][k]);
-                    }
-                }
-                const float3 c0 = pair_f32_bulk(d[0].x, d[0].y, d[0].z, fv[0], kc);
-                const float3 c1 = pair_f32_bulk(d[1].x, d[1].y, d[1].z, fv[1], kc);
+            // two pairs per iteration: independent chains for the scheduler
+            for (int it = 0; it < (need + 1) >> 1; ++it) {
+                const int e0 = q.pop(), e1 = q.pop();
+                const float4 s0 = ws.tile.sa[e0], b0 = ws.tile.sb[e0];
+                const float4 s1 = ws.tile.sa[e1], b1 = ws.tile.sb[e1];
+                const float f0 = ws.tile.sc[e0], f1 = ws.tile.sc[e1];
+                const float3 c0 = pair_f32_bulk((th.x - s0.x) + (tl.x - s0.w), (th.y - s0.y) + (tl.y - b0.x),
+                                                (th.z - s0.z) + (tl.z - b0.y), b0.z, b0.w, f0, kc);
+                const float3 c1 = pair_f32_bulk((th.x - s1.x) + (tl.x - s1.w), (th.y - s1.y) + (tl.y - b1.x),
+                                                (th.z - s1.z) + (tl.z - b1.y), b1.z, b1.w, f1, kc);
+                // the two terms summed first: one rounding at the partial sum's
+                // size per two pairs
                 px += c0.x + c1.x;
                 py += c0.y + c1.y;
                 pz += c0.z + c1.z;
@@ -673,15 +717,22 @@ __device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &k
             uy += py;
             uz += pz;
         }
-        // slot o & 1 is free: stage tile o + 2 there
-        mA = mB;
-        mB = 0ull;
-        if (o + 2 < ntile) {
+        // every lane is past tile o: drop its used-up words, which leaves the
+        // cursor in tile o + 1
+        q.shift_if((q.g >> 1) == (o & 1));
+        q.shift_if((q.g >> 1) == (o & 1));
+        if (o + 2 < ntile) {  // slot o & 1 is free: tile o + 2 goes there
             __syncwarp();
             stage_f32(a, ws, nseg, o & 1, o + 2, ntile, total, lane, sg);
             __syncwarp();
+            unsigned c0 = 0u, c1 = 0u;
             if (active)
-                mB = phase1_half(ws.tile.sh[o & 1], tx, ty, tz, lim);
+                phase1_words(ws.tile.sh[o & 1], tx, ty, tz, lim, c0, c1);
+            // queue its words behind tile o + 1's
+            const bool odd = q.g & 1;
+            q.w1 = odd ? c0 : q.w1;
+            q.w2 = odd ? c1 : c0;
+            q.w3 = odd ? 0u : c1;
         }
     }
     if (active) {
@@ -692,6 +743,7 @@ __device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &k
         un[3 * i + 2] = (float)(uz * inv_cell);
     }
 }
+
 
 template <bool KAHAN>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p_f32(P2PArgs a, F32Const kc, float inv_cell)

@@ -132,7 +132,7 @@ void free_plan(ewald_plan_s *p)
     void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
                     p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec, p->nflo,
                     p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
-                    p->err, p->hx, p->hf, p->hu, p->fftwork};
+                    p->err, p->hx, p->hf, p->hu, p->fftwork, p->wts};
     for (void *b : bufs)
         dfree(p, b);
     if (p->own_grid_g2p && p->grid_g2p)
@@ -173,6 +173,8 @@ ewald_status make_plan(ewald_plan_s *p)
     p->near64 = q.near_f64 != 0;
     p->near_ds = q.near_ds != 0;
     p->fft64 = q.fft_f64 != 0;
+    // the double-single grid kernels go with the double-single near field
+    p->grid_ds = p->near_ds && grid_ds_supported(g.P, g.T, g.M);
 
     double werr = 0;
     EW_ST(fit_window(g.P, q.poly_deg, &p->wpoly, &werr));
@@ -209,8 +211,13 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_CUDA(dalloc(p, &p->uf, 3 * rs * N));
     EW_CUDA(dalloc(p, &p->grid, 3 * fs * (size_t)g.nreal));
     // G2P reads the grid in its own precision: an FP32 copy when the FFT is
-    // FP64 and the kernels FP32 (the rounding G2P would apply on each read)
-    if (!p->near64 && p->fft64) {
+    // FP64 and the kernels FP32 (the rounding G2P would apply on each read),
+    // a double-single copy for the double-single kernels
+    if (p->grid_ds) {
+        EW_CUDA(dalloc(p, &p->wts, 4 * 3 * 2 * (size_t)ds_window_stride(g.P) * N));
+        EW_CUDA(dalloc(p, &p->grid_g2p, 2 * 3 * 4 * (size_t)g.nreal));
+        p->own_grid_g2p = true;
+    } else if (!p->near64 && p->fft64) {
         EW_CUDA(dalloc(p, &p->grid_g2p, 3 * 4 * (size_t)g.nreal));
         p->own_grid_g2p = true;
     } else {
@@ -297,12 +304,15 @@ ewald_status bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t
     a.T = g.T;
     a.nt = g.nt;
     a.f64 = p->near64;
+    a.tf_ds = p->grid_ds;
     EW_CUDA(cudaMemsetAsync(p->cntn, 0, 4 * (size_t)g.nkeys, s));
     EW_CUDA(cudaMemsetAsync(p->cntt, 0, 4 * (size_t)g.ntiles, s));
     EW_CUDA(launch_bin_keys(p, a, s));
     EW_CUDA(launch_scan2(p->cntn, p->startn, g.nkeys, p->cntt, p->startt, g.ntiles, s));
     EW_CUDA(launch_bin_scatter(p, a, s));
     EW_CUDA(launch_cell_items(p, s));
+    if (p->grid_ds)
+        EW_CUDA(launch_window_ds(p, s));
     p->positions_valid = true;
     return EWALD_OK;
 }
@@ -333,6 +343,17 @@ ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s)
     return EWALD_OK;
 }
 
+// G2P's input from an FP64 grid (the plan's after the inverse FFT, or a
+// caller's): the FP32 or double-single copy when the plan keeps one.
+cudaError_t prep_g2p_grid(ewald_plan_s *p, const void *grid64, cudaStream_t s)
+{
+    if (p->grid_ds)
+        return launch_grid_split((const double *)grid64, (float *)p->grid_g2p, 3 * p->g.nreal, s);
+    if (p->own_grid_g2p)
+        return launch_grid_convert(grid64, true, p->grid_g2p, false, 3 * p->g.nreal, s);
+    return cudaSuccess;
+}
+
 enum Mode { FULL, NEAR_ONLY, FAR_ONLY };
 
 // Everything after binning.  FULL writes u = near + far - self; NEAR_ONLY /
@@ -359,8 +380,7 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         EW_CUDA(launch_p2g(p, s));
         rec(p, 2, s);
         EW_ST(fgc(p, 8.0 * kPi * h3 / M3, s));
-        if (p->own_grid_g2p)
-            EW_CUDA(launch_grid_convert(p->grid, true, p->grid_g2p, false, 3 * p->g.nreal, s));
+        EW_CUDA(prep_g2p_grid(p, p->grid, s));
         EW_CUDA(launch_g2p(p, p->grid_g2p, 1.0, s));
         rec(p, 6, s);
     }
@@ -395,8 +415,7 @@ ewald_status plan_far(ewald_plan_s *p, cudaStream_t s)
     const double h3 = p->g.h * p->g.h * p->g.h;
     EW_CUDA(launch_p2g(p, s));
     EW_ST(fgc(p, 8.0 * kPi * h3 / (double)p->g.nreal, s));
-    if (p->own_grid_g2p)
-        EW_CUDA(launch_grid_convert(p->grid, true, p->grid_g2p, false, 3 * p->g.nreal, s));
+    EW_CUDA(prep_g2p_grid(p, p->grid, s));
     EW_CUDA(launch_g2p(p, p->grid_g2p, 1.0, s));
     return EWALD_OK;
 }
@@ -584,8 +603,11 @@ ewald_status ewald_interp(ewald_plan_t plan, const double *x, const double *grid
     EW_ST(bin(plan, x, nullptr, s));
     const double h3 = plan->g.h * plan->g.h * plan->g.h;
     const void *g = grid;
-    if (!plan->near64) {  // the FP32 kernels read an FP32 copy of the caller's grid
-        EW_CUDA(launch_grid_convert(grid, true, plan->grid_g2p, false, 3 * plan->g.nreal, s));
+    if (!plan->near64 || plan->grid_ds) {  // FP32 kernels: an FP32 copy of the caller's grid
+        if (plan->grid_ds)
+            EW_CUDA(launch_grid_split(grid, (float *)plan->grid_g2p, 3 * plan->g.nreal, s));
+        else
+            EW_CUDA(launch_grid_convert(grid, true, plan->grid_g2p, false, 3 * plan->g.nreal, s));
         g = plan->grid_g2p;
     }
     EW_CUDA(launch_g2p(plan, g, h3, s));
@@ -665,8 +687,9 @@ ewald_status ewald_launch_counts(ewald_plan_t plan, int32_t *kernels, int32_t *f
     if (!plan || !kernels || !ffts)
         return EWALD_EINVAL;
     // bin_keys, both scans (one launch), scatter, cell items with their scan,
-    // p2p, p2g, scale, g2p, sum -- plus the FP32 copy of an FP64 grid
-    *kernels = 9 + (plan->own_grid_g2p ? 1 : 0);
+    // p2p, p2g, scale, g2p, sum -- plus the FP32 or double-single copy of an
+    // FP64 grid, and the double-single window weights
+    *kernels = 9 + (plan->own_grid_g2p ? 1 : 0) + (plan->grid_ds ? 1 : 0);
     *ffts = 2;
     return EWALD_OK;
 }

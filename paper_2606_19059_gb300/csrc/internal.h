@@ -23,6 +23,40 @@ constexpr int kMaxP = 16;           // largest window support the kernels implem
 constexpr int kMaxDeg = 20;         // largest window polynomial degree
 constexpr int kNumEvents = 10;
 constexpr int kP2PChunk = 32;       // targets per P2P work item (one warp)
+constexpr int kGridDsMinP = 8;      // smallest support of the double-single grid kernels
+
+// double-single window weights: bins of one axis padded to a multiple of 4
+inline int ds_window_stride(int P) { return (P + 3) & ~3; }
+
+// Bank dealing for G2P from a staged grid block with row stride S (floats):
+// lane b takes the (y, x) pairs of a P x P face with (S y + x) mod 32 = b, one
+// per round.  g2p_rounds: the rounds that takes (the most pairs on one bank);
+// g2p_stride: the S, from T + P - 1 (T = 8) rounded up to 4, with the fewest.
+__host__ __device__ constexpr int g2p_rounds(int P, int S)
+{
+    int mx = 0;
+    for (int b = 0; b < 32; ++b) {
+        int cnt = 0;
+        for (int yy = 0; yy < P; ++yy)
+            if (((b - S * yy) & 31) < P)
+                ++cnt;
+        mx = cnt > mx ? cnt : mx;
+    }
+    return mx;
+}
+__host__ __device__ constexpr int g2p_stride(int P)
+{
+    const int s0 = (P + 7 + 3) & ~3;  // T + P - 1 rounded up to 4
+    int best = s0, br = g2p_rounds(P, s0);
+    for (int S = s0 + 4; S <= s0 + 8; S += 4) {
+        const int r = g2p_rounds(P, S);
+        if (r < br) {
+            best = S;
+            br = r;
+        }
+    }
+    return best;
+}
 
 // Window polynomial for one precision: coef[l * (deg+1) + k] is the z^k
 // coefficient of bin l, z = 2 delta - 1 (Sec. 2.2 / Sec. 4, Horner form).
@@ -70,6 +104,8 @@ struct ewald_plan_s {
     void *nrec = nullptr;                         // FP32: near-sorted 32-byte source records
     void *nflo = nullptr;                         // double-single: force low parts (float4)
     bool near_ds = false;                         // P2P in double-single arithmetic
+    bool grid_ds = false;                         // P2G / G2P in double-single arithmetic
+    void *wts = nullptr;                          // double-single window weights (tile order)
     void *tdat = nullptr, *tfrc = nullptr;        // tile-sorted window data / forces
     void *un = nullptr, *uf = nullptr;            // near / far results, user order
     void *grid = nullptr;                         // 3 M^3 real
@@ -113,6 +149,7 @@ struct BinArgs {
     double L, cell, h;
     int nc, M, P, T, nt;
     bool f64;            // sorted arrays in FP64 (else FP32)
+    bool tf_ds;          // tile-sorted forces as double-single pairs of float4
 };
 cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s);
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s);
@@ -125,8 +162,8 @@ cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);
-// G2P from a grid in the kernels' precision (FP64 when near64, else FP32);
-// the sum is multiplied by `scale`.
+// G2P from a grid in the kernels' precision (FP64 when near64, else FP32; the
+// double-single planes for grid_ds plans); the sum is multiplied by `scale`.
 cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s);
 cudaError_t load_p2p_constants();
 // The near field of many plans: one persistent launch per P2P variant over
@@ -149,5 +186,14 @@ cudaError_t launch_perturb_forces(double *f, int64_t N, double a, uint32_t step,
                                   double *sums, cudaStream_t s);
 cudaError_t launch_grid_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t n,
                                 cudaStream_t s);
+// Double-single grid kernels (k_grid_ds.cu): usable for tile 8, kGridDsMinP <=
+// P <= kMaxP, M <= 1024.  The window weights of the tile-sorted points (after
+// binning), P2G into the FP64 grid, G2P from a double-single copy of it (3 M^3
+// h values then 3 M^3 l values), and that copy.
+bool grid_ds_supported(int P, int T, int M);
+cudaError_t launch_window_ds(ewald_plan_s *p, cudaStream_t s);
+cudaError_t launch_p2g_ds(ewald_plan_s *p, cudaStream_t s);
+cudaError_t launch_g2p_ds(ewald_plan_s *p, const float *gds, double scale, cudaStream_t s);
+cudaError_t launch_grid_split(const double *src, float *dst, int64_t n, cudaStream_t s);
 
 }  // namespace ewg

@@ -24,8 +24,17 @@ struct KeyArgs {
     int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
     const int32_t *startn, *startt;
     void *npos, *nfrc, *nrec, *nflo, *tdat, *tfrc;
+    bool tf_ds;
     int *err;
 };
+
+// tile-sorted force of a double-single grid: (h.x, h.y, h.z, 0), (l.x, l.y, l.z, 0)
+__device__ __forceinline__ void store_force_ds(float4 *t, double fx, double fy, double fz)
+{
+    const float hx = (float)fx, hy = (float)fy, hz = (float)fz;
+    t[0] = make_float4(hx, hy, hz, 0.f);
+    t[1] = make_float4((float)(fx - (double)hx), (float)(fy - (double)hy), (float)(fz - (double)hz), 0.f);
+}
 
 struct Bin {
     double xw[3];      // wrapped position in [0, L)
@@ -158,7 +167,10 @@ __global__ void k_bin_scatter(KeyArgs k)
         fv.w = (R)0;
         if (!k.nrec)
             ((R4 *)k.nfrc)[pn] = fv;
-        tfrc[pt] = fv;
+        if (k.tf_ds)
+            store_force_ds((float4 *)k.tfrc + 2 * (int64_t)pt, k.f[3 * i], k.f[3 * i + 1], k.f[3 * i + 2]);
+        else
+            tfrc[pt] = fv;
     }
 }
 
@@ -168,7 +180,7 @@ __global__ void k_bin_scatter(KeyArgs k)
 template <typename R, typename R4>
 __global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__restrict__ permn,
                                 const int32_t *__restrict__ permt, dvec4 *nfrc, float *nrec,
-                                float4 *nflo, R4 *tfrc, int64_t N)
+                                float4 *nflo, R4 *tfrc, bool tf_ds, int64_t N)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N)
@@ -190,6 +202,10 @@ __global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__r
         a.z = f[3 * in + 2];
         a.w = 0.0;
         nfrc[p] = a;
+    }
+    if (tf_ds) {
+        store_force_ds((float4 *)tfrc + 2 * p, f[3 * it], f[3 * it + 1], f[3 * it + 2]);
+        return;
     }
     R4 b;
     b.x = (R)f[3 * it];
@@ -323,6 +339,7 @@ KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
     k.nflo = p->nflo;
     k.tdat = p->tdat;
     k.tfrc = p->tfrc;
+    k.tf_ds = a.tf_ds;
     k.err = p->err;
     return k;
 }
@@ -367,10 +384,10 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
     if (p->near64)
         k_gather_forces<double, dvec4><<<blocks_for(p->N, 256), 256, 0, s>>>(
             f, p->permn, p->permt, (dvec4 *)p->nfrc, (float *)p->nrec, (float4 *)p->nflo,
-            (dvec4 *)p->tfrc, p->N);
+            (dvec4 *)p->tfrc, p->grid_ds, p->N);
     else
         k_gather_forces<float, float4><<<blocks_for(p->N, 256), 256, 0, s>>>(
-            f, p->permn, p->permt, nullptr, (float *)p->nrec, nullptr, (float4 *)p->tfrc, p->N);
+            f, p->permn, p->permt, nullptr, (float *)p->nrec, nullptr, (float4 *)p->tfrc, false, p->N);
     return cudaGetLastError();
 }
 

@@ -461,32 +461,6 @@ __global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
 // whatever the point's offset (a shift moves all banks alike).  The number of
 // rounds is the largest number of pairs on one bank; S is picked to keep it
 // near ceil(P^2 / 32).
-__host__ __device__ constexpr int g2p_rounds(int P, int S)
-{
-    int mx = 0;
-    for (int b = 0; b < 32; ++b) {
-        int cnt = 0;
-        for (int yy = 0; yy < P; ++yy)
-            if (((b - S * yy) & 31) < P)
-                ++cnt;
-        mx = cnt > mx ? cnt : mx;
-    }
-    return mx;
-}
-__host__ __device__ constexpr int g2p_stride(int P)
-{
-    const int s0 = (P + 7 + 3) & ~3;  // T + P - 1 rounded up to 4
-    int best = s0, br = g2p_rounds(P, s0);
-    for (int S = s0 + 4; S <= s0 + 8; S += 4) {
-        const int r = g2p_rounds(P, S);
-        if (r < br) {
-            best = S;
-            br = r;
-        }
-    }
-    return best;
-}
-
 constexpr int kG2PPlanarThreads = 512;  // 16 warps: two blocks fill an SM's 64 warps by half
 
 template <int PC>
@@ -892,13 +866,18 @@ cudaError_t dispatch_p2g(ewald_plan_s *p, const GridArgs &a, cudaStream_t s)
 
 cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s)
 {
+    if (p->grid_ds)
+        return launch_p2g_ds(p, s);
     GridArgs a = grid_args(p);
     return p->g.T == 8 ? dispatch_p2g<8>(p, a, s) : dispatch_p2g<4>(p, a, s);
 }
 
-// G2P from a grid in the kernels' precision (FP64 when near64, else FP32).
+// G2P from a grid in the kernels' precision (FP64 when near64, else FP32;
+// double-single h and l planes for the double-single kernels).
 cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s)
 {
+    if (p->grid_ds)
+        return launch_g2p_ds(p, (const float *)grid, scale, s);
     GridArgs a = grid_args(p);
     a.grid = const_cast<void *>(grid);
     a.scale = scale;

@@ -1,0 +1,528 @@
+// k_grid_ds.cu -- steps a2 (P2G, eq. (p2g)) and a6 (G2P, eq. (g2p)) in
+// double-single arithmetic, for the FP32-bulk plans below tol 1e-7 (whose near
+// field is double-single too): on this GPU the FP64 pipe runs at a small
+// fraction of the FP32 one, and FP64 grid kernels were most of such an apply.
+//
+// A double-single value is h + l, two FP32 numbers (~44 significant bits).
+// Product x y: p = x.h y.h and its error term e = fma(x.h, y.h, -p) + x.h y.l
+// + x.l y.h (x.l y.l lies below 2^-44 relative), left unnormalised.  Sum
+// a += p + e: Knuth's two-sum of a.h + p, whose rounding error goes into a.l
+// together with e.  a.l is never renormalised: it stays within a few ulp of the
+// largest partial sum, so a.h + a.l carries ~2^-44 of it.  The _rn intrinsics
+// keep the compiler from contracting the products into the sums.
+//
+// Window weights (Sec. 2.2, Sec. 4): evaluated once per binning for every
+// point by FP64 Horner on the window polynomial and stored split h + l, the P
+// bins of an axis padded to PW (a multiple of 4).  P2G reads them for every
+// tile a point touches, G2P once per point.
+//
+// P2G: owner-computes over tiles of 8^3 grid points, as the FP32 kernel of
+// k_grid.cu, with one thread per (y, z) row of the tile holding the row's 8 x 3
+// double-single sums.  A warp holds the 32 rows of one z-half, so the z-halves
+// and x-halves a point's support misses are skipped warp-uniformly.  The sums
+// are rounded to FP64 on the store (cuFFT's input).
+//
+// G2P: from a double-single copy of the FP64 grid (h = fl32(v), l = fl32(v -
+// h)), staged per tile and component in shared memory (below).
+#include "internal.h"
+
+namespace ewg {
+namespace {
+
+__device__ __forceinline__ void ds_prod(float xh, float xl, float yh, float yl, float &p, float &e)
+{
+    p = __fmul_rn(xh, yh);
+    e = fmaf(xl, yh, fmaf(xh, yl, fmaf(xh, yh, -p)));
+}
+
+// (ah, al) += p + e
+__device__ __forceinline__ void ds_acc(float &ah, float &al, float p, float e)
+{
+    const float s = __fadd_rn(ah, p);
+    const float bb = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(err, e));
+}
+
+// (ah, al) += x y
+__device__ __forceinline__ void ds_fma(float &ah, float &al, float xh, float xl, float yh, float yl)
+{
+    float p, e;
+    ds_prod(xh, xl, yh, yl, p, e);
+    ds_acc(ah, al, p, e);
+}
+
+__device__ __forceinline__ void ds_split(double v, float &h, float &l)
+{
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - (double)h);
+}
+
+__device__ __forceinline__ double ds_join(float h, float l) { return (double)h + (double)l; }
+
+struct GridDsArgs {
+    const dvec4 *tdat;       // tile-sorted (delta, packed anchor offsets)
+    const float4 *tfrc;      // tile-sorted forces: [2 p] = h, [2 p + 1] = l (w unused)
+    const float *wts;        // window weights [p][axis][h: PW | l: PW]
+    const int32_t *startt, *permt;
+    int P, PW, M, nt, KT;
+    double *grid;            // P2G output, 3 M^3 FP64
+    const float *gds;        // G2P input: 3 M^3 h values, then 3 M^3 l values
+    double *uf;              // G2P output, user order
+    double scale;            // G2P: multiplies the sum
+};
+
+// ---- window weights ---------------------------------------------------------
+__global__ void k_window_ds(const dvec4 *__restrict__ tdat, const double *__restrict__ coef,
+                            float *__restrict__ wts, int64_t N, int P, int deg, int PW)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (point, axis)
+    if (q >= 3 * N)
+        return;
+    const int64_t p = q / 3;
+    const int d = (int)(q - 3 * p);
+    const dvec4 td = tdat[p];
+    const double z = 2.0 * (d == 0 ? td.x : (d == 1 ? td.y : td.z)) - 1.0;
+    float *w = wts + q * 2 * PW;
+    const int nd = deg + 1;
+    for (int j = 0; j < PW; ++j) {
+        float h = 0.f, l = 0.f;
+        if (j < P) {
+            const double *c = coef + j * nd;
+            double v = c[deg];
+            for (int k = deg - 1; k >= 0; --k)
+                v = fma(v, z, c[k]);
+            ds_split(v, h, l);
+        }
+        w[j] = h;
+        w[PW + j] = l;
+    }
+}
+
+// ---- P2G --------------------------------------------------------------------
+constexpr int kT = 8, kH = 4;
+constexpr int kP2GDsThreads = 256;
+constexpr int kDsRows = kT * kT;                      // one thread per (y, z) row
+constexpr int kDsSlices = kP2GDsThreads / kDsRows;    // point slices
+constexpr int kDsMaxSeg = 27;                         // (KT + 1)^3, KT = ceil((P-1)/8) <= 2
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+template <int PC>
+__global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
+{
+    constexpr int NT = kP2GDsThreads, B = NT, T = kT, H = kH, SL = kDsSlices, T3 = T * T * T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *wr = (float *)smem;                  // [6][B][T] rows: x h, x l, y h, y l, z h, z l
+    float4 *sf = (float4 *)(wr + 6 * B * T);    // [B][2] force h, l
+    __shared__ int soff[B], sidx[B];
+    __shared__ int seg_start[kDsMaxSeg], seg_pref[kDsMaxSeg + 1];
+    __shared__ int scount;
+
+    const int nt = a.nt, KT = a.KT, side = KT + 1, nseg = side * side * side;
+    const int tile = blockIdx.x;
+    const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
+    // the neighbour tiles (dz, dy, dx) in [-KT, 0]^3 whose anchors can reach
+    // this tile: their point ranges, concatenated
+    if (threadIdx.x < 32) {
+        const int s = threadIdx.x;
+        int len = 0;
+        if (s < nseg) {
+            const int dx = s % side - KT, dy = (s / side) % side - KT, dz = s / (side * side) - KT;
+            const int nb = (wrapi(tz + dz, nt) * nt + wrapi(ty + dy, nt)) * nt + wrapi(tx + dx, nt);
+            seg_start[s] = a.startt[nb];
+            len = a.startt[nb + 1] - a.startt[nb];
+        }
+        int v = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (s >= o)
+                v += u;
+        }
+        if (s < nseg)
+            seg_pref[s + 1] = v;
+        if (s == 0)
+            seg_pref[0] = 0;
+    }
+    const int row = threadIdx.x % kDsRows, slice = threadIdx.x / kDsRows;
+    const int y = row % T, z = row / T;
+    const bool zlo = z < H;  // warp-uniform
+    float ah[T][3], al[T][3];
+#pragma unroll
+    for (int x = 0; x < T; ++x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            ah[x][c] = al[x][c] = 0.f;
+    __syncthreads();
+    const int total = seg_pref[nseg];
+
+    for (int base = 0; base < total; base += B) {
+        if (threadIdx.x == 0)
+            scount = 0;
+        __syncthreads();
+        // (A) one thread per candidate: does its support reach the tile?
+        const int q = base + threadIdx.x;
+        bool keep = false;
+        int j = 0, ox = 0, oy = 0, oz = 0;
+        if (q < total) {
+            int lo = 0, hi = nseg;  // seg_pref[lo] <= q < seg_pref[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (seg_pref[mid] <= q)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int s = lo;
+            j = seg_start[s] + (q - seg_pref[s]);
+            const int dx = s % side - KT, dy = (s / side) % side - KT, dz = s / (side * side) - KT;
+            const int packed = (int)a.tdat[j].w;
+            ox = dx * T + (packed & 15);
+            oy = dy * T + ((packed >> 4) & 15);
+            oz = dz * T + ((packed >> 8) & 15);
+            keep = ox + PC > 0 && ox < T && oy + PC > 0 && oy < T && oz + PC > 0 && oz < T;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        int wbase = 0;
+        if ((threadIdx.x & 31) == 0 && ball)
+            wbase = atomicAdd(&scount, __popc(ball));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (keep) {
+            const int k = wbase + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u));
+            // offsets lie in (-P, T): bias by 32 into 6-bit fields
+            soff[k] = (ox + 32) | ((oy + 32) << 6) | ((oz + 32) << 12);
+            sidx[k] = j;
+        }
+        __syncthreads();
+        const int n = scount;
+        // (B) one thread per (point, axis): the axis' weights on the tile's 8
+        // grid lines (zero off the support), h and l rows; and the force
+        for (int w = threadIdx.x; w < 3 * n; w += NT) {
+            const int k = w / 3, d = w - 3 * k;
+            const int o = ((soff[k] >> (6 * d)) & 63) - 32;
+            const int jj = sidx[k];
+            const float *src = a.wts + ((int64_t)jj * 3 + d) * 2 * a.PW;
+            float hv[T], lv[T];
+#pragma unroll
+            for (int x = 0; x < T; ++x) {
+                const int l = x - o;
+                const bool in = l >= 0 && l < PC;
+                const int li = in ? l : 0;
+                hv[x] = in ? __ldg(src + li) : 0.f;
+                lv[x] = in ? __ldg(src + a.PW + li) : 0.f;
+            }
+            float4 *dh = (float4 *)(wr + ((2 * d) * B + k) * T);
+            float4 *dl = (float4 *)(wr + ((2 * d + 1) * B + k) * T);
+            dh[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            dh[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+            dl[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+            dl[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
+            if (d == 0) {
+                sf[2 * k] = a.tfrc[2 * (int64_t)jj];
+                sf[2 * k + 1] = a.tfrc[2 * (int64_t)jj + 1];
+            }
+        }
+        __syncthreads();
+        // (C) the slice's points into this thread's row
+        for (int k = slice; k < n; k += SL) {
+            const int so = soff[k];
+            const int okx = (so & 63) - 32, okz = ((so >> 12) & 63) - 32;
+            if (zlo ? okz >= H : okz + PC <= H)
+                continue;  // the warp's z-half is off the support
+            const bool hx0 = okx < H, hx1 = okx + PC > H;
+            float gp, ge;  // wy wz
+            ds_prod(wr[(2 * B + k) * T + y], wr[(3 * B + k) * T + y], wr[(4 * B + k) * T + z],
+                    wr[(5 * B + k) * T + z], gp, ge);
+            const float4 fh = sf[2 * k], fl = sf[2 * k + 1];
+            float g[3][2];  // wy wz f
+            ds_prod(gp, ge, fh.x, fl.x, g[0][0], g[0][1]);
+            ds_prod(gp, ge, fh.y, fl.y, g[1][0], g[1][1]);
+            ds_prod(gp, ge, fh.z, fl.z, g[2][0], g[2][1]);
+            const float *wxh = wr + (0 * B + k) * T, *wxl = wr + (1 * B + k) * T;
+            if (hx0) {
+#pragma unroll
+                for (int x = 0; x < H; ++x) {
+                    const float h = wxh[x], l = wxl[x];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        ds_fma(ah[x][c], al[x][c], h, l, g[c][0], g[c][1]);
+                }
+            }
+            if (hx1) {
+#pragma unroll
+                for (int x = H; x < T; ++x) {
+                    const float h = wxh[x], l = wxl[x];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        ds_fma(ah[x][c], al[x][c], h, l, g[c][0], g[c][1]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // sum the slices (reusing the staging area) and store the tile in FP64
+    float2 *red = (float2 *)smem;  // [SL][3][T^3]
+#pragma unroll
+    for (int x = 0; x < T; ++x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            red[(slice * 3 + c) * T3 + (z * T + y) * T + x] = make_float2(ah[x][c], al[x][c]);
+    __syncthreads();
+    const int M = a.M;
+    const int64_t M3 = (int64_t)M * M * M;
+    for (int o = threadIdx.x; o < 3 * T3; o += NT) {
+        const int c = o / T3, r = o - c * T3;
+        float sh = 0.f, sl = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < SL; ++qq) {
+            const float2 v = red[(qq * 3 + c) * T3 + r];
+            ds_acc(sh, sl, v.x, v.y);
+        }
+        const int x = r % T, yy = (r / T) % T, zz = r / (T * T);
+        const int64_t gx = tx * T + x, gy = ty * T + yy, gz = tz * T + zz;
+        a.grid[c * M3 + (gz * M + gy) * M + gx] = ds_join(sh, sl);
+    }
+}
+
+constexpr size_t kP2GDsStage = sizeof(float) * 6 * kP2GDsThreads * kT + sizeof(float4) * 2 * kP2GDsThreads;
+constexpr size_t kP2GDsRed = sizeof(float2) * kDsSlices * 3 * kT * kT * kT;
+constexpr size_t kP2GDsSmem = kP2GDsStage > kP2GDsRed ? kP2GDsStage : kP2GDsRed;
+
+// ---- G2P --------------------------------------------------------------------
+// One block per tile of anchors, one pass per component: the block stages the
+// component's (T + P - 1)^3 h and l values its points can touch (16-byte
+// asynchronous copies into rows of stride S; M a multiple of 8 keeps every
+// 4-float chunk on one side of the periodic wrap, M >= P keeps one wrap
+// enough), then one warp per point sums its support: lanes over the P x P
+// (y, x) pairs, dealt by bank (g2p_rounds), each walking its z column with
+// immediate offsets, s = sum_z wz v, then u += wy wx s.
+constexpr int kG2PDsThreads = 256;
+
+template <int PC>
+struct G2PDs {
+    static constexpr int T = kT, RR = T + PC - 1, S = g2p_stride(PC), NR = g2p_rounds(PC, S);
+    static constexpr int NCH = (RR + 3) / 4;  // 16-byte chunks per staged row
+    static constexpr int PLANE = RR * S, VOL = RR * PLANE;
+    static constexpr int NW = kG2PDsThreads / 32;
+    static constexpr size_t smem = sizeof(float) * (2 * (size_t)VOL + NW * 6 * 16) + sizeof(int) * NR * 32;
+};
+
+template <int PC>
+__global__ void __launch_bounds__(kG2PDsThreads, 2) k_g2p_ds(GridDsArgs a)
+{
+    using G = G2PDs<PC>;
+    constexpr int T = G::T, RR = G::RR, S = G::S, NR = G::NR, NCH = G::NCH, PLANE = G::PLANE,
+                  VOL = G::VOL, NW = G::NW;
+    const int tile = blockIdx.x;
+    const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
+    if (s0 == s1)
+        return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *vh = (float *)smem;       // [RR][RR][S] h values of the component
+    float *vl = vh + VOL;            // l values
+    float *wsm = vl + VOL;           // per warp [6][16]: x h, x l, y h, y l, z h, z l
+    int *tab = (int *)(wsm + NW * 6 * 16);  // [NR][32] bank-dealt pairs
+    const int nt = a.nt, M = a.M, PW = a.PW;
+    const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        int r = 0;
+        for (int yy = 0; yy < PC; ++yy) {
+            const int xx = (lane - S * yy) & 31;
+            if (xx < PC)
+                tab[r++ * 32 + lane] = (yy << 8) | xx;
+        }
+        for (; r < NR; ++r)
+            tab[r * 32 + lane] = -1;
+    }
+    const int64_t M2 = (int64_t)M * M, M3 = M2 * M;
+    const unsigned vh_a = (unsigned)__cvta_generic_to_shared(vh);
+    float *w = wsm + warp * 6 * 16;
+    for (int c = 0; c < 3; ++c) {
+        // stage component c: threads over (plane h/l, z, y, chunk)
+        const float *srch = a.gds + c * M3, *srcl = a.gds + (3 + c) * M3;
+        for (int t = threadIdx.x; t < 2 * RR * RR * NCH; t += kG2PDsThreads) {
+            const int half = t / (RR * RR * NCH), r = t - half * (RR * RR * NCH);
+            const int row = r / NCH, ch = r - row * NCH;
+            const int z = row / RR, y = row - z * RR;
+            int gx = tx * T + 4 * ch, gy = ty * T + y, gz = tz * T + z;
+            gx -= gx >= M ? M : 0;
+            gy -= gy >= M ? M : 0;
+            gz -= gz >= M ? M : 0;
+            const float *src = (half ? srcl : srch) + (gz * M2 + (int64_t)gy * M + gx);
+            const unsigned dst = vh_a + 4 * (half * VOL + row * S + 4 * ch);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        // this lane's pairs
+        int roff[NR], ry[NR], rx[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int e = tab[r * 32 + lane];
+            roff[r] = e >= 0 ? (e >> 8) * S + (e & 255) : -1;
+            ry[r] = e >= 0 ? e >> 8 : 0;
+            rx[r] = e >= 0 ? e & 255 : 0;
+        }
+        for (int p = s0 + warp; p < s1; p += NW) {
+            const int packed = (int)a.tdat[p].w;
+            const int ox = packed & 15, oy = (packed >> 4) & 15, oz = (packed >> 8) & 15;
+            const float *wp = a.wts + (int64_t)p * 6 * PW;
+            __syncwarp();
+            for (int q = lane; q < 6 * PC; q += 32) {
+                const int d = q / PC, l = q - d * PC;
+                w[d * 16 + l] = __ldg(wp + d * PW + l);
+            }
+            __syncwarp();
+            float wzh[PC], wzl[PC];
+#pragma unroll
+            for (int k = 0; k < PC; ++k) {
+                wzh[k] = w[4 * 16 + k];
+                wzl[k] = w[5 * 16 + k];
+            }
+            const int base = (oz * RR + oy) * S + ox;
+            float uh = 0.f, ul = 0.f;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (roff[r] >= 0) {
+                    const float *ch = vh + base + roff[r], *cl = vl + base + roff[r];
+                    float sh = 0.f, sl = 0.f;
+#pragma unroll
+                    for (int k = 0; k < PC; ++k)
+                        ds_fma(sh, sl, wzh[k], wzl[k], ch[k * PLANE], cl[k * PLANE]);
+                    float yp, ye;  // wy wx
+                    ds_prod(w[2 * 16 + ry[r]], w[3 * 16 + ry[r]], w[rx[r]], w[16 + rx[r]], yp, ye);
+                    float pp, pe;
+                    ds_prod(yp, ye, sh, sl, pp, pe);
+                    ds_acc(uh, ul, pp, pe);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, uh, o);
+                const float ol = __shfl_xor_sync(0xffffffffu, ul, o);
+                ds_acc(uh, ul, oh, ol);
+            }
+            if (lane == 0)
+                a.uf[3 * a.permt[p] + c] = ds_join(uh, ul) * a.scale;
+        }
+        __syncthreads();  // before the next component overwrites the block
+    }
+}
+
+// FP64 grid -> double-single planes (all h values, then all l values)
+__global__ void k_grid_split(const double *__restrict__ src, float *__restrict__ dst, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    float h, l;
+    ds_split(src[i], h, l);
+    dst[i] = h;
+    dst[n + i] = l;
+}
+
+GridDsArgs ds_args(ewald_plan_s *p)
+{
+    GridDsArgs a;
+    a.tdat = (const dvec4 *)p->tdat;
+    a.tfrc = (const float4 *)p->tfrc;
+    a.wts = (const float *)p->wts;
+    a.startt = p->startt;
+    a.permt = p->permt;
+    a.P = p->g.P;
+    a.PW = ds_window_stride(p->g.P);
+    a.M = p->g.M;
+    a.nt = p->g.nt;
+    a.KT = p->g.KT;
+    a.grid = (double *)p->grid;
+    a.gds = nullptr;
+    a.uf = (double *)p->uf;
+    a.scale = 1.0;
+    return a;
+}
+
+template <int PC>
+cudaError_t run_p2g_ds(const GridDsArgs &a, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (a.P != PC)
+            return run_p2g_ds<PC + 1>(a, s);
+        const cudaError_t e = cudaFuncSetAttribute(k_p2g_ds<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kP2GDsSmem);
+        if (e != cudaSuccess)
+            return e;
+        k_p2g_ds<PC><<<a.nt * a.nt * a.nt, kP2GDsThreads, kP2GDsSmem, s>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+template <int PC>
+cudaError_t run_g2p_ds(const GridDsArgs &a, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (a.P != PC)
+            return run_g2p_ds<PC + 1>(a, s);
+        constexpr size_t sm = G2PDs<PC>::smem;
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_g2p_ds<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess)
+            return e;
+        k_g2p_ds<PC><<<a.nt * a.nt * a.nt, kG2PDsThreads, sm, s>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+bool grid_ds_supported(int P, int T, int M)
+{
+    return T == kT && P >= kGridDsMinP && P <= kMaxP && M <= 1024;
+}
+
+cudaError_t launch_window_ds(ewald_plan_s *p, cudaStream_t s)
+{
+    const int64_t n = 3 * p->N;
+    if (n == 0)
+        return cudaSuccess;
+    k_window_ds<<<blocks_for(n, 256), 256, 0, s>>>((const dvec4 *)p->tdat, (const double *)p->wcoef_dev,
+                                                  (float *)p->wts, p->N, p->g.P, p->wpoly.deg,
+                                                  ds_window_stride(p->g.P));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2g_ds(ewald_plan_s *p, cudaStream_t s)
+{
+    return run_p2g_ds<kGridDsMinP>(ds_args(p), s);
+}
+
+cudaError_t launch_g2p_ds(ewald_plan_s *p, const float *gds, double scale, cudaStream_t s)
+{
+    GridDsArgs a = ds_args(p);
+    a.gds = gds;
+    a.scale = scale;
+    return run_g2p_ds<kGridDsMinP>(a, s);
+}
+
+cudaError_t launch_grid_split(const double *src, float *dst, int64_t n, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_grid_split<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace ewg

@@ -167,6 +167,7 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
     a.T = g.T;
     a.nt = g.nt;
     a.f64 = pl.near64;
+    a.tf_ds = false;
     // clear what the binning accumulates into (the array keeps the last call's contents)
     if (cudaMemsetAsync(pl.cntn, 0, 4 * (size_t)g.nkeys, s) != cudaSuccess ||
         cudaMemsetAsync(pl.cntt, 0, 4 * (size_t)g.ntiles, s) != cudaSuccess ||

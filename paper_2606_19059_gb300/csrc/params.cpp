@@ -235,14 +235,14 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
             double cand = (double)N * (double)N * 27.0 * cellv;       // P2P candidates
             double inr = (double)N * (double)N * 4.18879 * r * r * r;  // in-range pairs
             double m3 = (double)m * m * m;
-            // stage weights calibrated on a GB300 (N = 1e5, M = 128, P = 12:
-            // P2P 0.45, P2G + G2P 0.35, FFTs 0.084 ms in FP32); FP64 kernels
-            // cost 36x (P2P), 15x (P2G, G2P) and 16x (FFT) their FP32 time --
-            // the FP64 pipe is 1/64 of the FP32 one -- and the double-single
-            // P2P ~12x, so FP64 plans move work from the near field to the grid
-            const double wn = p.near_ds ? 12.0 : (p.near_f64 ? 36.0 : 1.0);
-            const double wg = p.near_f64 ? 15.0 : 1.0;
-            const double wf = p.fft_f64 ? 16.0 : 1.0;
+            // stage weights fitted to GB300 stage times (FP32: N = 1e5, M =
+            // 128, P = 12: P2P 0.34, P2G + G2P 0.35, FFTs + CNV 0.10 ms;
+            // double-single and FP64: N = 1e4 .. 1e6 over a range of M): one
+            // unit ~5.3e-11 ms.  The FP64 pipe is 1/64 of the FP32 one, so
+            // FP64 plans move work from the near field to the grid.
+            const double wn = p.near_ds ? 5.0 : (p.near_f64 ? 48.0 : 1.0);
+            const double wg = p.near_ds ? 3.65 : (p.near_f64 ? 13.6 : 1.0);
+            const double wf = p.fft_f64 ? 26.0 : 1.55;
             const double halo = pow((8.0 + P - 1.0) / 8.0, 3);      // staged block / tile
             double cost = wn * (10.0 * cand + 50.0 * inr)              // P2P
                           + wg * 28.0 * (double)N * P * P * P          // P2G + G2P per point
@@ -334,6 +334,12 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
     fb += 3 * m3 * (p.fft_f64 ? 8 : 4);                // real grid
     fb += 3 * mc * (p.fft_f64 ? 16 : 8);               // half spectrum
     fb += 2 * 3 * m3 * (p.fft_f64 ? 8 : 4);            // cuFFT work areas (estimate)
+    if (!p.near_f64 && p.fft_f64)
+        fb += 3 * m3 * 4;                              // FP32 copy of the grid for G2P
+    if (p.near_ds && grid_ds_supported(P, T, M)) {
+        fb += N * 3 * 2 * ds_window_stride(P) * 4;     // double-single window weights
+        fb += 2 * 3 * m3 * 4;                          // double-single copy of the grid
+    }
     p.footprint_bytes = fb;
     *out = p;
     return EWALD_OK;

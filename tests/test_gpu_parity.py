@@ -347,3 +347,65 @@ def test_f32_bulk_double_single_full_apply(kind, N, tol):
     ref = oracle.ewald(x, f, 1.0, targets=idx)
     l2, mx = errs(u[idx], ref)
     assert l2 <= tol and mx <= tol, (l2, mx)
+
+
+# ------------------------------------------------- double-single grid ------
+
+def _ds_plan(N, M, P):
+    # FP32 bulk below tol 1e-7: P2G / G2P in double-single arithmetic too (8^3
+    # tiles, P >= 8), with their extra kernels: window weights, grid copy
+    p = plan(N, 1.0, 1e-8, F32, M=M, P=P)
+    assert p.params.near_ds == 1 and p.params.tile == 8
+    assert ewald.ewald_launch_counts(p.handle) == (11, 2)
+    return p
+
+
+@pytest.mark.parametrize("P,M", [(12, 32), (16, 40), (8, 24)])
+def test_spread_double_single_matches_exact_window(P, M):
+    x, f = workloads.make("uniform", 400, seed=108)
+    p = _ds_plan(400, M, P)
+    g = host(p.spread(dev(x), dev(f)))
+    ref = spectral.spread(x, f, 1.0, M, P)
+    _, werr = ewald.ewald_window_eval(P, p.params.poly_deg, np.zeros(1))
+    bound = 3 * werr * np.abs(f).max() + 1e-13 * np.abs(ref).max()
+    assert np.abs(g - ref).max() <= bound, (np.abs(g - ref).max(), bound)
+
+
+@pytest.mark.parametrize("P,M", [(9, 32), (14, 48)])
+def test_interp_double_single_matches_exact_window(P, M):
+    rng = np.random.default_rng(109)
+    x = workloads.uniform(rng, 300)
+    v = rng.standard_normal((3, M, M, M))
+    p = _ds_plan(300, M, P)
+    u = host(p.interp(dev(x), dev(v)))
+    ref = spectral.gather(x, v, 1.0, M, P)
+    _, werr = ewald.ewald_window_eval(P, p.params.poly_deg, np.zeros(1))
+    h3 = (1.0 / M) ** 3
+    bound = 3 * werr * P ** 3 * h3 * np.abs(v).max() + 1e-12 * np.abs(ref).max()
+    assert np.abs(u - ref).max() <= bound, (np.abs(u - ref).max(), bound)
+
+
+def test_spread_interp_adjoint_double_single():
+    rng = np.random.default_rng(110)
+    M, P = 32, 13
+    x = workloads.uniform(rng, 700)
+    f = workloads.forces(rng, 700, zero_mean=False)
+    v = rng.standard_normal((3, M, M, M))
+    p = _ds_plan(700, M, P)
+    g = host(p.spread(dev(x), dev(f)))
+    u = host(p.interp(dev(x), dev(v)))
+    h3 = (1.0 / M) ** 3
+    lhs, rhs = h3 * np.sum(g * v), np.sum(f * u)
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+def test_double_single_grid_matches_fp64_grid():
+    # the same plan parameters with FP64 grid kernels (F64) and double-single
+    # ones (F32 bulk): far fields agree to double-single rounding
+    x, f = workloads.make("clustered", 6000, seed=111)
+    p = _ds_plan(6000, 48, 14)
+    q = plan(6000, 1.0, 1e-8, F64, M=48, P=14, xi=p.params.xi, rc=p.params.rc)
+    a = host(p.far_field(dev(x), dev(f)))
+    b = host(q.far_field(dev(x), dev(f)))
+    l2, mx = errs(a, b)
+    assert l2 <= 1e-11 and mx <= 1e-11, (l2, mx)

@@ -272,13 +272,13 @@ def run_batch(args, rank):
                         "FP32 bulk, autotuned (measured) per half-octave of N; inputs larger than L2"}
 
 
-def run_serving(args, rank):
+def run_serving(args, rank, rate_hz):
     """Poisson arrivals of mobility requests (N = 10^U(3, log10 4e6), uniform or
     clustered 50/50, tol in {1e-4, 1e-6, 1e-8}), 20 applies each with perturbed
     forces, through the continuous-batching server; host arrays in and out."""
     from paper_2606_19059_gb300 import ewald, workloads
 
-    stream = workloads.serving_stream(args.serve_requests, seed=1005 + rank, rate_hz=args.serve_rate)
+    stream = workloads.serving_stream(args.serve_requests, seed=1005 + rank, rate_hz=rate_hz)
     data = [workloads.served_box(r["kind"], r["N"], r["seed"]) for r in stream]
     srv = ewald.Server(200 << 30, max_active=8)
     t0 = time.perf_counter()
@@ -293,7 +293,7 @@ def run_serving(args, rank):
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
-    return {"requests": len(stream), "rate_hz": args.serve_rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+    return {"requests": len(stream), "rate_hz": rate_hz, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "value": st["throughput"], "unit": UNIT, "completed": st["completed"],
             "failed": st["failed"], "wall_s": wall, "peak_footprint_gb": st["peak_footprint_bytes"] / 1e9,
             "particle_applies": st["particle_applies"],
@@ -362,7 +362,9 @@ def main():
     ap.add_argument("--batch-boxes", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-rates", default="2,8",
+                    help="Poisson arrival rates (requests/s), comma-separated: the first is the reported "
+                         "serving run, the list the sweep toward saturation")
     ap.add_argument("--only-f32", action="store_true",
                     help="time the FP32-bulk applies only and print a short line (for ncu captures)")
     args = ap.parse_args()
@@ -440,6 +442,16 @@ def main():
         roof["kernel"] = "k_p2p<float> (P2P near field)"
         roof["peak_source"] = (f"FP32 pipe: {N_SM} SMs x {FP32_LANES} lanes x 2 flop x {sm_mhz:.0f} MHz "
                                f"({peak_src} sm_max_mhz)")
+        try:  # measured FMA-pipe peaks, beside the derived one
+            from paper_2606_19059_gb300 import ewald
+
+            p32, p64 = ewald.ewald_probe_fma_peaks(0)
+            roof["peak_probe"] = {"fp32_tflops": p32, "fp64_tflops": p64,
+                                  "frac_of_fp32_probe": p2p_tf / p32,
+                                  "method": "8 independent FMA chains per thread, 4 x 256 threads per SM, "
+                                            "best of 3 timed launches (ewald_probe_fma_peaks)"}
+        except Exception as exc:  # pragma: no cover - reported, not fatal
+            roof["peak_probe"] = {"error": str(exc)}
         roof["algorithmic"] = {"inrange_pairs": inr, "candidate_pairs": cand,
                                "flops_per_inrange": FP32_FLOPS_PER_INRANGE,
                                "flops_per_candidate": FLOPS_PER_CANDIDATE, "flops_per_launch": p2p_flops}
@@ -467,7 +479,11 @@ def main():
         if not args.no_batch:
             line["batched"] = run_batch(args, rank)
         if not args.no_serve:
-            line["serving"] = run_serving(args, rank)
+            rates = [float(r) for r in args.serve_rates.split(",") if r]
+            runs = [run_serving(args, rank, r) for r in rates]
+            line["serving"] = dict(runs[0])
+            line["serving"]["sweep"] = [{k: r[k] for k in ("rate_hz", "p50_ms", "p99_ms", "value", "wall_s",
+                                                         "completed")} for r in runs]
         if not args.no_cpu_baseline:
             cb = cpu_baseline(args.cpu_targets)
             cb.pop("seconds", None)

@@ -361,6 +361,14 @@ ewald_status ewald_window_hat(int32_t P, double h, int64_t n, const double *k, d
 ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *prm, const double *x,
                                       const double *f, double *u, void *stream);
 
+/* Measured FMA-pipe peaks of `device` (TFLOP/s, an FMA counted as 2 flops):
+ * 8 independent FP32 (then FP64) FMA chains per thread, 4 blocks of 256
+ * threads per SM, the best of three timed launches after a warm-up (~10 ms of
+ * device time in all).  The ALU-bound stages' roofline denominators besides
+ * the peak derived from unit counts and clocks; there is no library measure
+ * of these pipes.  Synchronises the device.  EWALD_ECUDA on a CUDA error. */
+ewald_status ewald_probe_fma_peaks(int32_t device, double *fp32_tflops, double *fp64_tflops);
+
 #ifdef __cplusplus
 }
 #endif

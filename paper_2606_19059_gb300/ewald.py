@@ -94,6 +94,8 @@ _SIGS = [
                                          ctypes.POINTER(ctypes.c_double)]),
     ("ewald_window_hat", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _P, _P]),
     ("ewald_near_field_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ewald_params), _P, _P, _P, _P]),
+    ("ewald_probe_fma_peaks", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]),
     ("ewald_autotune_candidates", ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                  ctypes.c_int32, ctypes.POINTER(ewald_params),
                                                  ctypes.POINTER(ctypes.c_int32)]),
@@ -259,6 +261,13 @@ def ewald_window_hat(P: int, h: float, k):
     _check(load().ewald_window_hat(int(P), float(h), k.size, k.ctypes.data, w.ctypes.data),
            "ewald_window_hat")
     return w
+
+
+def ewald_probe_fma_peaks(device: int = 0):
+    """Measured (FP32, FP64) FMA-pipe peaks of `device` in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().ewald_probe_fma_peaks(int(device), ctypes.byref(a), ctypes.byref(b)), "ewald_probe_fma_peaks")
+    return a.value, b.value
 
 
 def ewald_near_field_noalloc(N: int, params: ewald_params, x_ptr, f_ptr, u_ptr, stream=0):

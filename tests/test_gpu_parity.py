@@ -409,3 +409,11 @@ def test_double_single_grid_matches_fp64_grid():
     b = host(q.far_field(dev(x), dev(f)))
     l2, mx = errs(a, b)
     assert l2 <= 1e-11 and mx <= 1e-11, (l2, mx)
+
+
+def test_fma_probe_reports_plausible_peaks():
+    # FP32 FMA pipe of a GB300: 152 SMs x 128 lanes x 2 flops x ~2 GHz ~ 80
+    # TFLOP/s; FP64 a small fraction of it
+    p32, p64 = ewald.ewald_probe_fma_peaks(0)
+    assert 5.0 < p32 < 500.0, p32
+    assert 0.05 < p64 < p32 / 4, (p32, p64)

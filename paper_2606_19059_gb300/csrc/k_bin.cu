@@ -19,7 +19,7 @@ namespace {
 struct KeyArgs {
     const double *x, *f;
     int64_t N;
-    double L, inv_cell, cell, inv_h, half_odd;
+    double L, inv_L, inv_cell, cell, inv_h, half_odd;
     int nc, M, T, nt, ceilP2;
     int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
     const int32_t *startn, *startt;
@@ -55,9 +55,13 @@ __device__ __forceinline__ Bin compute_bin(const KeyArgs &k, int64_t i)
             b.bad = true;
             v = 0.0;
         }
-        v -= k.L * floor(v / k.L);
-        if (v >= k.L)
-            v -= k.L;
+        // wrap into [0, L) (positions already inside skip it: FP64 runs at a
+        // small fraction of the FP32 rate here, and binning is FP64-bound)
+        if (v < 0.0 || v >= k.L) {
+            v -= k.L * floor(v * k.inv_L);
+            if (v >= k.L)
+                v -= k.L;
+        }
         if (v < 0.0)
             v = 0.0;
         b.xw[d] = v;
@@ -314,6 +318,7 @@ KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
     k.f = a.f;
     k.N = a.N;
     k.L = a.L;
+    k.inv_L = 1.0 / a.L;
     k.cell = a.cell;
     k.inv_cell = 1.0 / a.cell;
     k.inv_h = 1.0 / a.h;

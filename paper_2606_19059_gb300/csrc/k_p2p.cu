@@ -419,6 +419,17 @@ __device__ __forceinline__ int locate(const WS &ws, int nseg, int q, int &dx, in
 
 constexpr float kFarHalf = 64.0f;  // FP16 dummy source: r^2 ~ 1e4, finite and never within rc
 
+// FP16 phase-1 threshold on r^2 (cell units, cutoff rcc <= 2 cells).  In FP16
+// a source coordinate (|v| < 4) is off by <= 2^-10, a target's (in [0, 1)) by
+// <= 2^-12, their difference adds <= 2^-11: |d| by <= 1.8e-3 per component,
+// r^2 by <= 6e-3 rcc; the FP16 sums add <= 3e-3 and rounding the threshold
+// <= 2e-3.  0.006 (rcc + rcc^2) + 0.002 covers that twice over, so no pair
+// within rc fails the test; the few beyond it that pass are dropped later.
+__host__ __device__ inline float half_threshold(double rcc)
+{
+    return (float)(rcc * rcc + 0.006 * (rcc + rcc * rcc) + 0.002);
+}
+
 // FP32 kernel: tiles of 64 sources, two staged at once (a ring of two slots),
 // so a lane may run up to one tile ahead of the slowest lane of its warp: the
 // warp's pair iterations then follow the busiest lane's total over the whole
@@ -804,7 +815,7 @@ __device__ __forceinline__ void p2p_f64_item(const P2PArgs &a, int item, WsF64 &
     // phase 1 in FP16 on cell-unit coordinates (the FP32 kernel's bound)
     const __half2 tx = __float2half2_rn((float)(xt.x * inv_cell)), ty = __float2half2_rn((float)(xt.y * inv_cell)),
                   tz = __float2half2_rn((float)(xt.z * inv_cell)),
-                  lim = __float2half2_rn((float)(rcc * rcc * 1.03 + 0.01));
+                  lim = __float2half2_rn(half_threshold(rcc));
     double ux = 0.0, uy = 0.0, uz = 0.0;
     for (int tile = 0; tile < ntile; ++tile) {
         const int n = (total - tile + ntile - 1) / ntile;
@@ -1015,94 +1026,130 @@ __device__ __forceinline__ void pair_ds(float dhx, float dhy, float dhz, float d
         acc[c] = ds_add(acc[c], ds_add(ds_mul(amb, f[c]), ds_mul(co, d[c])));
 }
 
-// Double-single tile of 128 sources: sa = (hi + colleague offset, lo.x),
-// sb = (lo.y, lo.z, fh.x, fh.y), sc = (fh.z, fl.x, fl.y, fl.z); FP16 copy for
-// phase 1 as the FP64 kernel.
+// Double-single ring: the FP32 kernel's two 64-source tiles in four groups of
+// 33 entries (entry 0 of a group its dummy): sa = (hi + colleague offset,
+// lo.x), sb = (lo.y, lo.z, fh.x, fh.y), sc = (fh.z, fl.x, fl.y, fl.z); and per
+// slot the FP16 copy of the positions for phase 1.
 struct TileDS {
-    float4 sa[kTile];
-    float4 sb[kTile];
-    float4 sc[kTile];
-    uint4 sh[kTile / 2];
+    float4 sa[4 * kGrp];
+    float4 sb[4 * kGrp];
+    float4 sc[4 * kGrp];
+    uint4 sh[2][kT32 / 2];
 };
 using WsDS = WarpSmem<TileDS>;
-constexpr int kDSBlocksPerSM = 6;  // shared-memory limited (4 warps x 9.2 KB)
 
-// The warps stride over the work items (the grid holds as many blocks as fit
-// at once): the heavier double-single pairs make a partial second wave costly.
+// Stage tile `tile` of the warp's stream into ring slot `slot` (as stage_f32,
+// with the forces' low parts).
+__device__ __forceinline__ void stage_ds(const P2PArgs &a, WsDS &ws, int nseg, int slot, int tile,
+                                         int ntile, int total, int lane, int (&sg)[2])
+{
+    const float4 *rec = (const float4 *)a.nrec, *flo = (const float4 *)a.nflo;
+    float3 hp[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h, q = tile + k * ntile;
+        if (q < total) {
+            if (tile == 0)
+                sg[h] = seg_of(ws, nseg, q);
+            else if (ws.seg_pref[sg[h] + 1] <= q)
+                ++sg[h];
+            int dx, dy, dz;
+            const int j = seg_element(ws, sg[h], q, dx, dy, dz);
+            float3 hi, lo, f;
+            unpack_rec(rec[2 * j], rec[2 * j + 1], hi, lo, f);
+            const float4 fl = flo[j];
+            hp[h] = make_float3(hi.x + (float)dx, hi.y + (float)dy, hi.z + (float)dz);
+            const int e = kGrp * (2 * slot + (lane >> 4)) + 1 + (lane & 15) + 16 * h;
+            ws.tile.sa[e] = make_float4(hp[h].x, hp[h].y, hp[h].z, lo.x);
+            ws.tile.sb[e] = make_float4(lo.y, lo.z, f.x, f.y);
+            ws.tile.sc[e] = make_float4(f.z, fl.x, fl.y, fl.z);
+        } else {
+            hp[h] = make_float3(kFarHalf, kFarHalf, kFarHalf);
+        }
+    }
+    const __half2 hx = __floats2half2_rn(hp[0].x, hp[1].x);
+    const __half2 hy = __floats2half2_rn(hp[0].y, hp[1].y);
+    const __half2 hz = __floats2half2_rn(hp[0].z, hp[1].z);
+    ws.tile.sh[slot][lane] = make_uint4(*(const unsigned *)&hx, *(const unsigned *)&hy,
+                                        *(const unsigned *)&hz, 0u);
+}
+
+// One work item by one warp: the FP32 kernel's rounds over the ring (the
+// busiest lane's count of in-range sources per round, lanes done early going
+// on into the next tile), one double-single pair per iteration.
 __device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc, int item, WsDS &ws,
                                             int lane)
 {
-    const float4 *rec = (const float4 *)a.nrec, *flo = (const float4 *)a.nflo;
-    {
-        int c, tb, te;
-        if (!find_item(a, item, c, tb, te))
-            return;  // past the last real item: the same for the whole warp
-        const int t = tb + lane;
-        const bool active = t < te;
-        float3 th = make_float3(0.f, 0.f, 0.f), tl = th, fdum;
-        if (active)
-            unpack_rec(rec[2 * t], rec[2 * t + 1], th, tl, fdum);
-        const float3 blo = make_float3(warp_min(active ? th.x : 1e30f), warp_min(active ? th.y : 1e30f),
-                                       warp_min(active ? th.z : 1e30f));
-        const float3 bhi = make_float3(warp_max(active ? th.x : -1e30f),
-                                       warp_max(active ? th.y : -1e30f),
-                                       warp_max(active ? th.z : -1e30f));
-        const int nseg = build_segments(a, c, ws, lane, blo, bhi, 0.5f, kc.rcm);
-        const int total = ws.seg_pref[nseg];
-        const int ntile = (total + kTile - 1) / kTile;
-        const __half2 tx = __float2half2_rn(th.x), ty = __float2half2_rn(th.y),
-                      tz = __float2half2_rn(th.z), lim = __float2half2_rn(kc.rc2_half);
-        dsf acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        for (int tile = 0; tile < ntile; ++tile) {
-#pragma unroll
-            for (int i = 0; i < kTile / 64; ++i) {
-                float3 hp[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = lane + 32 * i + 64 * h, q = tile + k * ntile;
-                    if (q < total) {
-                        int dx, dy, dz;
-                        const int j = locate(ws, nseg, q, dx, dy, dz);
-                        float3 hi, lo, f;
-                        unpack_rec(rec[2 * j], rec[2 * j + 1], hi, lo, f);
-                        const float4 fl = flo[j];
-                        hp[h] = make_float3(hi.x + (float)dx, hi.y + (float)dy, hi.z + (float)dz);
-                        ws.tile.sa[k] = make_float4(hp[h].x, hp[h].y, hp[h].z, lo.x);
-                        ws.tile.sb[k] = make_float4(lo.y, lo.z, f.x, f.y);
-                        ws.tile.sc[k] = make_float4(f.z, fl.x, fl.y, fl.z);
-                    } else {
-                        hp[h] = make_float3(kFarHalf, kFarHalf, kFarHalf);
-                    }
-                }
-                const __half2 hx = __floats2half2_rn(hp[0].x, hp[1].x);
-                const __half2 hy = __floats2half2_rn(hp[0].y, hp[1].y);
-                const __half2 hz = __floats2half2_rn(hp[0].z, hp[1].z);
-                ws.tile.sh[lane + 32 * i] = make_uint4(*(const unsigned *)&hx, *(const unsigned *)&hy,
-                                                       *(const unsigned *)&hz, 0u);
-            }
+    const float4 *rec = (const float4 *)a.nrec;
+    int c, tb, te;
+    if (!find_item(a, item, c, tb, te))
+        return;  // past the last real item: the same for the whole warp
+    const int t = tb + lane;
+    const bool active = t < te;
+    float3 th = make_float3(0.f, 0.f, 0.f), tl = th, fdum;
+    if (active)
+        unpack_rec(rec[2 * t], rec[2 * t + 1], th, tl, fdum);
+    const float3 blo = make_float3(warp_min(active ? th.x : 1e30f), warp_min(active ? th.y : 1e30f),
+                                   warp_min(active ? th.z : 1e30f));
+    const float3 bhi = make_float3(warp_max(active ? th.x : -1e30f), warp_max(active ? th.y : -1e30f),
+                                   warp_max(active ? th.z : -1e30f));
+    const int nseg = build_segments(a, c, ws, lane, blo, bhi, 0.5f, kc.rcm);
+    const int total = ws.seg_pref[nseg];
+    const int ntile = (total + kT32 - 1) / kT32;
+    const __half2 tx = __float2half2_rn(th.x), ty = __float2half2_rn(th.y),
+                  tz = __float2half2_rn(th.z), lim = __float2half2_rn(kc.rc2_half);
+    if (lane < 4) {  // the groups' dummy sources
+        ws.tile.sa[kGrp * lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+        ws.tile.sb[kGrp * lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ws.tile.sc[kGrp * lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int sg[2] = {0, 0};
+    for (int tt = 0; tt < 2 && tt < ntile; ++tt)
+        stage_ds(a, ws, nseg, tt, tt, ntile, total, lane, sg);
+    __syncwarp();
+    BitQueue q = {0u, 0u, 0u, 0u, 0};
+    if (active) {
+        if (ntile > 0)
+            phase1_words(ws.tile.sh[0], tx, ty, tz, lim, q.w0, q.w1);
+        if (ntile > 1)
+            phase1_words(ws.tile.sh[1], tx, ty, tz, lim, q.w2, q.w3);
+    }
+    dsf acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int o = 0; o < ntile; ++o) {
+        const int need = (int)__reduce_max_sync(0xffffffffu, (unsigned)q.pending());
+        for (int it = 0; it < need; ++it) {
+            const int e = q.pop();
+            const float4 sa = ws.tile.sa[e], sb = ws.tile.sb[e], sc = ws.tile.sc[e];
+            pair_ds(th.x - sa.x, th.y - sa.y, th.z - sa.z, tl.x - sa.w, tl.y - sb.x, tl.z - sb.y,
+                    make_float3(sb.z, sb.w, sc.x), make_float3(sc.y, sc.z, sc.w), kc, acc);
+        }
+        q.shift_if((q.g >> 1) == (o & 1));
+        q.shift_if((q.g >> 1) == (o & 1));
+        if (o + 2 < ntile) {
             __syncwarp();
-            unsigned long long m0 = 0ull, m1 = 0ull;
+            stage_ds(a, ws, nseg, o & 1, o + 2, ntile, total, lane, sg);
+            __syncwarp();
+            unsigned c0 = 0u, c1 = 0u;
             if (active)
-                phase1_half_128(ws.tile.sh, tx, ty, tz, lim, m0, m1);
-            while (m0 | m1) {
-                const int k = half_slot_128(next_bit(m0, m1));
-                const float4 sa = ws.tile.sa[k], sb = ws.tile.sb[k], sc = ws.tile.sc[k];
-                pair_ds(th.x - sa.x, th.y - sa.y, th.z - sa.z, tl.x - sa.w, tl.y - sb.x, tl.z - sb.y,
-                        make_float3(sb.z, sb.w, sc.x), make_float3(sc.y, sc.z, sc.w), kc, acc);
-            }
-            __syncwarp();
+                phase1_words(ws.tile.sh[o & 1], tx, ty, tz, lim, c0, c1);
+            const bool odd = q.g & 1;
+            q.w1 = odd ? c0 : q.w1;
+            q.w2 = odd ? c1 : c0;
+            q.w3 = odd ? 0u : c1;
         }
-        if (active) {
-            const int i = a.permn[t];
-            double *un = (double *)a.un;
-            const double inv_cell = 1.0 / a.cell;
-            un[3 * i] = ((double)acc[0].h + (double)acc[0].l) * inv_cell;
-            un[3 * i + 1] = ((double)acc[1].h + (double)acc[1].l) * inv_cell;
-            un[3 * i + 2] = ((double)acc[2].h + (double)acc[2].l) * inv_cell;
-        }
+    }
+    if (active) {
+        const int i = a.permn[t];
+        double *un = (double *)a.un;
+        const double inv_cell = 1.0 / a.cell;
+        un[3 * i] = ((double)acc[0].h + (double)acc[0].l) * inv_cell;
+        un[3 * i + 1] = ((double)acc[1].h + (double)acc[1].l) * inv_cell;
+        un[3 * i + 2] = ((double)acc[2].h + (double)acc[2].l) * inv_cell;
     }
 }
 
+// The warps stride over the work items (the grid holds as many blocks as fit
+// at once): the heavier double-single pairs make a partial second wave costly.
 __global__ void __launch_bounds__(kWarps * 32) k_p2p_ds(P2PArgs a, DSConst kc, int items)
 {
     __shared__ WsDS wsm[kWarps];
@@ -1242,9 +1289,7 @@ F32Const f32_const(const ewald_plan_s *p)
     F32Const kc;
     const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
     kc.rc2 = (float)(rcc * rcc);
-    // phase 1 runs in FP16: coordinates within 3 cells carry <= 2^-10 each,
-    // so |r^2 error| < 0.03 rc^2 + 0.005 below the cutoff (K <= 2)
-    kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
+    kc.rc2_half = half_threshold(rcc);
     kc.rcm = (float)(rcc + 1e-3);  // sub-cell culling reach: |lo| <= 2^-21 fits the margin
     kc.xi = (float)xic;
     const double c = -xic * xic * 1.4426950408889634;  // -xi^2 log2(e), cell units
@@ -1267,7 +1312,7 @@ DSConst ds_const(const ewald_plan_s *p)
     DSConst kc;
     const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
     kc.rc2 = (float)(rcc * rcc);
-    kc.rc2_half = (float)(rcc * rcc * 1.03 + 0.01);
+    kc.rc2_half = half_threshold(rcc);
     kc.rcm = (float)(rcc + 1e-3);
     kc.xi = split(xic);
     kc.xi2 = split(xic * xic);

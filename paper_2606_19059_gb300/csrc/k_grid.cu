@@ -12,9 +12,9 @@
 // (The paper's P2G-hybrid, Algorithm 4, is the prior art: it also keeps the
 // window values in shared memory, but scatters with O(27 N) atomics.)
 // The neighbour tiles' point ranges are concatenated and processed in rounds
-// of 256 points: (A) one thread per point tests overlap with the tile and
-// compacts, (B) one thread per (point, axis, offset) evaluates the window
-// polynomial, (C) threads = (two rows (y, z), (y, z + T/2) of the tile) x
+// of 512 points: (A) two points per thread, each tested for overlap with the
+// tile and compacted, (B) one thread per (point, axis) evaluates the window
+// polynomial's bins, (C) threads = (two rows (y, z), (y, z + T/2) of the tile) x
 // (slice of the point list) accumulate 2 x T values x 3 components in
 // registers, sharing each point's x weights and force between the rows.
 //
@@ -55,6 +55,7 @@ template <> struct Vec4<float> { using T = float4; };
 template <> struct Vec4<double> { using T = dvec4; };
 
 constexpr int kP2GThreads = 256;
+constexpr int kP2GCandidates = 2;  // candidates per thread and round (512 a round)
 constexpr int kMaxSeg = 125;  // (KT+1)^3 with KT <= 4 (T = 4, P = 16)
 
 __device__ __forceinline__ int wrapi(int i, int n)
@@ -74,7 +75,8 @@ __global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(Gri
     constexpr int NT = kP2GThreads;
     constexpr int ROWS = T * T / 2;  // row pairs (y, z), (y, z + T/2)
     constexpr int SL = NT / ROWS;
-    constexpr int B = NT;  // points per round
+    constexpr int CPT = kP2GCandidates;  // candidates per thread and round
+    constexpr int B = CPT * NT;          // points per round
     constexpr int H = T / 2;
     // a warp holds one slice when ROWS is a multiple of 32: per-point tests
     // are then warp-uniform, and the tile halves [0, H), [H, T) in x and z
@@ -146,9 +148,11 @@ __global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(Gri
         if (threadIdx.x == 0)
             scount = 0;
         __syncthreads();
-        // (A) one thread per point: overlap test and compaction (one shared
-        // atomic per warp)
-        const int q = base + threadIdx.x;
+        // (A) CPT candidates per thread: overlap test and compaction (one
+        // shared atomic per warp and candidate)
+#pragma unroll
+        for (int h = 0; h < CPT; ++h) {
+        const int q = base + threadIdx.x + h * NT;
         bool keep = false;
         R4 td;
         int j = 0, ox = 0, oy = 0, oz = 0;
@@ -188,6 +192,7 @@ __global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(Gri
                 fv.w = (R)0;
                 ((R4 *)sf)[k] = fv;
             }
+        }
         }
         __syncthreads();
         const int n = scount;
@@ -797,7 +802,7 @@ GridArgs grid_args(ewald_plan_s *p)
 template <int T, typename R, typename G, int PC>
 cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
 {
-    constexpr int B = kP2GThreads;
+    constexpr int B = kP2GThreads * kP2GCandidates;
     const size_t ncoef = PC > 0 ? (size_t)(a.deg + 1) * ((PC + 3) & ~3) : (size_t)a.P * (a.deg + 1);
     size_t stage = sizeof(R) * ((size_t)B * (3 * T + 7) + ncoef);
     size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * T;

@@ -308,9 +308,8 @@ ewald_status bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t
     EW_CUDA(cudaMemsetAsync(p->cntn, 0, 4 * (size_t)g.nkeys, s));
     EW_CUDA(cudaMemsetAsync(p->cntt, 0, 4 * (size_t)g.ntiles, s));
     EW_CUDA(launch_bin_keys(p, a, s));
-    EW_CUDA(launch_scan2(p->cntn, p->startn, g.nkeys, p->cntt, p->startt, g.ntiles, s));
+    EW_CUDA(launch_bin_scans(p, s));
     EW_CUDA(launch_bin_scatter(p, a, s));
-    EW_CUDA(launch_cell_items(p, s));
     if (p->grid_ds)
         EW_CUDA(launch_window_ds(p, s));
     p->positions_valid = true;
@@ -686,10 +685,10 @@ ewald_status ewald_launch_counts(ewald_plan_t plan, int32_t *kernels, int32_t *f
 {
     if (!plan || !kernels || !ffts)
         return EWALD_EINVAL;
-    // bin_keys, both scans (one launch), scatter, cell items with their scan,
-    // p2p, p2g, scale, g2p, sum -- plus the FP32 or double-single copy of an
-    // FP64 grid, and the double-single window weights
-    *kernels = 9 + (plan->own_grid_g2p ? 1 : 0) + (plan->grid_ds ? 1 : 0);
+    // bin_keys, the scans (one launch), scatter, p2p, p2g, scale, g2p, sum --
+    // plus the FP32 or double-single copy of an FP64 grid, and the
+    // double-single window weights
+    *kernels = 8 + (plan->own_grid_g2p ? 1 : 0) + (plan->grid_ds ? 1 : 0);
     *ffts = 2;
     return EWALD_OK;
 }

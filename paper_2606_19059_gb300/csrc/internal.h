@@ -153,12 +153,12 @@ struct BinArgs {
 };
 cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s);
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s);
-// both scans in one launch (independent arrays)
-cudaError_t launch_scan2(const int32_t *in0, int32_t *out0, int n0, const int32_t *in1, int32_t *out1,
-                         int n1, cudaStream_t s);
+// binning's scans in one launch: sub-cell and tile starts, and the P2P work
+// items per cell with their offsets
+cudaError_t launch_bin_scans(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_bin_scatter(ewald_plan_s *p, const BinArgs &a, cudaStream_t s);
 cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t s);
-cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s);
+cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s);  // the work items alone
 cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);

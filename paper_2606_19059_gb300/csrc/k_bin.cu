@@ -219,10 +219,10 @@ __global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__r
     tfrc[p] = b;
 }
 
-// Exclusive scans of up to two count arrays, one block each (blockIdx.x
-// picks the pair); out[n] receives the total.  With `chunk` > 0 the values
+// Exclusive scans of up to three count arrays, one block each (blockIdx.x
+// picks the job); out[n] receives the total.  With `chunk` > 0 the values
 // scanned are the P2P work items of each cell, ceil(count / chunk) with count
-// read from the sub-cell starts `in` (stride kSub3), instead of in[i].
+// the sum of the cell's kSub3 sub-cell counts `in`, instead of in[i].
 struct ScanJob {
     const int32_t *in;
     int32_t *out;
@@ -233,14 +233,17 @@ __device__ __forceinline__ int scan_value(const ScanJob &j, int i)
 {
     if (j.chunk <= 0)
         return j.in[i];
-    const int cnt = j.in[(i + 1) * kSub3] - j.in[i * kSub3];
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kSub3; ++k)
+        cnt += j.in[i * kSub3 + k];
     return (cnt + j.chunk - 1) / j.chunk;
 }
 
-__global__ void __launch_bounds__(1024) k_scan(ScanJob j0, ScanJob j1)
+__global__ void __launch_bounds__(1024) k_scan(ScanJob j0, ScanJob j1, ScanJob j2)
 {
     __shared__ int32_t wsum[32];
-    const ScanJob j = blockIdx.x == 0 ? j0 : j1;
+    const ScanJob j = blockIdx.x == 0 ? j0 : (blockIdx.x == 1 ? j1 : j2);
     const int n = j.n;
     int32_t *__restrict__ out = j.out;
     int tid = threadIdx.x, nthr = blockDim.x;
@@ -363,14 +366,15 @@ cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s)
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s)
 {
     ScanJob j{in, out, n, 0};
-    k_scan<<<1, 1024, 0, s>>>(j, j);
+    k_scan<<<1, 1024, 0, s>>>(j, j, j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan2(const int32_t *in0, int32_t *out0, int n0, const int32_t *in1, int32_t *out1,
-                         int n1, cudaStream_t s)
+cudaError_t launch_bin_scans(ewald_plan_s *p, cudaStream_t s)
 {
-    k_scan<<<2, 1024, 0, s>>>(ScanJob{in0, out0, n0, 0}, ScanJob{in1, out1, n1, 0});
+    const Geometry &g = p->g;
+    k_scan<<<3, 1024, 0, s>>>(ScanJob{p->cntn, p->startn, g.nkeys, 0}, ScanJob{p->cntt, p->startt, g.ntiles, 0},
+                              ScanJob{p->cntn, p->item_off, g.ncells, kP2PChunk});
     return cudaGetLastError();
 }
 
@@ -400,8 +404,8 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
 // prefix offsets, in one launch.
 cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s)
 {
-    ScanJob j{p->startn, p->item_off, p->g.ncells, kP2PChunk};
-    k_scan<<<1, 1024, 0, s>>>(j, j);
+    ScanJob j{p->cntn, p->item_off, p->g.ncells, kP2PChunk};
+    k_scan<<<1, 1024, 0, s>>>(j, j, j);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,25 @@ constexpr int kNumEvents = 10;
 constexpr int kP2PChunk = 32;       // targets per P2P work item (one warp)
 constexpr int kGridDsMinP = 8;      // smallest support of the double-single grid kernels
 
+// P2P work items are cut from groups of cells: two x-neighbours when the
+// cutoff reaches one cell (K = 1; a warp's 32 targets may straddle them, so
+// warps stay full), single cells when it reaches two (K = 2).  Groups run
+// along x in each row (y, z); with odd n_c a row ends on a one-cell group.
+__host__ __device__ inline int p2p_group_cells(int K) { return K == 1 ? 2 : 1; }
+__host__ __device__ inline int p2p_groups_per_row(int nc, int K)
+{
+    return (nc + p2p_group_cells(K) - 1) / p2p_group_cells(K);
+}
+__host__ __device__ inline int p2p_groups(int nc, int K) { return nc * nc * p2p_groups_per_row(nc, K); }
+// first cell of group g and its number of cells
+__host__ __device__ inline int p2p_group_cell(int g, int nc, int K, int &ncg)
+{
+    const int gpr = p2p_groups_per_row(nc, K), gc = p2p_group_cells(K);
+    const int row = g / gpr, x0 = (g - row * gpr) * gc;
+    ncg = nc - x0 < gc ? nc - x0 : gc;
+    return row * nc + x0;
+}
+
 // double-single window weights: bins of one axis padded to a multiple of 4
 inline int ds_window_stride(int P) { return (P + 3) & ~3; }
 

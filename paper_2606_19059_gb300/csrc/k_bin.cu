@@ -221,22 +221,24 @@ __global__ void k_gather_forces(const double *__restrict__ f, const int32_t *__r
 
 // Exclusive scans of up to three count arrays, one block each (blockIdx.x
 // picks the job); out[n] receives the total.  With `chunk` > 0 the values
-// scanned are the P2P work items of each cell, ceil(count / chunk) with count
-// the sum of the cell's kSub3 sub-cell counts `in`, instead of in[i].
+// scanned are the P2P work items of each cell group (p2p_group_cell),
+// ceil(count / chunk) with count the sum of its sub-cell counts `in`, instead
+// of in[i].
 struct ScanJob {
     const int32_t *in;
     int32_t *out;
-    int n, chunk;
+    int n, chunk, nc, K;
 };
 
 __device__ __forceinline__ int scan_value(const ScanJob &j, int i)
 {
     if (j.chunk <= 0)
         return j.in[i];
+    int ncg;
+    const int c = p2p_group_cell(i, j.nc, j.K, ncg);
     int cnt = 0;
-#pragma unroll
-    for (int k = 0; k < kSub3; ++k)
-        cnt += j.in[i * kSub3 + k];
+    for (int k = 0; k < ncg * kSub3; ++k)
+        cnt += j.in[c * kSub3 + k];
     return (cnt + j.chunk - 1) / j.chunk;
 }
 
@@ -365,7 +367,7 @@ cudaError_t launch_bin_keys(ewald_plan_s *p, const BinArgs &a, cudaStream_t s)
 
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s)
 {
-    ScanJob j{in, out, n, 0};
+    ScanJob j{in, out, n, 0, 0, 0};
     k_scan<<<1, 1024, 0, s>>>(j, j, j);
     return cudaGetLastError();
 }
@@ -373,8 +375,9 @@ cudaError_t launch_scan(const int32_t *in, int32_t *out, int n, cudaStream_t s)
 cudaError_t launch_bin_scans(ewald_plan_s *p, cudaStream_t s)
 {
     const Geometry &g = p->g;
-    k_scan<<<3, 1024, 0, s>>>(ScanJob{p->cntn, p->startn, g.nkeys, 0}, ScanJob{p->cntt, p->startt, g.ntiles, 0},
-                              ScanJob{p->cntn, p->item_off, g.ncells, kP2PChunk});
+    k_scan<<<3, 1024, 0, s>>>(ScanJob{p->cntn, p->startn, g.nkeys, 0, 0, 0},
+                              ScanJob{p->cntt, p->startt, g.ntiles, 0, 0, 0},
+                              ScanJob{p->cntn, p->item_off, p2p_groups(g.nc, g.K), kP2PChunk, g.nc, g.K});
     return cudaGetLastError();
 }
 
@@ -404,7 +407,7 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
 // prefix offsets, in one launch.
 cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s)
 {
-    ScanJob j{p->cntn, p->item_off, p->g.ncells, kP2PChunk};
+    ScanJob j{p->cntn, p->item_off, p2p_groups(p->g.nc, p->g.K), kP2PChunk, p->g.nc, p->g.K};
     k_scan<<<1, 1024, 0, s>>>(j, j, j);
     return cudaGetLastError();
 }

@@ -257,7 +257,7 @@ __device__ __forceinline__ int wrap(int i, int n)
 }
 
 constexpr int kWarps = 4;       // independent warps per block
-constexpr int kMaxSeg = 216;    // K = 1: the 6^3 colleague sub-cells; K = 2: 125 colleague cells
+constexpr int kMaxSeg = 288;    // K = 1: the 8 x 6 x 6 sub-cells around a group; K = 2: 125 cells
 
 // Per-warp shared state: the colleague source ranges kept for this warp,
 // concatenated into one stream (prefix offsets), and one staged tile of it.
@@ -269,12 +269,15 @@ struct WarpSmem {
     uint16_t seg_off[kMaxSeg];  // colleague cell offset, (dx+2) | (dy+2) << 4 | (dz+2) << 8
 };
 
-// Work item = (cell, chunk of <= 32 targets) handled by one warp.
-__device__ __forceinline__ bool find_item(const P2PArgs &a, int item, int &c, int &tb, int &te)
+// Work item = (cell group, chunk of <= 32 targets) handled by one warp: c is
+// the group's first cell, targets [tb, te); those from tsplit on lie in the
+// group's second cell (one cell further in x).
+__device__ __forceinline__ bool find_item(const P2PArgs &a, int item, int &c, int &tb, int &te, int &tsplit)
 {
-    if (item >= a.item_off[a.ncells])
+    const int ng = p2p_groups(a.nc, a.K);
+    if (item >= a.item_off[ng])
         return false;
-    int lo = 0, hi = a.ncells;  // item_off[lo] <= item < item_off[hi]
+    int lo = 0, hi = ng;  // item_off[lo] <= item < item_off[hi]
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
         if (a.item_off[mid] <= item)
@@ -282,11 +285,13 @@ __device__ __forceinline__ bool find_item(const P2PArgs &a, int item, int &c, in
         else
             hi = mid;
     }
-    c = lo;
-    int chunk = item - a.item_off[c];
-    int nch = a.item_off[c + 1] - a.item_off[c];
-    int t0 = a.startn[c * kSub3], t1 = a.startn[(c + 1) * kSub3];
-    int per = (t1 - t0 + nch - 1) / nch;
+    int ncg;
+    c = p2p_group_cell(lo, a.nc, a.K, ncg);
+    const int chunk = item - a.item_off[lo];
+    const int nch = a.item_off[lo + 1] - a.item_off[lo];
+    const int t0 = a.startn[c * kSub3], t1 = a.startn[(c + ncg) * kSub3];
+    tsplit = ncg > 1 ? a.startn[(c + 1) * kSub3] : t1;
+    const int per = (t1 - t0 + nch - 1) / nch;
     tb = t0 + chunk * per;
     te = min(t1, tb + per);
     return true;
@@ -307,13 +312,14 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-// Build the warp's source stream for cell c.  K = 1: the 6^3 sub-cells (half
-// a cell wide) of the 27 colleague cells, keeping those whose box comes within
-// rc of the bounding box [blo, bhi] of the warp's targets -- the warp's 32
-// targets sit in one or two sub-cells, so about a third of the colleague
-// volume is out of reach.  K = 2 (small boxes): the 125 colleague cells, all
-// kept.  Coordinates are cell-local; `hw` is half a cell in their units and
-// `rcm` the cutoff plus a margin.  Empty segments are dropped.
+// Build the warp's source stream for the group starting at cell c.  K = 1: the
+// 8 x 6 x 6 sub-cells (half a cell wide) of the colleague cells of the group's
+// two cells, keeping those whose box comes within rc of the bounding box
+// [blo, bhi] of the warp's targets -- the warp's 32 targets sit in a few
+// sub-cells, so most of the colleague volume is out of reach.  K = 2 (small
+// boxes): the 125 colleague cells, all kept.  Coordinates are local to cell c;
+// `hw` is half a cell in their units and `rcm` the cutoff plus a margin.
+// Empty segments are dropped.
 template <typename WS>
 __device__ __forceinline__ int build_segments(const P2PArgs &a, int c, WS &ws, int lane, float3 blo,
                                               float3 bhi, float hw, float rcm)
@@ -322,7 +328,7 @@ __device__ __forceinline__ int build_segments(const P2PArgs &a, int c, WS &ws, i
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     const bool sub = K == 1;
     const int side = 2 * K + 1;
-    const int nent = sub ? 216 : side * side * side;
+    const int nent = sub ? 288 : side * side * side;
     int carry = 0, kept = 0;
     for (int s0 = 0; s0 < nent; s0 += 32) {
         const int s = s0 + lane;
@@ -331,8 +337,9 @@ __device__ __forceinline__ int build_segments(const P2PArgs &a, int c, WS &ws, i
         if (s < nent) {
             int dx, dy, dz, key_lo, key_hi;
             if (sub) {
-                // half-cell index relative to this cell's corner, -2..3 per axis
-                const int ix = s % 6 - 2, iy = (s / 6) % 6 - 2, iz = s / 36 - 2;
+                // half-cell index relative to cell c's corner: -2..5 in x,
+                // -2..3 in y and z
+                const int ix = s % 8 - 2, iy = (s / 8) % 6 - 2, iz = s / 48 - 2;
                 const float gx = fmaxf(0.f, fmaxf(ix * hw - bhi.x, blo.x - (ix + 1) * hw));
                 const float gy = fmaxf(0.f, fmaxf(iy * hw - bhi.y, blo.y - (iy + 1) * hw));
                 const float gz = fmaxf(0.f, fmaxf(iz * hw - bhi.z, blo.z - (iz + 1) * hw));
@@ -420,14 +427,15 @@ __device__ __forceinline__ int locate(const WS &ws, int nseg, int q, int &dx, in
 constexpr float kFarHalf = 64.0f;  // FP16 dummy source: r^2 ~ 1e4, finite and never within rc
 
 // FP16 phase-1 threshold on r^2 (cell units, cutoff rcc <= 2 cells).  In FP16
-// a source coordinate (|v| < 4) is off by <= 2^-10, a target's (in [0, 1)) by
-// <= 2^-12, their difference adds <= 2^-11: |d| by <= 1.8e-3 per component,
-// r^2 by <= 6e-3 rcc; the FP16 sums add <= 3e-3 and rounding the threshold
-// <= 2e-3.  0.006 (rcc + rcc^2) + 0.002 covers that twice over, so no pair
-// within rc fails the test; the few beyond it that pass are dropped later.
+// a source coordinate (|v| < 4) is off by <= 2^-10, a target's (in [0, 2): a
+// cell group's second cell) by <= 2^-11, their difference adds <= 2^-11: |d|
+// by <= 2e-3 per component, r^2 by <= 7e-3 rcc; the FP16 sums add <= 3e-3 and
+// rounding the threshold <= 2e-3.  0.008 (rcc + rcc^2) + 0.002 covers that
+// about twice over, so no pair within rc fails the test; the few beyond it
+// that pass are dropped later.
 __host__ __device__ inline float half_threshold(double rcc)
 {
-    return (float)(rcc * rcc + 0.006 * (rcc + rcc * rcc) + 0.002);
+    return (float)(rcc * rcc + 0.008 * (rcc + rcc * rcc) + 0.002);
 }
 
 // FP32 kernel: tiles of 64 sources, two staged at once (a ring of two slots),
@@ -664,8 +672,8 @@ __device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &k
                                              int item, WsF32 &ws, int lane)
 {
     using Tot = typename std::conditional<KAHAN, double, float>::type;
-    int c, tb, te;
-    if (!find_item(a, item, c, tb, te))
+    int c, tb, te, tsplit;
+    if (!find_item(a, item, c, tb, te, tsplit))
         return;  // whole warp: no block-wide barrier follows
     const int t = tb + lane;
     const bool active = t < te;
@@ -674,7 +682,8 @@ __device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &k
         const float4 *rec = (const float4 *)a.nrec;
         float3 hi, lo, f;
         unpack_rec(rec[2 * t], rec[2 * t + 1], hi, lo, f);
-        th = make_float4(hi.x, hi.y, hi.z, 0.f);
+        // relative to cell c: the group's second cell is one cell on in x (exact)
+        th = make_float4(hi.x + (t >= tsplit ? 1.f : 0.f), hi.y, hi.z, 0.f);
         tl = make_float4(lo.x, lo.y, lo.z, 0.f);
     }
     // the warp's target bounding box (hi parts; the margin covers lo)
@@ -790,15 +799,18 @@ __device__ __forceinline__ void p2p_f64_item(const P2PArgs &a, int item, WsF64 &
 {
     double3 *sp = ws.tile.sp, *sf = ws.tile.sf;
     uint4 *sh = ws.tile.sh;
-    int c, tb, te;
-    if (!find_item(a, item, c, tb, te))
+    int c, tb, te, tsplit;
+    if (!find_item(a, item, c, tb, te, tsplit))
         return;
     const dvec4 *npos = (const dvec4 *)a.npos, *nfrc = (const dvec4 *)a.nfrc;
     const int t = tb + lane;
     const bool active = t < te;
     dvec4 xt = {0.0, 0.0, 0.0, 0.0};
-    if (active)
+    if (active) {
         xt = npos[t];
+        if (t >= tsplit)  // relative to cell c: the group's second cell
+            xt.x += a.cell;
+    }
     const double rc2 = a.rc * a.rc, xi = a.xi, xi2 = a.xi * a.xi;
     const double c2 = 2.0 * a.xi / sqrt(3.14159265358979323846), selfc = 2.0 * c2;
     const double inv_cell = 1.0 / a.cell, rcc = a.rc * inv_cell;
@@ -1081,14 +1093,17 @@ __device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc,
                                             int lane)
 {
     const float4 *rec = (const float4 *)a.nrec;
-    int c, tb, te;
-    if (!find_item(a, item, c, tb, te))
+    int c, tb, te, tsplit;
+    if (!find_item(a, item, c, tb, te, tsplit))
         return;  // past the last real item: the same for the whole warp
     const int t = tb + lane;
     const bool active = t < te;
     float3 th = make_float3(0.f, 0.f, 0.f), tl = th, fdum;
-    if (active)
+    if (active) {
         unpack_rec(rec[2 * t], rec[2 * t + 1], th, tl, fdum);
+        if (t >= tsplit)  // relative to cell c: the group's second cell (exact)
+            th.x += 1.f;
+    }
     const float3 blo = make_float3(warp_min(active ? th.x : 1e30f), warp_min(active ? th.y : 1e30f),
                                    warp_min(active ? th.z : 1e30f));
     const float3 bhi = make_float3(warp_max(active ? th.x : -1e30f), warp_max(active ? th.y : -1e30f),

@@ -165,6 +165,14 @@ static double rc_for_xi(double xi, double target)
     }
     return hi;
 }
+// cuFFT's relative cost per element for sizes with a radix-7 or radix-5 factor
+// (measured, FP64 3-D real transforms on GB300: M = 112 ran ~40 % and M = 160
+// ~20 % above the m^3 log m^3 scaling of M = 128 and 144)
+static double fft_size_factor(int m)
+{
+    return 1.0 + (m % 7 == 0 ? 0.4 : 0.0) + (m % 5 == 0 ? 0.2 : 0.0);
+}
+
 static bool fft_friendly(int m)
 {
     if (m % 2)
@@ -247,7 +255,7 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
             double cost = wn * (10.0 * cand + 50.0 * inr)              // P2P
                           + wg * 28.0 * (double)N * P * P * P          // P2G + G2P per point
                           + wg * 65.0 * m3 * halo                      // P2G + G2P per tile
-                          + wf * 27.0 * m3 * log2(m3);                 // FFTs
+                          + wf * 27.0 * m3 * log2(m3) * fft_size_factor(m);  // FFTs
             if (cost < best) {
                 best = cost;
                 M = m;

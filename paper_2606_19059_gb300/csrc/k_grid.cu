@@ -134,12 +134,22 @@ __global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(Gri
     }
     const int row = threadIdx.x % ROWS, slice = threadIdx.x / ROWS;
     const int y = row % T, z = row / T;  // rows (y, z) and (y, z + T/2)
-    R acc[2][T][3];
+    // FP32: the sums of x and x + 1 packed for FP32x2 FMAs, acc2[h][x / 2][c]
+    constexpr bool kPack = sizeof(R) == 4 && T % 2 == 0;
+    R acc[kPack ? 1 : 2][kPack ? 1 : T][3];
+    float2 acc2[2][kPack ? T / 2 : 1][3];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < 2; ++h) {
+        if constexpr (kPack) {
 #pragma unroll
-        for (int x = 0; x < T; ++x)
-            acc[h][x][0] = acc[h][x][1] = acc[h][x][2] = (R)0;
+            for (int x = 0; x < T / 2; ++x)
+                acc2[h][x][0] = acc2[h][x][1] = acc2[h][x][2] = make_float2(0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int x = 0; x < T; ++x)
+                acc[h][x][0] = acc[h][x][1] = acc[h][x][2] = (R)0;
+        }
+    }
     __syncthreads();
     const int total = seg_pref[nseg];
     const R4 *tdat = (const R4 *)a.tdat, *tfrc = (const R4 *)a.tfrc;
@@ -282,38 +292,59 @@ __global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(Gri
                 wv[4 * x4 + 2] = qv.z;
                 wv[4 * x4 + 3] = qv.w;
             }
-            if (hz0) {
-                const R g0[3] = {wz0 * f.x, wz0 * f.y, wz0 * f.z};
-                if (hx0) {
+            if constexpr (kPack) {
+                // (sum[x], sum[x + 1]) += (w[x], w[x + 1]) g: one FP32x2 FMA a pair
 #pragma unroll
-                    for (int x = 0; x < H; ++x)
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 0 ? hz0 : hz1) {
+                        const float wzh = h == 0 ? wz0 : wz1;
+                        const float2 g[3] = {make_float2(wzh * f.x, wzh * f.x), make_float2(wzh * f.y, wzh * f.y),
+                                             make_float2(wzh * f.z, wzh * f.z)};
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
+                        for (int x = 0; x < T / 2; ++x) {
+                            if (x < H / 2 ? hx0 : hx1) {
+                                const float2 w2 = make_float2(wv[2 * x], wv[2 * x + 1]);
+#pragma unroll
+                                for (int c = 0; c < 3; ++c)
+                                    acc2[h][x][c] = __ffma2_rn(w2, g[c], acc2[h][x][c]);
+                            }
+                        }
+                    }
                 }
-                if (hx1) {
+            } else {
+                if (hz0) {
+                    const R g0[3] = {wz0 * f.x, wz0 * f.y, wz0 * f.z};
+                    if (hx0) {
 #pragma unroll
-                    for (int x = H; x < T; ++x)
+                        for (int x = 0; x < H; ++x)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
+                            for (int c = 0; c < 3; ++c)
+                                acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
+                    }
+                    if (hx1) {
+#pragma unroll
+                        for (int x = H; x < T; ++x)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c)
+                                acc[0][x][c] = fma(wv[x], g0[c], acc[0][x][c]);
+                    }
                 }
-            }
-            if (hz1) {
-                const R g1[3] = {wz1 * f.x, wz1 * f.y, wz1 * f.z};
-                if (hx0) {
+                if (hz1) {
+                    const R g1[3] = {wz1 * f.x, wz1 * f.y, wz1 * f.z};
+                    if (hx0) {
 #pragma unroll
-                    for (int x = 0; x < H; ++x)
+                        for (int x = 0; x < H; ++x)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
-                }
-                if (hx1) {
+                            for (int c = 0; c < 3; ++c)
+                                acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
+                    }
+                    if (hx1) {
 #pragma unroll
-                    for (int x = H; x < T; ++x)
+                        for (int x = H; x < T; ++x)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
+                            for (int c = 0; c < 3; ++c)
+                                acc[1][x][c] = fma(wv[x], g1[c], acc[1][x][c]);
+                    }
                 }
             }
         }
@@ -327,7 +358,8 @@ __global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(Gri
         for (int x = 0; x < T; ++x)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                red[((slice * 3 + c) * T + z + h * H) * T * T + y * T + x] = acc[h][x][c];
+                red[((slice * 3 + c) * T + z + h * H) * T * T + y * T + x] =
+                    kPack ? (x & 1 ? acc2[h][x / 2][c].y : acc2[h][x / 2][c].x) : acc[kPack ? 0 : h][kPack ? 0 : x][c];
     __syncthreads();
     G *grid = (G *)a.grid;
     const int64_t M = a.M, M3 = M * M * M;

@@ -53,6 +53,36 @@ __device__ __forceinline__ void ds_fma(float &ah, float &al, float xh, float xl,
     ds_acc(ah, al, p, e);
 }
 
+// ds_fma on two sums at once in FP32x2 arithmetic: (ah, al) += (xh, xl) y,
+// y = (yh, yl) common to both lanes and passed negated (nyh = -yh, nyl = -yl).
+// The same operations, each rounded once: a - b is fma(b, -1, a).
+__device__ __forceinline__ void ds_fma2(float2 &ah, float2 &al, float2 xh, float2 xl, float2 yh, float2 nyh,
+                                        float2 nyl)
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 p = __fmul2_rn(xh, yh);
+    // -(product error + cross terms), exact up to the last two roundings
+    const float2 ne = __ffma2_rn(xl, nyh, __ffma2_rn(xh, nyl, __ffma2_rn(xh, nyh, p)));
+    const float2 s = __fadd2_rn(ah, p);
+    const float2 bb = __ffma2_rn(ah, m1, s);
+    const float2 err = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, s), m1, ah), __ffma2_rn(bb, m1, p));
+    ah = s;
+    al = __fadd2_rn(al, __ffma2_rn(ne, m1, err));
+}
+
+// ds_fma on two sums at once, both operands per lane: (ah, al) += (xh, xl) (yh, yl)
+__device__ __forceinline__ void ds_fma2v(float2 &ah, float2 &al, float2 xh, float2 xl, float2 yh, float2 yl)
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 p = __fmul2_rn(xh, yh);
+    const float2 e = __ffma2_rn(xl, yh, __ffma2_rn(xh, yl, __ffma2_rn(xh, yh, __fmul2_rn(p, m1))));
+    const float2 s = __fadd2_rn(ah, p);
+    const float2 bb = __ffma2_rn(ah, m1, s);
+    const float2 err = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, s), m1, ah), __ffma2_rn(bb, m1, p));
+    ah = s;
+    al = __fadd2_rn(al, __fadd2_rn(err, e));
+}
+
 __device__ __forceinline__ void ds_split(double v, float &h, float &l)
 {
     h = __double2float_rn(v);
@@ -153,12 +183,12 @@ __global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
     const int row = threadIdx.x % kDsRows, slice = threadIdx.x / kDsRows;
     const int y = row % T, z = row / T;
     const bool zlo = z < H;  // warp-uniform
-    float ah[T][3], al[T][3];
+    float2 ah[T / 2][3], al[T / 2][3];  // x and x + 1 packed for FP32x2 arithmetic
 #pragma unroll
-    for (int x = 0; x < T; ++x)
+    for (int x = 0; x < T / 2; ++x)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            ah[x][c] = al[x][c] = 0.f;
+            ah[x][c] = al[x][c] = make_float2(0.f, 0.f);
     __syncthreads();
     const int total = seg_pref[nseg];
 
@@ -244,23 +274,22 @@ __global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
             ds_prod(gp, ge, fh.x, fl.x, g[0][0], g[0][1]);
             ds_prod(gp, ge, fh.y, fl.y, g[1][0], g[1][1]);
             ds_prod(gp, ge, fh.z, fl.z, g[2][0], g[2][1]);
-            const float *wxh = wr + (0 * B + k) * T, *wxl = wr + (1 * B + k) * T;
-            if (hx0) {
+            const float2 *wxh = (const float2 *)(wr + (0 * B + k) * T),
+                         *wxl = (const float2 *)(wr + (1 * B + k) * T);
+            float2 gh[3], ngh[3], ngl[3];
 #pragma unroll
-                for (int x = 0; x < H; ++x) {
-                    const float h = wxh[x], l = wxl[x];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        ds_fma(ah[x][c], al[x][c], h, l, g[c][0], g[c][1]);
-                }
+            for (int c = 0; c < 3; ++c) {
+                gh[c] = make_float2(g[c][0], g[c][0]);
+                ngh[c] = make_float2(-g[c][0], -g[c][0]);
+                ngl[c] = make_float2(-g[c][1], -g[c][1]);
             }
-            if (hx1) {
 #pragma unroll
-                for (int x = H; x < T; ++x) {
-                    const float h = wxh[x], l = wxl[x];
+            for (int x = 0; x < T / 2; ++x) {
+                if (x < H / 2 ? hx0 : hx1) {
+                    const float2 h = wxh[x], l = wxl[x];
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
-                        ds_fma(ah[x][c], al[x][c], h, l, g[c][0], g[c][1]);
+                        ds_fma2(ah[x][c], al[x][c], h, l, gh[c], ngh[c], ngl[c]);
                 }
             }
         }
@@ -272,7 +301,8 @@ __global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
     for (int x = 0; x < T; ++x)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            red[(slice * 3 + c) * T3 + (z * T + y) * T + x] = make_float2(ah[x][c], al[x][c]);
+            red[(slice * 3 + c) * T3 + (z * T + y) * T + x] =
+                x & 1 ? make_float2(ah[x / 2][c].y, al[x / 2][c].y) : make_float2(ah[x / 2][c].x, al[x / 2][c].x);
     __syncthreads();
     const int M = a.M;
     const int64_t M3 = (int64_t)M * M * M;
@@ -393,10 +423,17 @@ __global__ void __launch_bounds__(kG2PDsThreads, 2) k_g2p_ds(GridDsArgs a)
             for (int r = 0; r < NR; ++r) {
                 if (roff[r] >= 0) {
                     const float *ch = vh + base + roff[r], *cl = vl + base + roff[r];
-                    float sh = 0.f, sl = 0.f;
+                    // even and odd planes as the two lanes of FP32x2 sums
+                    float2 sh2 = make_float2(0.f, 0.f), sl2 = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int k = 0; k < PC; ++k)
-                        ds_fma(sh, sl, wzh[k], wzl[k], ch[k * PLANE], cl[k * PLANE]);
+                    for (int k = 0; k + 1 < PC; k += 2)
+                        ds_fma2v(sh2, sl2, make_float2(wzh[k], wzh[k + 1]), make_float2(wzl[k], wzl[k + 1]),
+                                 make_float2(ch[k * PLANE], ch[(k + 1) * PLANE]),
+                                 make_float2(cl[k * PLANE], cl[(k + 1) * PLANE]));
+                    if constexpr (PC % 2)
+                        ds_fma(sh2.x, sl2.x, wzh[PC - 1], wzl[PC - 1], ch[(PC - 1) * PLANE], cl[(PC - 1) * PLANE]);
+                    float sh = sh2.x, sl = sl2.x;
+                    ds_acc(sh, sl, sh2.y, sl2.y);
                     float yp, ye;  // wy wx
                     ds_prod(w[2 * 16 + ry[r]], w[3 * 16 + ry[r]], w[rx[r]], w[16 + rx[r]], yp, ye);
                     float pp, pe;

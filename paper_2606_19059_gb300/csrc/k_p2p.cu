@@ -83,8 +83,6 @@ struct F32Const {
 };
 
 __constant__ float c_exp2f32[EXP2_F32_N];
-__constant__ float c_erfcx_ds_hi[ERFCX_DS_N], c_erfcx_ds_lo[ERFCX_DS_SPLIT];
-__constant__ float c_exp_ds_hi[EXP_DS_N], c_exp_ds_lo[6];
 
 // e^{-xi^2 r^2} = 2^y, y = (r2 + r2lo) * (chi + clo) kept as y_hi + y_lo (the
 // product's rounding recovered by an FMA), reduced to 2^f, |f| <= 1/2, by a minimax
@@ -923,29 +921,11 @@ __device__ __forceinline__ dsf quick_two_sum(float a, float b)  // |a| >= |b|
     const float s = __fadd_rn(a, b);
     return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
-__device__ __forceinline__ dsf two_prod(float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    return {p, fmaf(a, b, -p)};
-}
 __device__ __forceinline__ dsf ds_add(dsf x, dsf y)
 {
     const dsf s = two_sum(x.h, y.h);
     return quick_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
 }
-__device__ __forceinline__ dsf ds_add_f(dsf x, float y)
-{
-    const dsf s = two_sum(x.h, y);
-    return quick_two_sum(s.h, __fadd_rn(s.l, x.l));
-}
-__device__ __forceinline__ dsf ds_neg(dsf x) { return {-x.h, -x.l}; }
-__device__ __forceinline__ dsf ds_mul(dsf x, dsf y)
-{
-    const float p = __fmul_rn(x.h, y.h);
-    const float e = fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p)));
-    return quick_two_sum(p, e);
-}
-__device__ __forceinline__ dsf ds_scale2(dsf x, float pow2) { return {x.h * pow2, x.l * pow2}; }
 
 struct DSConst {
     float rc2;              // cutoff^2 (cell units), compared on the high part
@@ -954,88 +934,140 @@ struct DSConst {
     dsf xi, xi2, c2, selfc; // xi, xi^2, 2 xi / sqrt(pi), 4 xi / sqrt(pi) (cell units)
 };
 
+// ---- two double-single pairs at once ---------------------------------------
+// The operations above on float2 pairs, one source in flight per lane of the
+// FP32x2 arithmetic, each operation rounded once as in the scalar form (a - b
+// is fma(b, -1, a)); the cutoff and r = 0 cases become selects (an
+// out-of-range source, or a dummy entry, runs on a stand-in r^2 = 1 and
+// contributes exactly 0).  Coefficients come from duplicated-pair tables.
+__constant__ float2 c_erfcx_ds2_hi[ERFCX_DS_N], c_erfcx_ds2_lo[ERFCX_DS_SPLIT];
+__constant__ float2 c_exp_ds2_hi[EXP_DS_N], c_exp_ds2_lo[6];
+
+struct dsf2 {
+    float2 h, l;
+};
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ dsf2 two_sum2(float2 a, float2 b)
+{
+    const float2 s = add2(a, b), v = sub2(s, a);
+    return {s, add2(sub2(a, sub2(s, v)), sub2(b, v))};
+}
+__device__ __forceinline__ dsf2 quick_two_sum2(float2 a, float2 b)  // |a| >= |b|
+{
+    const float2 s = add2(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ dsf2 two_prod2(float2 a, float2 b)
+{
+    const float2 p = mul2(a, b);
+    return {p, __ffma2_rn(a, b, neg2(p))};
+}
+__device__ __forceinline__ dsf2 ds_add2(dsf2 x, dsf2 y)
+{
+    const dsf2 s = two_sum2(x.h, y.h);
+    return quick_two_sum2(s.h, add2(s.l, add2(x.l, y.l)));
+}
+__device__ __forceinline__ dsf2 ds_add_f2(dsf2 x, float2 y)
+{
+    const dsf2 s = two_sum2(x.h, y);
+    return quick_two_sum2(s.h, add2(s.l, x.l));
+}
+__device__ __forceinline__ dsf2 ds_mul2(dsf2 x, dsf2 y)
+{
+    const float2 p = mul2(x.h, y.h);
+    const float2 e = __ffma2_rn(x.h, y.l, __ffma2_rn(x.l, y.h, __ffma2_rn(x.h, y.h, neg2(p))));
+    return quick_two_sum2(p, e);
+}
+__device__ __forceinline__ dsf2 dup(dsf c) { return {f2(c.h), f2(c.l)}; }
+__device__ __forceinline__ dsf2 sel(bool a, bool b, dsf2 x, dsf2 y)  // lane-wise a, b ? x : y
+{
+    return {make_float2(a ? x.h.x : y.h.x, b ? x.h.y : y.h.y), make_float2(a ? x.l.x : y.l.x, b ? x.l.y : y.l.y)};
+}
+
 // e^{-y} for 0 <= y <= ~60: y = n ln2 - s with |s| <= ln2/2 (ln2 split so that
-// n ln2_hi is exact and n ln2_mid is carried exactly by two_prod), e^s by its
+// n ln2_hi is exact and n ln2_mid is carried exactly by a two-product), e^s by its
 // Taylor series to s^13 (terms from s^6 on in FP32: they are below 3e-6), then
 // the exact scaling by 2^-n.
-__device__ __forceinline__ dsf exp_neg_ds(dsf y)
+__device__ __forceinline__ dsf2 exp_neg_ds2(dsf2 y)
 {
-    const float kLn2Hi = 0.693145751953125f;          // 45426 * 2^-16
-    const float kLn2Mid = 1.428606765330187e-06f;     // ln2 - kLn2Hi, rounded
-    const float kLn2Lo = 5.497923148104107e-14f;      // ln2 - kLn2Hi - kLn2Mid, rounded
-    const float n = rintf(y.h * 1.44269504088896341f);
-    const float a = fmaf(n, kLn2Hi, -y.h);  // exact: both sides multiples of 2^-25, |a| < 1
-    const dsf m = two_prod(n, kLn2Mid);
-    dsf s = two_sum(a, m.h);
-    s = quick_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(m.l, fmaf(n, kLn2Lo, -y.l))));
-    float q = c_exp_ds_hi[EXP_DS_N - 1];
+    const float kLn2Hi = 0.693145751953125f, kLn2Mid = 1.428606765330187e-06f, kLn2Lo = 5.497923148104107e-14f;
+    const float2 n = make_float2(rintf(y.h.x * 1.44269504088896341f), rintf(y.h.y * 1.44269504088896341f));
+    const float2 a = __ffma2_rn(n, f2(kLn2Hi), neg2(y.h));
+    const dsf2 m = two_prod2(n, f2(kLn2Mid));
+    dsf2 s = two_sum2(a, m.h);
+    s = quick_two_sum2(s.h, add2(s.l, add2(m.l, __ffma2_rn(n, f2(kLn2Lo), neg2(y.l)))));
+    float2 q = c_exp_ds2_hi[EXP_DS_N - 1];
 #pragma unroll
     for (int k = EXP_DS_N - 2; k >= 6; --k)
-        q = fmaf(q, s.h, c_exp_ds_hi[k]);
-    dsf p = {q, 0.f};
+        q = __ffma2_rn(q, s.h, c_exp_ds2_hi[k]);
+    dsf2 p = {q, f2(0.f)};
 #pragma unroll
     for (int k = 5; k >= 3; --k)
-        p = ds_add(ds_mul(p, s), {c_exp_ds_hi[k], c_exp_ds_lo[k]});
+        p = ds_add2(ds_mul2(p, s), {c_exp_ds2_hi[k], c_exp_ds2_lo[k]});
 #pragma unroll
     for (int k = 2; k >= 0; --k)
-        p = ds_add_f(ds_mul(p, s), c_exp_ds_hi[k]);
-    return ds_scale2(p, __int_as_float((127 - (int)n) << 23));
+        p = ds_add_f2(ds_mul2(p, s), c_exp_ds2_hi[k]);
+    const float2 sc = make_float2(__int_as_float((127 - (int)n.x) << 23), __int_as_float((127 - (int)n.y) << 23));
+    return {mul2(p.h, sc), mul2(p.l, sc)};
 }
 
 // erfcx(x) = t g(u), t = 1/(1 + x/2), u = (8t - 5)/3 (fit_erf.py: 1.2e-13
 // relative on [0, 6]); g's coefficients from k = ERFCX_DS_SPLIT on are below
 // 7e-6 and summed in FP32.
-__device__ __forceinline__ dsf erfcx_ds(dsf x)
+__device__ __forceinline__ dsf2 erfcx_ds2(dsf2 x)
 {
-    const dsf den = ds_add_f(ds_scale2(x, 0.5f), 1.0f);
-    const float t0 = __frcp_rn(den.h);
-    const dsf pr = ds_mul({den.h, den.l}, {t0, 0.f});
-    dsf t = quick_two_sum(t0, t0 * __fsub_rn(__fsub_rn(1.0f, pr.h), pr.l));
-    if (t.h < 0.25f)  // past the fit (x > 6): never for an in-range pair
-        t = {0.25f, 0.f};
-    const dsf u = ds_mul(ds_add_f(ds_scale2(t, 8.0f), -5.0f), {0.3333333432674408f, -9.934107758624577e-09f});
-    float q = c_erfcx_ds_hi[ERFCX_DS_N - 1];
+    const dsf2 den = ds_add_f2({mul2(x.h, f2(0.5f)), mul2(x.l, f2(0.5f))}, f2(1.0f));
+    const float2 t0 = make_float2(__frcp_rn(den.h.x), __frcp_rn(den.h.y));
+    const dsf2 pr = ds_mul2(den, {t0, f2(0.f)});
+    dsf2 t = quick_two_sum2(t0, mul2(t0, sub2(sub2(f2(1.0f), pr.h), pr.l)));
+    // past the fit (x > 6): never for an in-range pair
+    t = sel(t.h.x < 0.25f, t.h.y < 0.25f, {f2(0.25f), f2(0.f)}, t);
+    const dsf2 u = ds_mul2(ds_add_f2({mul2(t.h, f2(8.0f)), mul2(t.l, f2(8.0f))}, f2(-5.0f)),
+                           {f2(0.3333333432674408f), f2(-9.934107758624577e-09f)});
+    float2 q = c_erfcx_ds2_hi[ERFCX_DS_N - 1];
 #pragma unroll
     for (int k = ERFCX_DS_N - 2; k >= ERFCX_DS_SPLIT; --k)
-        q = fmaf(q, u.h, c_erfcx_ds_hi[k]);
-    dsf g = {q, 0.f};
+        q = __ffma2_rn(q, u.h, c_erfcx_ds2_hi[k]);
+    dsf2 g = {q, f2(0.f)};
 #pragma unroll
     for (int k = ERFCX_DS_SPLIT - 1; k >= 0; --k)
-        g = ds_add(ds_mul(g, u), {c_erfcx_ds_hi[k], c_erfcx_ds_lo[k]});
-    return ds_mul(t, g);
+        g = ds_add2(ds_mul2(g, u), {c_erfcx_ds2_hi[k], c_erfcx_ds2_lo[k]});
+    return ds_mul2(t, g);
 }
 
-// One double-single candidate (cell units): d = (hi diff, exact) + (lo diff),
-// force fh + fl; adds the pair's term (or the removed far part at r = 0) to acc.
-__device__ __forceinline__ void pair_ds(float dhx, float dhy, float dhz, float dlx, float dly,
-                                        float dlz, const float3 &fh, const float3 &fl,
-                                        const DSConst &k, dsf (&acc)[3])
+// Two double-single candidates (cell units): d = (hi diff, exact) + (lo diff)
+// per component as (source 0, source 1) pairs, forces fh + fl likewise; adds
+// the pairs' terms to the two lanes of acc.
+__device__ __forceinline__ void pair_ds2(const float2 (&dh)[3], const float2 (&dl)[3], const float2 (&fh)[3],
+                                         const float2 (&fl)[3], const DSConst &k, dsf2 (&acc)[3])
 {
-    const dsf d[3] = {two_sum(dhx, dlx), two_sum(dhy, dly), two_sum(dhz, dlz)};
-    const dsf r2 = ds_add(ds_add(ds_mul(d[0], d[0]), ds_mul(d[1], d[1])), ds_mul(d[2], d[2]));
-    const dsf f[3] = {{fh.x, fl.x}, {fh.y, fl.y}, {fh.z, fl.z}};
-    if (r2.h > k.rc2)
-        return;
-    if (r2.h == 0.0f) {  // self or coincident point: the pair's far part comes out
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            acc[c] = ds_add(acc[c], ds_neg(ds_mul(k.selfc, f[c])));
-        return;
-    }
+    const dsf2 d[3] = {two_sum2(dh[0], dl[0]), two_sum2(dh[1], dl[1]), two_sum2(dh[2], dl[2])};
+    const dsf2 r2 = ds_add2(ds_add2(ds_mul2(d[0], d[0]), ds_mul2(d[1], d[1])), ds_mul2(d[2], d[2]));
+    const bool in0 = r2.h.x <= k.rc2 && r2.h.x > 0.0f, in1 = r2.h.y <= k.rc2 && r2.h.y > 0.0f;
+    const bool z0 = r2.h.x == 0.0f, z1 = r2.h.y == 0.0f;
+    const dsf2 r2s = sel(in0, in1, r2, {f2(1.0f), f2(0.f)});
     // 1/r: FP32 estimate and one Newton step carried in double-single
-    const float y0 = rsqrtf(r2.h);
-    const dsf t = ds_mul(r2, two_prod(y0, y0));
-    const dsf rinv = quick_two_sum(y0, 0.5f * y0 * __fsub_rn(__fsub_rn(1.0f, t.h), t.l));
-    const dsf x = ds_mul(k.xi, ds_mul(r2, rinv));
-    const dsf E = exp_neg_ds(ds_mul(k.xi2, r2));                       // e^{-xi^2 r^2}
-    const dsf A = ds_mul(ds_mul(E, erfcx_ds(x)), rinv);                // erfc(xi r) / r
-    const dsf B = ds_mul(k.c2, E);
-    const dsf amb = ds_add(A, ds_neg(B)), apb = ds_add(A, B);
-    const dsf rf = ds_add(ds_add(ds_mul(d[0], f[0]), ds_mul(d[1], f[1])), ds_mul(d[2], f[2]));
-    const dsf co = ds_mul(ds_mul(apb, rf), ds_mul(rinv, rinv));
+    const float2 y0 = make_float2(rsqrtf(r2s.h.x), rsqrtf(r2s.h.y));
+    const dsf2 t = ds_mul2(r2s, two_prod2(y0, y0));
+    const dsf2 rinv = quick_two_sum2(y0, mul2(mul2(f2(0.5f), y0), sub2(sub2(f2(1.0f), t.h), t.l)));
+    const dsf2 x = ds_mul2(dup(k.xi), ds_mul2(r2s, rinv));
+    const dsf2 E = exp_neg_ds2(ds_mul2(dup(k.xi2), r2s));      // e^{-xi^2 r^2}
+    const dsf2 A = ds_mul2(ds_mul2(E, erfcx_ds2(x)), rinv);     // erfc(xi r) / r
+    const dsf2 B = ds_mul2(dup(k.c2), E);
+    const dsf2 zero = {f2(0.f), f2(0.f)};
+    const dsf2 nself = {f2(-k.selfc.h), f2(-k.selfc.l)};
+    const dsf2 amb = sel(in0, in1, ds_add2(A, {neg2(B.h), neg2(B.l)}), sel(z0, z1, nself, zero));
+    const dsf2 apb = ds_add2(A, B);
+    const dsf2 f[3] = {{fh[0], fl[0]}, {fh[1], fl[1]}, {fh[2], fl[2]}};
+    const dsf2 rf = ds_add2(ds_add2(ds_mul2(d[0], f[0]), ds_mul2(d[1], f[1])), ds_mul2(d[2], f[2]));
+    const dsf2 co = sel(in0, in1, ds_mul2(ds_mul2(apb, rf), ds_mul2(rinv, rinv)), zero);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        acc[c] = ds_add(acc[c], ds_add(ds_mul(amb, f[c]), ds_mul(co, d[c])));
+        acc[c] = ds_add2(acc[c], ds_add2(ds_mul2(amb, f[c]), ds_mul2(co, d[c])));
 }
 
 // Double-single ring: the FP32 kernel's two 64-source tiles in four groups of
@@ -1129,14 +1161,21 @@ __device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc,
         if (ntile > 1)
             phase1_words(ws.tile.sh[1], tx, ty, tz, lim, q.w2, q.w3);
     }
-    dsf acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    // two sources in flight: the lanes of FP32x2 double-single sums
+    dsf2 acc[3] = {{f2(0.f), f2(0.f)}, {f2(0.f), f2(0.f)}, {f2(0.f), f2(0.f)}};
     for (int o = 0; o < ntile; ++o) {
         const int need = (int)__reduce_max_sync(0xffffffffu, (unsigned)q.pending());
-        for (int it = 0; it < need; ++it) {
-            const int e = q.pop();
-            const float4 sa = ws.tile.sa[e], sb = ws.tile.sb[e], sc = ws.tile.sc[e];
-            pair_ds(th.x - sa.x, th.y - sa.y, th.z - sa.z, tl.x - sa.w, tl.y - sb.x, tl.z - sb.y,
-                    make_float3(sb.z, sb.w, sc.x), make_float3(sc.y, sc.z, sc.w), kc, acc);
+        for (int it = 0; it < (need + 1) >> 1; ++it) {
+            const int e0 = q.pop(), e1 = q.pop();
+            const float4 a0 = ws.tile.sa[e0], b0 = ws.tile.sb[e0], c0 = ws.tile.sc[e0];
+            const float4 a1 = ws.tile.sa[e1], b1 = ws.tile.sb[e1], c1 = ws.tile.sc[e1];
+            const float2 dh[3] = {make_float2(th.x - a0.x, th.x - a1.x), make_float2(th.y - a0.y, th.y - a1.y),
+                                  make_float2(th.z - a0.z, th.z - a1.z)};
+            const float2 dl[3] = {make_float2(tl.x - a0.w, tl.x - a1.w), make_float2(tl.y - b0.x, tl.y - b1.x),
+                                  make_float2(tl.z - b0.y, tl.z - b1.y)};
+            const float2 fh[3] = {make_float2(b0.z, b1.z), make_float2(b0.w, b1.w), make_float2(c0.x, c1.x)};
+            const float2 fl[3] = {make_float2(c0.y, c1.y), make_float2(c0.z, c1.z), make_float2(c0.w, c1.w)};
+            pair_ds2(dh, dl, fh, fl, kc, acc);
         }
         q.shift_if((q.g >> 1) == (o & 1));
         q.shift_if((q.g >> 1) == (o & 1));
@@ -1157,9 +1196,11 @@ __device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc,
         const int i = a.permn[t];
         double *un = (double *)a.un;
         const double inv_cell = 1.0 / a.cell;
-        un[3 * i] = ((double)acc[0].h + (double)acc[0].l) * inv_cell;
-        un[3 * i + 1] = ((double)acc[1].h + (double)acc[1].l) * inv_cell;
-        un[3 * i + 2] = ((double)acc[2].h + (double)acc[2].l) * inv_cell;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const dsf u = ds_add({acc[c].h.x, acc[c].l.x}, {acc[c].h.y, acc[c].l.y});
+            un[3 * i + c] = ((double)u.h + (double)u.l) * inv_cell;
+        }
     }
 }
 
@@ -1257,14 +1298,24 @@ cudaError_t load_p2p_constants()
         e = cudaMemcpyToSymbol(c_erfp64, erf_rat_f64_p, sizeof(erf_rat_f64_p));
     if (e == cudaSuccess)
         e = cudaMemcpyToSymbol(c_erfq64, erf_rat_f64_q, sizeof(erf_rat_f64_q));
-    if (e == cudaSuccess)
-        e = cudaMemcpyToSymbol(c_erfcx_ds_hi, erfcx_ds_hi, sizeof(erfcx_ds_hi));
-    if (e == cudaSuccess)
-        e = cudaMemcpyToSymbol(c_erfcx_ds_lo, erfcx_ds_lo, sizeof(erfcx_ds_lo));
-    if (e == cudaSuccess)
-        e = cudaMemcpyToSymbol(c_exp_ds_hi, exp_ds_hi, sizeof(exp_ds_hi));
-    if (e == cudaSuccess)
-        e = cudaMemcpyToSymbol(c_exp_ds_lo, exp_ds_lo, sizeof(exp_ds_lo));
+    if (e == cudaSuccess) {  // duplicated pairs for the FP32x2 form
+        float2 a[ERFCX_DS_N], b[ERFCX_DS_SPLIT], c[EXP_DS_N], d[6];
+        for (int k = 0; k < ERFCX_DS_N; ++k)
+            a[k] = make_float2(erfcx_ds_hi[k], erfcx_ds_hi[k]);
+        for (int k = 0; k < ERFCX_DS_SPLIT; ++k)
+            b[k] = make_float2(erfcx_ds_lo[k], erfcx_ds_lo[k]);
+        for (int k = 0; k < EXP_DS_N; ++k)
+            c[k] = make_float2(exp_ds_hi[k], exp_ds_hi[k]);
+        for (int k = 0; k < 6; ++k)
+            d[k] = make_float2(exp_ds_lo[k], exp_ds_lo[k]);
+        e = cudaMemcpyToSymbol(c_erfcx_ds2_hi, a, sizeof(a));
+        if (e == cudaSuccess)
+            e = cudaMemcpyToSymbol(c_erfcx_ds2_lo, b, sizeof(b));
+        if (e == cudaSuccess)
+            e = cudaMemcpyToSymbol(c_exp_ds2_hi, c, sizeof(c));
+        if (e == cudaSuccess)
+            e = cudaMemcpyToSymbol(c_exp_ds2_lo, d, sizeof(d));
+    }
     if (e == cudaSuccess && dev >= 0 && dev < 64)
         g_const_loaded[dev] = true;
     return e;

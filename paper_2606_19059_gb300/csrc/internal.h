@@ -142,6 +142,17 @@ struct ewald_plan_s {
     void *fftwork = nullptr;                      // shared cuFFT work area (both plans)
     bool pooled = false;                          // workspaces from the stream-ordered pool
     cudaStream_t s2 = nullptr;                    // second stream: P2P alongside the far field
+    cudaStream_t s3 = nullptr;                    // origin stream of the applies' graph captures
+    struct GraphSlot {                            // a captured apply and the buffers it bakes in
+        enum Mode { kUndecided, kGraph, kDirect };
+        const void *a = nullptr, *b = nullptr, *c = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int calls = 0;                            // calls with these buffers (counted up to 3)
+        Mode mode = kUndecided;                   // replay or direct launches, once both are timed
+        cudaEvent_t ev[4] = {};                   // graph launch and direct apply, start and end
+    };
+    GraphSlot graphs[3];                          // ewald_apply, ewald_apply_forces, ewald_apply_host
+    bool graphs_off = false;                      // a capture failed: direct launches from then on
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev[ewg::kNumEvents] = {};
     int timing = 0;                               // 0 off, 1 timed, 2 timed with serialised stages

@@ -303,6 +303,37 @@ def test_apply_host_equals_device_apply():
     assert errs(uh.numpy(), ud)[1] < 1e-6
 
 
+def test_repeated_apply_sees_new_buffer_contents():
+    """Repeated applies on the same buffers replay a captured graph; the
+    replay must read the buffers' current contents, and new buffers must
+    capture again.  Binning orders each cell's points by atomics, so two
+    applies of the same input differ by FP32 rounding (a few 1e-7); a stale
+    replay would be off by O(1)."""
+    N = 4000
+    x, f = workloads.make("uniform", N, seed=118)
+    x2, g = workloads.make("uniform", N, seed=119)
+    p = plan(N, 1.0, 1e-6, F32)
+    s = torch.cuda.current_stream().cuda_stream
+    xd, fd = dev(x), dev(f)
+    u = torch.empty_like(xd)
+    for _ in range(3):
+        ewald.ewald_apply(p.handle, xd.data_ptr(), fd.data_ptr(), u.data_ptr(), s)
+    ua = host(u)
+    xd.copy_(dev(x2))
+    fd.copy_(dev(g))
+    ewald.ewald_apply(p.handle, xd.data_ptr(), fd.data_ptr(), u.data_ptr(), s)
+    ub = host(u)
+    ref_a = host(plan(N, 1.0, 1e-6, F32).apply(dev(x), dev(f)))
+    ref_b = host(plan(N, 1.0, 1e-6, F32).apply(dev(x2), dev(g)))
+    assert errs(ua, ref_a)[1] < 5e-6
+    assert errs(ub, ref_b)[1] < 5e-6
+    x3d, f3d = dev(x), dev(f)  # new buffers: a new capture
+    u3 = torch.empty_like(x3d)
+    for _ in range(2):
+        ewald.ewald_apply(p.handle, x3d.data_ptr(), f3d.data_ptr(), u3.data_ptr(), s)
+    assert errs(host(u3), ref_a)[1] < 5e-6
+
+
 def test_fp32_and_fp64_agree_to_tolerance():
     x, f = workloads.make("uniform", 20000, seed=117)
     a = host(plan(20000, 1.0, 1e-6, F32, M=64, P=10).apply(dev(x), dev(f)))

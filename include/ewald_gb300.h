@@ -147,9 +147,10 @@ ewald_status ewald_set_positions(ewald_plan_t plan, const double *x, void *strea
 ewald_status ewald_apply_forces(ewald_plan_t plan, const double *f, double *u, void *stream);
 
 /* The full apply with HOST arrays (x, f read; u written; N x 3 FP64 each).
- * Copies host -> device into plan-owned buffers, applies, copies the result
- * back and synchronises `stream` before returning.  Pinned host memory gives
- * the full copy bandwidth; pageable memory works. */
+ * Page-locked buffers (device-addressable) are read and written in place by
+ * the kernels over the CPU-GPU link; pageable ones are copied through
+ * plan-owned device buffers.  Synchronises `stream` before returning, so the
+ * host buffers may be reused at once. */
 ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const double *f_host,
                               double *u_host, void *stream);
 

@@ -643,13 +643,36 @@ ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const dou
         return EWALD_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     size_t bytes = 3 * sizeof(double) * (size_t)plan->N;
-    if (!plan->hx) {
+    // Page-locked buffers have device addresses (unified addressing maps
+    // them); over a coherent CPU-GPU link (NVLink-C2C on GB300) the binning
+    // kernels then read x and f, and the sum kernel writes u, in place: the
+    // bytes cross the link inside those kernels instead of in three staged
+    // copies, each with its own start-up latency.
+    const void *hp[3] = {x_host, f_host, u_host};
+    void *dp[3] = {nullptr, nullptr, nullptr};
+    bool pinned = true;
+    for (int k = 0; k < 3; ++k) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, hp[k]) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            pinned = false;
+        } else {
+            dp[k] = at.devicePointer;
+        }
+    }
+    const bool mapped = pinned && dp[0] && dp[1] && dp[2];
+    if (!mapped && !plan->hx) {  // device staging for the copies
         EW_CUDA(dalloc(plan, &plan->hx, bytes));
         EW_CUDA(dalloc(plan, &plan->hf, bytes));
         EW_CUDA(dalloc(plan, &plan->hu, bytes));
         EW_CUDA(cudaStreamSynchronize(plan->s2));  // pool allocations ready for `s`
     }
     auto body = [&](cudaStream_t cs) -> ewald_status {
+        if (mapped) {
+            rec(plan, 0, cs);
+            EW_ST(bin(plan, (const double *)dp[0], (const double *)dp[1], cs));
+            return compute(plan, (const double *)dp[1], (double *)dp[2], FULL, cs);
+        }
         EW_CUDA(cudaMemcpyAsync(plan->hx, x_host, bytes, cudaMemcpyHostToDevice, cs));
         EW_CUDA(cudaMemcpyAsync(plan->hf, f_host, bytes, cudaMemcpyHostToDevice, cs));
         rec(plan, 0, cs);
@@ -660,14 +683,6 @@ ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const dou
     };
     // graphs only with page-locked host buffers (copies from pageable memory
     // do not capture)
-    bool pinned = true;
-    for (const void *hp : {(const void *)x_host, (const void *)f_host, (const void *)u_host}) {
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, hp) != cudaSuccess || at.type != cudaMemoryTypeHost) {
-            cudaGetLastError();
-            pinned = false;
-        }
-    }
     EW_ST(pinned ? graph_call(plan, 2, x_host, f_host, u_host, s, body) : body(s));
     EW_CUDA(cudaStreamSynchronize(s));
     return EWALD_OK;

@@ -298,9 +298,26 @@ def test_apply_host_equals_device_apply():
     xh = torch.from_numpy(x.copy()).pin_memory()
     fh = torch.from_numpy(f.copy()).pin_memory()
     uh = torch.empty_like(xh).pin_memory()
-    ewald.ewald_apply_host(p.handle, xh.data_ptr(), fh.data_ptr(), uh.data_ptr(),
-                           torch.cuda.current_stream().cuda_stream)
-    assert errs(uh.numpy(), ud)[1] < 1e-6
+    for _ in range(4):  # direct, captured, direct again, then the faster
+        uh.zero_()
+        ewald.ewald_apply_host(p.handle, xh.data_ptr(), fh.data_ptr(), uh.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+        assert errs(uh.numpy(), ud)[1] < 5e-6
+
+
+def test_apply_host_pageable_equals_device_apply():
+    """Pageable host arrays take the staged-copy path (page-locked ones are
+    read and written in place by the kernels)."""
+    x, f = workloads.make("uniform", 3000, seed=120)
+    p = plan(3000, 1.0, 1e-6, F32)
+    ud = host(p.apply(dev(x), dev(f)))
+    xh, fh = np.ascontiguousarray(x), np.ascontiguousarray(f)
+    uh = np.zeros_like(xh)
+    for _ in range(3):
+        ewald.ewald_apply_host(p.handle, xh.ctypes.data, fh.ctypes.data, uh.ctypes.data,
+                               torch.cuda.current_stream().cuda_stream)
+        assert errs(uh, ud)[1] < 5e-6
+        uh[:] = 0.0
 
 
 def test_repeated_apply_sees_new_buffer_contents():

@@ -11,6 +11,9 @@ Contents
   image sum of the bare Stokeslet.  Built here with gcc into ``_oracle.so``.
 * ``spectral.py`` (numpy): the far-field pipeline of Sec. 2.2 (P2G, FFT,
   CNV, IFFT, G2P) with the exact truncated Kaiser-Bessel window.
+* ``stresslet.py`` (numpy): the double-layer (stresslet) part of the combined
+  potential of Sec. 2.3 -- direct Ewald sum, near-field reference and the
+  grid pipeline -- and a textbook Coulomb Ewald sum that pins it.
 """
 from __future__ import annotations
 

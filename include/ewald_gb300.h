@@ -146,6 +146,24 @@ ewald_status ewald_set_positions(ewald_plan_t plan, const double *x, void *strea
  * and new forces f. */
 ewald_status ewald_apply_forces(ewald_plan_t plan, const double *f, double *u, void *stream);
 
+/* Combined single and double layer apply (Sec. 2.3): u = the Stokeslet sum
+ * of the forces f plus the double-layer sum over sources j and periodic
+ * images of T(x_i - y_j + p) applied to q_j (x) n_j, with the stresslet
+ * T_jlm(r) = -6 r_j r_l r_m / |r|^5 (u_j = sum_lm T_jlm q_l n_m; only the
+ * symmetric part of q (x) n enters).  x, f, q, n: device, N x 3 row-major
+ * FP64, read; u: device N x 3 FP64, written.  The double layer uses the
+ * plan's xi, rc, M and P (chosen for the Stokeslet at the plan's tol); on
+ * uniform points its error relative to its own size measured 2e-10 at
+ * tol 1e-8 and 3e-8 at tol 1e-6 (oracle, CPU).  Near field in FP64; far
+ * field in the plan's grid precision.
+ * The first call allocates the double layer's workspaces (two 3-component
+ * grids and spectra, tile-order densities).  Errors: EINVAL (NULL pointer),
+ * EUNSUPPORTED (plans with double-single grid kernels: FP32 bulk below
+ * tol 1e-7), ENOMEM, ECUDA; non-finite q or n raise the device error flag
+ * read by ewald_sync_status. */
+ewald_status ewald_apply_combined(ewald_plan_t plan, const double *x, const double *f, const double *q,
+                                  const double *n, double *u, void *stream);
+
 /* The full apply with HOST arrays (x, f read; u written; N x 3 FP64 each).
  * Page-locked buffers (device-addressable) are read and written in place by
  * the kernels over the CPU-GPU link; pageable ones are copied through

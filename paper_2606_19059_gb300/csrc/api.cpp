@@ -132,7 +132,7 @@ void free_plan(ewald_plan_s *p)
     void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
                     p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec, p->nflo,
                     p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
-                    p->err, p->hx, p->hf, p->hu, p->fftwork, p->wts};
+                    p->err, p->hx, p->hf, p->hu, p->fftwork, p->wts, p->dl_tf, p->dl_grid, p->dl_spec};
     for (void *b : bufs)
         dfree(p, b);
     if (p->own_grid_g2p && p->grid_g2p)
@@ -333,16 +333,29 @@ void rec(ewald_plan_s *p, int i, cudaStream_t s)
 }
 
 // FFT -> CNV -> IFFT on the plan's grid (in place through the spectrum).
-ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s)
+// dl: the double layer's two 3-component grids are transformed too and
+// their v-hat added in the CNV (Sec. 2.3).
+ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s, bool dl = false)
 {
     EW_FFT(cufftSetStream(p->fwd, s));
     EW_FFT(cufftSetStream(p->inv, s));
-    if (p->fft64)
-        EW_FFT(cufftExecD2Z(p->fwd, (cufftDoubleReal *)p->grid, (cufftDoubleComplex *)p->spec));
-    else
-        EW_FFT(cufftExecR2C(p->fwd, (cufftReal *)p->grid, (cufftComplex *)p->spec));
+    const int ntr = dl ? 3 : 1;
+    for (int t = 0; t < ntr; ++t) {
+        const int64_t ro = t == 0 ? 0 : 3 * p->g.nreal * (t - 1), co = t == 0 ? 0 : 3 * p->g.ncplx * (t - 1);
+        if (p->fft64) {
+            cufftDoubleReal *in = t == 0 ? (cufftDoubleReal *)p->grid : (cufftDoubleReal *)p->dl_grid + ro;
+            cufftDoubleComplex *out = t == 0 ? (cufftDoubleComplex *)p->spec : (cufftDoubleComplex *)p->dl_spec + co;
+            EW_FFT(cufftExecD2Z(p->fwd, in, out));
+        } else {
+            cufftReal *in = t == 0 ? (cufftReal *)p->grid : (cufftReal *)p->dl_grid + ro;
+            cufftComplex *out = t == 0 ? (cufftComplex *)p->spec : (cufftComplex *)p->dl_spec + co;
+            EW_FFT(cufftExecR2C(p->fwd, in, out));
+        }
+    }
     rec(p, 3, s);
     EW_CUDA(launch_scale(p, C, s));
+    if (dl)
+        EW_CUDA(launch_scale_dl(p, C, s));
     rec(p, 4, s);
     if (p->fft64)
         EW_FFT(cufftExecZ2D(p->inv, (cufftDoubleComplex *)p->spec, (cufftDoubleReal *)p->grid));
@@ -367,7 +380,14 @@ enum Mode { FULL, NEAR_ONLY, FAR_ONLY };
 
 // Everything after binning.  FULL writes u = near + far - self; NEAR_ONLY /
 // FAR_ONLY write that stage alone (converted to FP64).
-ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cudaStream_t s)
+// The double layer's inputs of a combined apply (Sec. 2.3): user-order
+// positions and the two source vectors q and n.
+struct DlIn {
+    const double *x, *q, *n;
+};
+
+ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cudaStream_t s,
+                     const DlIn *dl = nullptr)
 {
     const double h3 = p->g.h * p->g.h * p->g.h;
     const double M3 = (double)p->g.nreal;
@@ -383,9 +403,22 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
     const bool far_first = overlap && !p->near_ds && !p->near64;
     if (overlap)  // binning done: both branches may start (P2P waits on this)
         EW_CUDA(cudaEventRecord(p->ev_fork, s));
+    // P2G of the Stokeslet forces, then of the double layer's six densities
+    auto p2g = [&]() -> cudaError_t {
+        cudaError_t e = launch_p2g(p, s);
+        if (e != cudaSuccess || !dl)
+            return e;
+        const size_t r4 = p->near64 ? sizeof(dvec4) : sizeof(float4);
+        const size_t gs = p->fft64 ? sizeof(double) : sizeof(float);
+        e = launch_dl_densities(p, dl->q, dl->n, s);
+        for (int t = 0; t < 2 && e == cudaSuccess; ++t)
+            e = launch_p2g_with(p, (const char *)p->dl_tf + t * r4 * p->N,
+                                (char *)p->dl_grid + t * 3 * gs * p->g.nreal, s);
+        return e;
+    };
     if (far_first) {
         rec(p, 1, s);
-        EW_CUDA(launch_p2g(p, s));
+        EW_CUDA(p2g());
         rec(p, 2, s);
     }
     if (mode != FAR_ONLY) {
@@ -400,10 +433,10 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
     if (mode != NEAR_ONLY) {
         if (!far_first) {
             rec(p, 1, s);
-            EW_CUDA(launch_p2g(p, s));
+            EW_CUDA(p2g());
             rec(p, 2, s);
         }
-        EW_ST(fgc(p, 8.0 * kPi * h3 / M3, s));
+        EW_ST(fgc(p, 8.0 * kPi * h3 / M3, s, dl != nullptr));
         EW_CUDA(prep_g2p_grid(p, p->grid, s));
         EW_CUDA(launch_g2p(p, p->grid_g2p, 1.0, s));
         rec(p, 6, s);
@@ -412,6 +445,8 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         EW_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     if (mode == FULL) {
         EW_CUDA(launch_sum(p, f, u, s));
+        if (dl)  // the double layer's near field, added to u
+            EW_CUDA(launch_p2p_dl(p, dl->x, dl->q, dl->n, u, s));
     } else if (mode == NEAR_ONLY) {
         EW_CUDA(launch_copy_out(p->un, p->near64, u, 3 * p->N, s));
     } else {
@@ -646,6 +681,31 @@ ewald_status ewald_apply_forces(ewald_plan_t plan, const double *f, double *u, v
         EW_CUDA(launch_gather_forces(plan, f, s));
         return compute(plan, f, u, FULL, s);
     });
+}
+
+ewald_status ewald_apply_combined(ewald_plan_t plan, const double *x, const double *f, const double *q,
+                                  const double *n, double *u, void *stream)
+{
+    if (!plan || bad_ptr(x) || bad_ptr(f) || bad_ptr(q) || bad_ptr(n) || bad_ptr(u))
+        return EWALD_EINVAL;
+    if (plan->grid_ds)
+        return EWALD_EUNSUPPORTED;
+    DeviceGuard dg(plan->device);
+    if (!dg.ok)
+        return EWALD_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!plan->dl_tf) {
+        const size_t r4 = plan->near64 ? sizeof(dvec4) : sizeof(float4);
+        const size_t gs = plan->fft64 ? sizeof(double) : sizeof(float);
+        EW_CUDA(dalloc(plan, &plan->dl_tf, 2 * r4 * (size_t)plan->N));
+        EW_CUDA(dalloc(plan, &plan->dl_grid, 2 * 3 * gs * (size_t)plan->g.nreal));
+        EW_CUDA(dalloc(plan, &plan->dl_spec, 2 * 3 * 2 * gs * (size_t)plan->g.ncplx));
+        EW_CUDA(cudaStreamSynchronize(plan->s2));  // pool allocations ready for `s`
+    }
+    rec(plan, 0, s);
+    EW_ST(bin(plan, x, f, s));
+    const DlIn dl{x, q, n};
+    return compute(plan, f, u, FULL, s, &dl);
 }
 
 ewald_status ewald_apply_host(ewald_plan_t plan, const double *x_host, const double *f_host,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
+#include <cmath>
 
 #include <vector>
 
@@ -16,6 +17,20 @@ namespace ewg {
 struct __align__(32) dvec4 {
     double x, y, z, w;
 };
+
+// A coordinate wrapped into [0, L) the way binning places points: positions
+// already inside are left as they are (inv_L = 1.0 / L).
+__host__ __device__ inline double wrap_coord(double v, double L, double inv_L)
+{
+    if (v < 0.0 || v >= L) {
+        v -= L * floor(v * inv_L);
+        if (v >= L)
+            v -= L;
+    }
+    if (v < 0.0)
+        v = 0.0;
+    return v;
+}
 
 constexpr int kSub = 2;             // sub-cells per near cell per side (target ordering)
 constexpr int kSub3 = kSub * kSub * kSub;
@@ -130,6 +145,10 @@ struct ewald_plan_s {
     void *grid = nullptr;                         // 3 M^3 real
     void *grid_g2p = nullptr;                     // G2P input in the kernels' precision (may alias grid)
     bool own_grid_g2p = false;
+    // double layer (Sec. 2.3), allocated by the first combined apply: the
+    // tile-order symmetric densities (2 x N quadruples in the P2G input
+    // precision), their two 3-component grids and half spectra
+    void *dl_tf = nullptr, *dl_grid = nullptr, *dl_spec = nullptr;
     void *spec = nullptr;                         // 3 M^2 (M/2+1) complex
     void *tab = nullptr;                          // CNV 1-D table (M entries)
     void *wcoef_dev = nullptr;                    // window polynomial coefficients
@@ -191,6 +210,14 @@ cudaError_t launch_gather_forces(ewald_plan_s *p, const double *f, cudaStream_t 
 cudaError_t launch_cell_items(ewald_plan_s *p, cudaStream_t s);  // the work items alone
 cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s);
+// P2G of three tile-order source components `tfrc` (the plan's force layout)
+// onto the 3-component grid `grid`
+cudaError_t launch_p2g_with(ewald_plan_s *p, const void *tfrc, void *grid, cudaStream_t s);
+// double layer (k_dl.cu)
+cudaError_t launch_dl_densities(ewald_plan_s *p, const double *q, const double *n, cudaStream_t s);
+cudaError_t launch_scale_dl(ewald_plan_s *p, double C, cudaStream_t s);
+cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, const double *n, double *u,
+                          cudaStream_t s);
 cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);
 // G2P from a grid in the kernels' precision (FP64 when near64, else FP32; the
 // double-single planes for grid_ds plans); the sum is multiplied by `scale`.

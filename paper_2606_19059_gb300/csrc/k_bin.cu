@@ -57,13 +57,7 @@ __device__ __forceinline__ Bin compute_bin(const KeyArgs &k, int64_t i)
         }
         // wrap into [0, L) (positions already inside skip it: FP64 runs at a
         // small fraction of the FP32 rate here, and binning is FP64-bound)
-        if (v < 0.0 || v >= k.L) {
-            v -= k.L * floor(v * k.inv_L);
-            if (v >= k.L)
-                v -= k.L;
-        }
-        if (v < 0.0)
-            v = 0.0;
+        v = wrap_coord(v, k.L, k.inv_L);
         b.xw[d] = v;
         double q = v * k.inv_cell;
         int ci = min(max((int)q, 0), k.nc - 1);

@@ -930,6 +930,16 @@ cudaError_t launch_p2g(ewald_plan_s *p, cudaStream_t s)
     return p->g.T == 8 ? dispatch_p2g<8>(p, a, s) : dispatch_p2g<4>(p, a, s);
 }
 
+cudaError_t launch_p2g_with(ewald_plan_s *p, const void *tfrc, void *grid, cudaStream_t s)
+{
+    if (p->grid_ds)
+        return cudaErrorNotSupported;
+    GridArgs a = grid_args(p);
+    a.tfrc = tfrc;
+    a.grid = grid;
+    return p->g.T == 8 ? dispatch_p2g<8>(p, a, s) : dispatch_p2g<4>(p, a, s);
+}
+
 // G2P from a grid in the kernels' precision (FP64 when near64, else FP32;
 // double-single h and l planes for the double-single kernels).
 cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s)

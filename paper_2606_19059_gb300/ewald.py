@@ -80,6 +80,7 @@ _SIGS = [
     ("ewald_apply", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("ewald_set_positions", ctypes.c_int, [_P, _P, _P]),
     ("ewald_apply_forces", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ewald_apply_combined", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("ewald_apply_host", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("ewald_near_field", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("ewald_far_field", ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -195,6 +196,10 @@ def ewald_set_positions(plan, x_ptr, stream=0):
 
 def ewald_apply_forces(plan, f_ptr, u_ptr, stream=0):
     _call("ewald_apply_forces", plan, f_ptr, u_ptr, stream)
+
+
+def ewald_apply_combined(plan, x_ptr, f_ptr, q_ptr, n_ptr, u_ptr, stream=0):
+    _call("ewald_apply_combined", plan, x_ptr, f_ptr, q_ptr, n_ptr, u_ptr, stream)
 
 
 def ewald_apply_host(plan, x_ptr, f_ptr, u_ptr, stream=0):
@@ -512,6 +517,17 @@ class Plan:
         self._check_arr(f, (self.N, 3))
         u = out if out is not None else torch.empty_like(x)
         ewald_apply(self.handle, x.data_ptr(), f.data_ptr(), u.data_ptr(), self._stream(stream))
+        return u
+
+    def apply_combined(self, x, f, q, n, out=None, stream=None):
+        """Stokeslet sum of f plus the double-layer sum of q (x) n (Sec. 2.3)."""
+        import torch
+
+        for a in (x, f, q, n):
+            self._check_arr(a, (self.N, 3))
+        u = out if out is not None else torch.empty_like(x)
+        ewald_apply_combined(self.handle, x.data_ptr(), f.data_ptr(), q.data_ptr(), n.data_ptr(),
+                             u.data_ptr(), self._stream(stream))
         return u
 
     def set_positions(self, x, stream=None):

@@ -217,10 +217,41 @@ def run_gpu(args, rank, world):
         ewald.ewald_apply_host(plan32.handle, xh.data_ptr(), fh.data_ptr(), uh.data_ptr(), sp)
         e2e.append(time.perf_counter() - t)
 
+    # combined single and double layer apply (Sec. 2.3) on the same points:
+    # synthetic source vectors q, n ~ N(0, 1) per component
+    dl = None
+    if not args.no_double_layer:
+        rng = np.random.default_rng(seed + 7 + rank)
+        qd = torch.tensor(rng.standard_normal((N, 3)), device=dev)
+        nd = torch.tensor(rng.standard_normal((N, 3)), device=dev)
+
+        def combined():
+            ewald.ewald_apply_combined(plan32.handle, xd.data_ptr(), fd.data_ptr(), qd.data_ptr(),
+                                       nd.data_ptr(), ud.data_ptr(), sp)
+
+        for _ in range(3):
+            combined()
+        torch.cuda.synchronize()
+        ms_dl = []
+        for _ in range(max(3, args.steps // 20)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            combined()
+            b.record(stream)
+            b.synchronize()
+            ms_dl.append(a.elapsed_time(b))
+        ewald.ewald_set_timing(plan32.handle, 2)
+        flush.zero_()
+        combined()
+        st_dl = ewald.ewald_stage_times(plan32.handle)
+        ewald.ewald_set_timing(plan32.handle, 0)
+        dl = {"ms": ms_dl, "stages": st_dl}
+
     kern, nfft = ewald.ewald_launch_counts(plan32.handle)
     prm = plan32.params
     res = {
-        "ms32": ms32, "wall32": wall32, "ms64": ms64, "stages": stages, "e2e_s": e2e,
+        "ms32": ms32, "wall32": wall32, "ms64": ms64, "stages": stages, "e2e_s": e2e, "dl": dl,
         "clocks": clocks, "kernels_per_step": kern, "ffts_per_step": nfft, "params": prm.as_dict(),
         "N": N, "L": L, "tol": tol, "M": M, "P": P, "x": x if rank == 0 else None,
     }
@@ -361,6 +392,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the many-box batched run")
     ap.add_argument("--batch-boxes", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-double-layer", action="store_true",
+                    help="skip the combined single + double layer measurement")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rates", default="2,8",
                     help="Poisson arrival rates (requests/s), comma-separated: the first is the reported "
@@ -476,6 +509,18 @@ def main():
             "gpu_launches": res["kernels_per_step"] * args.steps,
             "clocks": res["clocks"],
         }
+        if res["dl"] is not None:
+            dms = float(np.median(res["dl"]["ms"]))
+            sd = res["dl"]["stages"]
+            line["double_layer"] = {
+                "what": "combined single + double layer apply (Sec. 2.3), same points, q and n ~ N(0, 1)",
+                "value": world * N / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
+                "stages_ms": {k: round(v, 5) for k, v in sd.items()},
+                # the double layer's FP64 near field runs after the sum: the
+                # difference of the two plans' sum stages is its time
+                "near_dl_ms": round(sd["sum_ms"] - st["sum_ms"], 5),
+                "near_dl_kernel": "k_p2p_dl (FP64, one thread per target)",
+            }
         if not args.no_batch:
             line["batched"] = run_batch(args, rank)
         if not args.no_serve:

@@ -132,7 +132,7 @@ void free_plan(ewald_plan_s *p)
     void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
                     p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec, p->nflo,
                     p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
-                    p->err, p->hx, p->hf, p->hu, p->fftwork, p->wts, p->dl_tf, p->dl_grid, p->dl_spec};
+                    p->err, p->hx, p->hf, p->hu, p->fftwork, p->wts, p->dl_tf, p->dl_grid, p->dl_spec, p->dl_near};
     for (void *b : bufs)
         dfree(p, b);
     if (p->own_grid_g2p && p->grid_g2p)
@@ -700,6 +700,7 @@ ewald_status ewald_apply_combined(ewald_plan_t plan, const double *x, const doub
         EW_CUDA(dalloc(plan, &plan->dl_tf, 2 * r4 * (size_t)plan->N));
         EW_CUDA(dalloc(plan, &plan->dl_grid, 2 * 3 * gs * (size_t)plan->g.nreal));
         EW_CUDA(dalloc(plan, &plan->dl_spec, 2 * 3 * 2 * gs * (size_t)plan->g.ncplx));
+        EW_CUDA(dalloc(plan, &plan->dl_near, (3 * sizeof(dvec4) + 4 * sizeof(float4)) * (size_t)plan->N));
         EW_CUDA(cudaStreamSynchronize(plan->s2));  // pool allocations ready for `s`
     }
     rec(plan, 0, s);

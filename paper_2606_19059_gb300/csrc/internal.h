@@ -149,6 +149,7 @@ struct ewald_plan_s {
     // tile-order symmetric densities (2 x N quadruples in the P2G input
     // precision), their two 3-component grids and half spectra
     void *dl_tf = nullptr, *dl_grid = nullptr, *dl_spec = nullptr;
+    void *dl_near = nullptr;  // near-sorted positions, q, n (3 x N dvec4) and FP32 local hi, lo, q, n (4 x N float4)
     void *spec = nullptr;                         // 3 M^2 (M/2+1) complex
     void *tab = nullptr;                          // CNV 1-D table (M entries)
     void *wcoef_dev = nullptr;                    // window polynomial coefficients

@@ -21,9 +21,11 @@
 // before the one inverse FFT and G2P.  T^F is odd: no self term.
 //
 // Kernels: k_dl_densities (tile-order S, the P2G input format), k_scale_dl
-// (CNV, HBM-bound: 6 complex components in, 3 read-modify-written), and
-// k_p2p_dl (near field in FP64, one thread per target in near-sorted order,
-// (2K+1)^3 neighbour cells of the plan's cell lists).
+// (CNV, HBM-bound: 6 complex components in, 3 read-modify-written), k_dl_sort
+// (near-sorted copies of positions, q and n) and k_p2p_dl (near field: an FP32
+// distance filter over the (2K+1)^3 neighbour cells of the plan's cell lists,
+// then the pair arithmetic for queued in-range pairs only -- FP32 where the
+// plan's FFTs are FP32, FP64 otherwise -- summed in FP64).
 #include "internal.h"
 
 namespace ewg {
@@ -113,72 +115,215 @@ __global__ void __launch_bounds__(256) k_scale_dl(C2 *__restrict__ spec, const C
 }
 
 struct DlNearArgs {
-    const double *x, *q, *n;
     const int32_t *permn, *keyn, *startn;
+    const dvec4 *pos, *qs, *ns;       // near-sorted: wrapped positions, q, n (FP64 pairs)
+    const float4 *lhi, *llo;          // near-sorted cell-local positions, hi + lo parts
+    const float4 *q32, *n32;          // near-sorted q, n in FP32 (FP32 pairs)
     double *u;
     int64_t N;
-    double L, inv_L, xi, rc2;
+    double L, xi, rc2;
+    float w_hi, w_lo;                 // cell width as hi + lo
+    float rcm2;                       // FP32 filter threshold: rc grown past FP32 rounding
     int nc, K;
 };
 
+// near-sorted copies (slot s holds source permn[s]): wrapped positions, q and
+// n in FP64; cell-local positions (wrapped position - corner of its cell) as
+// FP32 hi + lo parts, and q, n in FP32
+__global__ void __launch_bounds__(256) k_dl_sort(const double *__restrict__ x, const double *__restrict__ q,
+                                                 const double *__restrict__ n, const int32_t *__restrict__ permn,
+                                                 const int32_t *__restrict__ keyn, int64_t N, double L,
+                                                 double inv_L, double cell, int nc, dvec4 *pos, dvec4 *qs,
+                                                 dvec4 *ns, float4 *lhi, float4 *llo, float4 *q32, float4 *n32)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N)
+        return;
+    const int64_t j = permn[s];
+    const int c = keyn[j] / kSub3;
+    const int cc[3] = {c % nc, (c / nc) % nc, c / (nc * nc)};
+    double w[3];
+    float h[3], l[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        w[d] = wrap_coord(x[3 * j + d], L, inv_L);
+        const double loc = w[d] - cc[d] * cell;
+        h[d] = (float)loc;
+        l[d] = (float)(loc - (double)h[d]);
+    }
+    dvec4 v;
+    v.x = w[0];
+    v.y = w[1];
+    v.z = w[2];
+    v.w = 0.0;
+    pos[s] = v;
+    lhi[s] = make_float4(h[0], h[1], h[2], 0.f);
+    llo[s] = make_float4(l[0], l[1], l[2], 0.f);
+    dvec4 a, b;
+    a.x = q[3 * j];
+    a.y = q[3 * j + 1];
+    a.z = q[3 * j + 2];
+    a.w = 0.0;
+    b.x = n[3 * j];
+    b.y = n[3 * j + 1];
+    b.z = n[3 * j + 2];
+    b.w = 0.0;
+    qs[s] = a;
+    ns[s] = b;
+    q32[s] = make_float4((float)a.x, (float)a.y, (float)a.z, 0.f);
+    n32[s] = make_float4((float)b.x, (float)b.y, (float)b.z, 0.f);
+}
+
 __device__ __forceinline__ int floor_div(int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); }
 
-// u_i += sum over sources j and images within rc of T^N(x_i - y_j - p) : S_j,
-// one thread per target in near-sorted order (so a warp's targets share cells)
-__global__ void __launch_bounds__(128) k_p2p_dl(DlNearArgs a)
+constexpr int kDlWarps = 4;
+constexpr int kDlQ = 16;  // queued in-range sources per lane before an evaluation round
+
+struct DlQueue {
+    int src[kDlQ][32];   // [entry][lane]: a lane touches only its own column
+    int code[kDlQ][32];  // neighbour cell offset (ox, oy, oz), each biased by 64 into 8 bits
+};
+
+// T^N(r) : S of one pair, r = target - source image, in precision R
+template <typename R>
+__device__ __forceinline__ void dl_pair(R r0, R r1, R r2, R rr2, R q0, R q1, R q2, R n0, R n1, R n2, R xi,
+                                        R c_e, R &u0, R &u1, R &u2)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.N)
-        return;
-    const int i = a.permn[t];
-    const int nc = a.nc, K = a.K;
-    const int c = a.keyn[i] / kSub3;
-    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-    const double xi0 = wrap_coord(a.x[3 * i], a.L, a.inv_L);
-    const double xi1 = wrap_coord(a.x[3 * i + 1], a.L, a.inv_L);
-    const double xi2 = wrap_coord(a.x[3 * i + 2], a.L, a.inv_L);
-    const double xi = a.xi, c_e = 2.0 * xi / 1.7724538509055160273;  // 2 xi / sqrt(pi)
+    const R qr = fma(q0, r0, fma(q1, r1, q2 * r2));
+    const R nr = fma(n0, r0, fma(n1, r1, n2 * r2));
+    const R qn = fma(q0, n0, fma(q1, n1, q2 * n2));
+    const R rr = sqrt(rr2), inv2 = (R)1 / rr2;
+    const R e = exp(-xi * xi * rr2);
+    const R beta = (R)-3 * erfc(xi * rr) * inv2 * inv2 / rr - c_e * ((R)3 * inv2 * inv2 + (R)2 * xi * xi * inv2) * e;
+    const R gamma = c_e * xi * xi * e;
+    // 2 beta r (q.r)(n.r) + 2 gamma (r q.n + q n.r + n q.r)
+    const R br = (R)2 * beta * qr * nr, g2 = (R)2 * gamma;
+    u0 += br * r0 + g2 * (r0 * qn + q0 * nr + n0 * qr);
+    u1 += br * r1 + g2 * (r1 * qn + q1 * nr + n1 * qr);
+    u2 += br * r2 + g2 * (r2 * qn + q2 * nr + n2 * qr);
+}
+
+// u_i += sum over sources j and images within rc of T^N(x_i - y_j - p) : S_j.
+// One warp per 32 near-sorted targets, one lane per target.  Each lane walks
+// the sources of its (2K+1)^3 neighbour cells with an FP32 distance test on
+// cell-local coordinates (threshold rc grown past FP32 rounding) and queues
+// the sources that pass; when a lane's queue is full, every lane evaluates
+// its queued pairs and sums its own target -- so the pair arithmetic runs for
+// in-range pairs only, with the warp's lanes busy, and no atomics.
+//   R = float: r = ((t_hi - o w_hi) - s_hi) + ((t_lo - o w_lo) - s_lo) from
+//     the cell-local hi + lo parts (o the cell offset; relative error of r
+//     ~1e-7 down to coincident points), the cutoff and the pair in FP32, one
+//     FP32 partial sum per round added to the FP64 total;
+//   R = double: r from the wrapped FP64 positions and the image shift of the
+//     cell offset, the cutoff and the pair in FP64.
+template <typename R>
+__global__ void __launch_bounds__(kDlWarps * 32) k_p2p_dl(DlNearArgs a)
+{
+    __shared__ DlQueue wq[kDlWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    DlQueue &w = wq[warp];
+    const int64_t t = ((int64_t)blockIdx.x * kDlWarps + warp) * 32 + lane;
+    const bool active = t < a.N;
+    const int nc = a.nc, K = a.K, side = 2 * K + 1, nO = side * side * side;
+    int i = 0, cx = 0, cy = 0, cz = 0;
+    float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+    if (active) {
+        i = a.permn[t];
+        const int c = a.keyn[i] / kSub3;
+        cx = c % nc;
+        cy = (c / nc) % nc;
+        cz = c / (nc * nc);
+        th = a.lhi[t];
+        tl = a.llo[t];
+    }
+    // walk state: next neighbour offset oi, current source range [s, se) of
+    // the neighbour cell at offset (ox, oy, oz), and the target relative to it
+    int oi = active ? 0 : nO, s = 0, se = 0, code = 0;
+    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    auto next_cell = [&]() {
+        while (s == se && oi < nO) {
+            const int ox = oi % side - K, oy = (oi / side) % side - K, oz = oi / (side * side) - K;
+            ++oi;
+            const int ax = cx + ox, ay = cy + oy, az = cz + oz;
+            const int bx = ax - floor_div(ax, nc) * nc, by = ay - floor_div(ay, nc) * nc,
+                      bz = az - floor_div(az, nc) * nc;
+            const int nb = (bz * nc + by) * nc + bx;
+            s = a.startn[nb * kSub3];
+            se = a.startn[(nb + 1) * kSub3];
+            code = (ox + 64) | ((oy + 64) << 8) | ((oz + 64) << 16);
+            b0 = fmaf(-(float)ox, a.w_hi, th.x);
+            b1 = fmaf(-(float)oy, a.w_hi, th.y);
+            b2 = fmaf(-(float)oz, a.w_hi, th.z);
+        }
+    };
+    next_cell();
+    const R xi = (R)a.xi, c_e = (R)(2.0 * a.xi / 1.7724538509055160273);  // 2 xi / sqrt(pi)
     double u0 = 0.0, u1 = 0.0, u2 = 0.0;
-    for (int oz = -K; oz <= K; ++oz) {
-        const int az = cz + oz, sz = floor_div(az, nc), bz = az - sz * nc;
-        for (int oy = -K; oy <= K; ++oy) {
-            const int ay = cy + oy, sy = floor_div(ay, nc), by = ay - sy * nc;
-            for (int ox = -K; ox <= K; ++ox) {
-                const int ax = cx + ox, sx = floor_div(ax, nc), bx = ax - sx * nc;
-                const int nb = (bz * nc + by) * nc + bx;
-                const int s0 = a.startn[nb * kSub3], s1 = a.startn[(nb + 1) * kSub3];
-                // the image of cell nb that sits at (ax, ay, az): sources shifted by L (sx, sy, sz)
-                const double b0 = xi0 - a.L * sx, b1 = xi1 - a.L * sy, b2 = xi2 - a.L * sz;
-                for (int s = s0; s < s1; ++s) {
-                    const int j = a.permn[s];
-                    const double r0 = b0 - wrap_coord(a.x[3 * j], a.L, a.inv_L);
-                    const double r1 = b1 - wrap_coord(a.x[3 * j + 1], a.L, a.inv_L);
-                    const double r2 = b2 - wrap_coord(a.x[3 * j + 2], a.L, a.inv_L);
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    if constexpr (sizeof(R) == 8) {
+        if (active) {
+            const dvec4 P = a.pos[t];
+            t0 = P.x;
+            t1 = P.y;
+            t2 = P.z;
+        }
+    }
+    int len = 0;
+    auto evaluate = [&]() {
+        const int m = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+        R v0 = 0, v1 = 0, v2 = 0;
+        for (int k = 0; k < m; ++k) {
+            if (k < len) {
+                const int sj = w.src[k][lane], cd = w.code[k][lane];
+                const int ox = (cd & 255) - 64, oy = ((cd >> 8) & 255) - 64, oz = ((cd >> 16) & 255) - 64;
+                if constexpr (sizeof(R) == 4) {
+                    const float4 Sh = a.lhi[sj], Sl = a.llo[sj];
+                    const float r0 = (fmaf(-(float)ox, a.w_hi, th.x) - Sh.x) + (fmaf(-(float)ox, a.w_lo, tl.x) - Sl.x);
+                    const float r1 = (fmaf(-(float)oy, a.w_hi, th.y) - Sh.y) + (fmaf(-(float)oy, a.w_lo, tl.y) - Sl.y);
+                    const float r2 = (fmaf(-(float)oz, a.w_hi, th.z) - Sh.z) + (fmaf(-(float)oz, a.w_lo, tl.z) - Sl.z);
+                    const float rr2 = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
+                    if (rr2 <= (float)a.rc2 && rr2 > 0.f) {
+                        const float4 Q = a.q32[sj], Nn = a.n32[sj];
+                        dl_pair<float>(r0, r1, r2, rr2, Q.x, Q.y, Q.z, Nn.x, Nn.y, Nn.z, xi, c_e, v0, v1, v2);
+                    }
+                } else {
+                    const int sx = floor_div(cx + ox, nc), sy = floor_div(cy + oy, nc), sz = floor_div(cz + oz, nc);
+                    const dvec4 P = a.pos[sj];
+                    const double r0 = (t0 - a.L * sx) - P.x, r1 = (t1 - a.L * sy) - P.y, r2 = (t2 - a.L * sz) - P.z;
                     const double rr2 = fma(r0, r0, fma(r1, r1, r2 * r2));
-                    if (rr2 > a.rc2 || rr2 == 0.0)
-                        continue;
-                    const double q0 = a.q[3 * j], q1 = a.q[3 * j + 1], q2 = a.q[3 * j + 2];
-                    const double n0 = a.n[3 * j], n1 = a.n[3 * j + 1], n2 = a.n[3 * j + 2];
-                    const double qr = fma(q0, r0, fma(q1, r1, q2 * r2));
-                    const double nr = fma(n0, r0, fma(n1, r1, n2 * r2));
-                    const double qn = fma(q0, n0, fma(q1, n1, q2 * n2));
-                    const double rr = sqrt(rr2), inv2 = 1.0 / rr2;
-                    const double e = exp(-xi * xi * rr2);
-                    const double beta = -3.0 * erfc(xi * rr) * inv2 * inv2 / rr -
-                                        c_e * (3.0 * inv2 * inv2 + 2.0 * xi * xi * inv2) * e;
-                    const double gamma = c_e * xi * xi * e;
-                    // 2 beta r (q.r)(n.r) + 2 gamma (r q.n + q n.r + n q.r)
-                    const double br = 2.0 * beta * qr * nr, g2 = 2.0 * gamma;
-                    u0 += br * r0 + g2 * (r0 * qn + q0 * nr + n0 * qr);
-                    u1 += br * r1 + g2 * (r1 * qn + q1 * nr + n1 * qr);
-                    u2 += br * r2 + g2 * (r2 * qn + q2 * nr + n2 * qr);
+                    if (rr2 <= a.rc2 && rr2 > 0.0) {
+                        const dvec4 Q = a.qs[sj], Nn = a.ns[sj];
+                        dl_pair<double>(r0, r1, r2, rr2, Q.x, Q.y, Q.z, Nn.x, Nn.y, Nn.z, xi, c_e, v0, v1, v2);
+                    }
                 }
             }
         }
+        u0 += (double)v0;
+        u1 += (double)v1;
+        u2 += (double)v2;
+        len = 0;
+    };
+    while (__any_sync(0xffffffffu, s < se)) {
+        if (s < se) {
+            const float4 P = a.lhi[s];
+            const float r0 = b0 - P.x, r1 = b1 - P.y, r2 = b2 - P.z;
+            if (fmaf(r0, r0, fmaf(r1, r1, r2 * r2)) <= a.rcm2) {
+                w.src[len][lane] = s;
+                w.code[len][lane] = code;
+                ++len;
+            }
+            ++s;
+            next_cell();
+        }
+        if (__any_sync(0xffffffffu, len == kDlQ))
+            evaluate();
     }
-    a.u[3 * i] += u0;
-    a.u[3 * i + 1] += u1;
-    a.u[3 * i + 2] += u2;
+    evaluate();
+    if (active) {
+        a.u[3 * i] += u0;
+        a.u[3 * i + 1] += u1;
+        a.u[3 * i + 2] += u2;
+    }
 }
 
 }  // namespace
@@ -220,23 +365,44 @@ cudaError_t launch_scale_dl(ewald_plan_s *p, double C, cudaStream_t s)
 cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, const double *n, double *u,
                           cudaStream_t s)
 {
+    const int64_t N = p->N;
+    dvec4 *pos = (dvec4 *)p->dl_near, *qs = pos + N, *ns = qs + N;
+    float4 *lhi = (float4 *)(ns + N), *llo = lhi + N, *q32 = llo + N, *n32 = q32 + N;
+    k_dl_sort<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(x, q, n, p->permn, p->keyn, N, p->prm.L, 1.0 / p->prm.L,
+                                                          p->g.cell, p->g.nc, pos, qs, ns, lhi, llo, q32, n32);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
     DlNearArgs a;
-    a.x = x;
-    a.q = q;
-    a.n = n;
     a.permn = p->permn;
     a.keyn = p->keyn;
     a.startn = p->startn;
+    a.pos = pos;
+    a.qs = qs;
+    a.ns = ns;
+    a.lhi = lhi;
+    a.llo = llo;
+    a.q32 = q32;
+    a.n32 = n32;
     a.u = u;
-    a.N = p->N;
+    a.N = N;
     a.L = p->prm.L;
-    a.inv_L = 1.0 / p->prm.L;
     a.xi = p->prm.xi;
     a.rc2 = p->prm.rc * p->prm.rc;
+    a.w_hi = (float)p->g.cell;
+    a.w_lo = (float)(p->g.cell - (double)a.w_hi);
+    // the filter works on the hi parts alone: each is within 2^-24 of its
+    // cell-local value (|lo| <= 2^-24 cell), so 1e-4 rc + 1e-5 cell covers it
+    const double rcm = p->prm.rc * (1.0 + 1e-4) + 1e-5 * p->g.cell;
+    a.rcm2 = (float)(rcm * rcm);
     a.nc = p->g.nc;
     a.K = p->g.K;
-    const unsigned nb = (unsigned)((p->N + 127) / 128);
-    k_p2p_dl<<<nb, 128, 0, s>>>(a);
+    const unsigned nb = (unsigned)((N + 32 * kDlWarps - 1) / (32 * kDlWarps));
+    // FP32 pair arithmetic where the plan's FFTs are FP32 (tol >= 1e-6), FP64 below
+    if (p->fft64 || p->near64)
+        k_p2p_dl<double><<<nb, 32 * kDlWarps, 0, s>>>(a);
+    else
+        k_p2p_dl<float><<<nb, 32 * kDlWarps, 0, s>>>(a);
     return cudaGetLastError();
 }
 

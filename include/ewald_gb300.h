@@ -154,8 +154,10 @@ ewald_status ewald_apply_forces(ewald_plan_t plan, const double *f, double *u, v
  * FP64, read; u: device N x 3 FP64, written.  The double layer uses the
  * plan's xi, rc, M and P (chosen for the Stokeslet at the plan's tol); on
  * uniform points its error relative to its own size measured 2e-10 at
- * tol 1e-8 and 3e-8 at tol 1e-6 (oracle, CPU).  Near field in FP64; far
- * field in the plan's grid precision.
+ * tol 1e-8 and 3e-8 at tol 1e-6 (oracle, CPU).  Near-field pairs in FP32
+ * (from cell-local hi + lo coordinates) where the plan's FFTs are FP32
+ * (tol >= 1e-6), else in FP64, summed in FP64; far field in the plan's grid
+ * precision.
  * The first call allocates the double layer's workspaces (two 3-component
  * grids and spectra, tile-order densities).  Errors: EINVAL (NULL pointer),
  * EUNSUPPORTED (plans with double-single grid kernels: FP32 bulk below

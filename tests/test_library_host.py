@@ -169,3 +169,12 @@ def test_erfcx_fp32_form_meets_bound():
     rel = np.abs(g - special.erfcx(x)) / special.erfcx(x)
     assert rel.max() <= 1.5 * const("ERFCX_F32_MAXERR")
     assert rel.max() < 1e-8
+
+
+def test_apply_entry_points_reject_null_plan_on_the_host():
+    # argument checks come before any CUDA call, so they run without a GPU
+    for fn, nargs in ((ewald.ewald_apply, 3), (ewald.ewald_apply_forces, 2),
+                      (ewald.ewald_apply_combined, 5), (ewald.ewald_apply_host, 3)):
+        with pytest.raises(ewald.EwaldError) as e:
+            fn(None, *([None] * nargs))
+        assert e.value.status == ewald.EWALD_EINVAL

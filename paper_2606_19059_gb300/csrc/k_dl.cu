@@ -117,23 +117,25 @@ __global__ void __launch_bounds__(256) k_scale_dl(C2 *__restrict__ spec, const C
 struct DlNearArgs {
     const int32_t *permn, *keyn, *startn;
     const dvec4 *pos, *qs, *ns;       // near-sorted: wrapped positions, q, n (FP64 pairs)
-    const float4 *lhi, *llo;          // near-sorted cell-local positions, hi + lo parts
+    const float4 *lhi, *llo;          // near-sorted cell-local positions in cell units, hi + lo parts
     const float4 *q32, *n32;          // near-sorted q, n in FP32 (FP32 pairs)
     double *u;
     int64_t N;
     double L, xi, rc2;
-    float w_hi, w_lo;                 // cell width as hi + lo
-    float rcm2;                       // FP32 filter threshold: rc grown past FP32 rounding
+    float w;                          // cell width
+    float rcm2;                       // FP32 filter threshold, cell units: rc / w grown past the lo parts
     int nc, K;
 };
 
 // near-sorted copies (slot s holds source permn[s]): wrapped positions, q and
-// n in FP64; cell-local positions (wrapped position - corner of its cell) as
-// FP32 hi + lo parts, and q, n in FP32
+// n in FP64; the cell-local position in cell units, q = x / cell - c, as FP32
+// parts hi (rounded to a 2^-20 lattice, so hi minus an integer neighbour
+// offset and differences of such values are exact in FP32) and lo = q - hi
+// (|lo| <= 2^-21); q and n in FP32
 __global__ void __launch_bounds__(256) k_dl_sort(const double *__restrict__ x, const double *__restrict__ q,
                                                  const double *__restrict__ n, const int32_t *__restrict__ permn,
                                                  const int32_t *__restrict__ keyn, int64_t N, double L,
-                                                 double inv_L, double cell, int nc, dvec4 *pos, dvec4 *qs,
+                                                 double inv_L, double inv_cell, int nc, dvec4 *pos, dvec4 *qs,
                                                  dvec4 *ns, float4 *lhi, float4 *llo, float4 *q32, float4 *n32)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,9 +149,10 @@ __global__ void __launch_bounds__(256) k_dl_sort(const double *__restrict__ x, c
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         w[d] = wrap_coord(x[3 * j + d], L, inv_L);
-        const double loc = w[d] - cc[d] * cell;
-        h[d] = (float)loc;
-        l[d] = (float)(loc - (double)h[d]);
+        const double qd = w[d] * inv_cell - cc[d];
+        const double X = rint(qd * 1048576.0) * (1.0 / 1048576.0);
+        h[d] = (float)X;
+        l[d] = (float)(qd - X);
     }
     dvec4 v;
     v.x = w[0];
@@ -210,10 +213,11 @@ __device__ __forceinline__ void dl_pair(R r0, R r1, R r2, R rr2, R q0, R q1, R q
 // the sources that pass; when a lane's queue is full, every lane evaluates
 // its queued pairs and sums its own target -- so the pair arithmetic runs for
 // in-range pairs only, with the warp's lanes busy, and no atomics.
-//   R = float: r = ((t_hi - o w_hi) - s_hi) + ((t_lo - o w_lo) - s_lo) from
-//     the cell-local hi + lo parts (o the cell offset; relative error of r
-//     ~1e-7 down to coincident points), the cutoff and the pair in FP32, one
-//     FP32 partial sum per round added to the FP64 total;
+//   R = float: in cell units r = ((t_hi - o) - s_hi) + (t_lo - s_lo), o the
+//     neighbour cell offset: the hi terms are exact, so r is good to a few
+//     ulp of |r| down to near-coincident points; times the cell width, the
+//     cutoff and the pair in FP32, one FP32 partial sum per round added to
+//     the FP64 total;
 //   R = double: r from the wrapped FP64 positions and the image shift of the
 //     cell offset, the cutoff and the pair in FP64.
 template <typename R>
@@ -251,9 +255,9 @@ __global__ void __launch_bounds__(kDlWarps * 32) k_p2p_dl(DlNearArgs a)
             s = a.startn[nb * kSub3];
             se = a.startn[(nb + 1) * kSub3];
             code = (ox + 64) | ((oy + 64) << 8) | ((oz + 64) << 16);
-            b0 = fmaf(-(float)ox, a.w_hi, th.x);
-            b1 = fmaf(-(float)oy, a.w_hi, th.y);
-            b2 = fmaf(-(float)oz, a.w_hi, th.z);
+            b0 = th.x - (float)ox;  // exact: th on the 2^-20 lattice
+            b1 = th.y - (float)oy;
+            b2 = th.z - (float)oz;
         }
     };
     next_cell();
@@ -278,9 +282,9 @@ __global__ void __launch_bounds__(kDlWarps * 32) k_p2p_dl(DlNearArgs a)
                 const int ox = (cd & 255) - 64, oy = ((cd >> 8) & 255) - 64, oz = ((cd >> 16) & 255) - 64;
                 if constexpr (sizeof(R) == 4) {
                     const float4 Sh = a.lhi[sj], Sl = a.llo[sj];
-                    const float r0 = (fmaf(-(float)ox, a.w_hi, th.x) - Sh.x) + (fmaf(-(float)ox, a.w_lo, tl.x) - Sl.x);
-                    const float r1 = (fmaf(-(float)oy, a.w_hi, th.y) - Sh.y) + (fmaf(-(float)oy, a.w_lo, tl.y) - Sl.y);
-                    const float r2 = (fmaf(-(float)oz, a.w_hi, th.z) - Sh.z) + (fmaf(-(float)oz, a.w_lo, tl.z) - Sl.z);
+                    const float r0 = (((th.x - (float)ox) - Sh.x) + (tl.x - Sl.x)) * a.w;
+                    const float r1 = (((th.y - (float)oy) - Sh.y) + (tl.y - Sl.y)) * a.w;
+                    const float r2 = (((th.z - (float)oz) - Sh.z) + (tl.z - Sl.z)) * a.w;
                     const float rr2 = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
                     if (rr2 <= (float)a.rc2 && rr2 > 0.f) {
                         const float4 Q = a.q32[sj], Nn = a.n32[sj];
@@ -369,7 +373,7 @@ cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, con
     dvec4 *pos = (dvec4 *)p->dl_near, *qs = pos + N, *ns = qs + N;
     float4 *lhi = (float4 *)(ns + N), *llo = lhi + N, *q32 = llo + N, *n32 = q32 + N;
     k_dl_sort<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(x, q, n, p->permn, p->keyn, N, p->prm.L, 1.0 / p->prm.L,
-                                                          p->g.cell, p->g.nc, pos, qs, ns, lhi, llo, q32, n32);
+                                                          1.0 / p->g.cell, p->g.nc, pos, qs, ns, lhi, llo, q32, n32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -389,11 +393,10 @@ cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, con
     a.L = p->prm.L;
     a.xi = p->prm.xi;
     a.rc2 = p->prm.rc * p->prm.rc;
-    a.w_hi = (float)p->g.cell;
-    a.w_lo = (float)(p->g.cell - (double)a.w_hi);
-    // the filter works on the hi parts alone: each is within 2^-24 of its
-    // cell-local value (|lo| <= 2^-24 cell), so 1e-4 rc + 1e-5 cell covers it
-    const double rcm = p->prm.rc * (1.0 + 1e-4) + 1e-5 * p->g.cell;
+    a.w = (float)p->g.cell;
+    // the filter works on the hi parts alone, in cell units: each is within
+    // 2^-21 of its coordinate, so a margin of 1e-4 rc + 1e-5 cell covers it
+    const double rcm = (p->prm.rc / p->g.cell) * (1.0 + 1e-4) + 1e-5;
     a.rcm2 = (float)(rcm * rcm);
     a.nc = p->g.nc;
     a.K = p->g.K;

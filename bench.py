@@ -367,6 +367,21 @@ def cpu_baseline(n_targets: int, seed_shift: int = 0):
                       f"structure factors over all {N} sources", "seconds": dt}
 
 
+def job_time_and_rate(ms_local: float, units_per_rank: int, world: int):
+    """Max over ranks of the per-step time (an all-reduce over the gloo group
+    when world > 1) and the whole-job rate: the units all ranks processed per
+    second at that time."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 def main_reference(args, rank, world):
     if rank != 0:
         return
@@ -433,17 +448,10 @@ def main():
         res = run_gpu(args, rank, world)
         if res is None:
             return
-        ms_mean = float(np.mean(res["ms32"]))
-        if world > 1:
-            import torch
-            import torch.distributed as dist
-            t = torch.tensor([ms_mean], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_mean = float(t.item())
+        ms_mean, value = job_time_and_rate(float(np.mean(res["ms32"])), res["N"], world)
         if rank != 0:
             return
         N, L, tol, M, P = res["N"], res["L"], res["tol"], res["M"], res["P"]
-        value = world * N / (ms_mean * 1e-3)
         ms64 = float(np.mean(res["ms64"]))
         peaks, peak_src = load_peaks()
         st = res["stages"]

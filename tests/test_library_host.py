@@ -178,3 +178,11 @@ def test_apply_entry_points_reject_null_plan_on_the_host():
         with pytest.raises(ewald.EwaldError) as e:
             fn(None, *([None] * nargs))
         assert e.value.status == ewald.EWALD_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the CUDA library the binding raises
+    monkeypatch.setattr(ewald, "_lib", None)
+    monkeypatch.setattr(ewald, "LIB_PATH", str(tmp_path / "libewald_gb300.so"))
+    with pytest.raises(RuntimeError, match="CUDA library not built"):
+        ewald.load(build_if_missing=False)

@@ -58,9 +58,10 @@ typedef enum {
     EWALD_F64 = 0,
     /* P2P, P2G and G2P in FP32 with FP32 accumulation; FFT, CNV and the final
      * near + far sum in FP64 when tol < 1e-6, else FP32 FFT/CNV and FP64 sum.
-     * Below tol 1e-7, where single precision cannot reach: P2P in
-     * double-single FP32 arithmetic (down to tol 1e-9; FP64 below) and P2G/G2P
-     * in FP64.  Callers still pass and receive FP64 arrays. */
+     * At tol 1e-7 and below, where plain single precision does not reach
+     * with margin: P2P in double-single FP32 arithmetic (down to tol 1e-9;
+     * FP64 below) and P2G/G2P in double-single (8^3 tiles, 8 <= P <= 16) or
+     * FP64.  Callers still pass and receive FP64 arrays. */
     EWALD_F32_BULK = 1
 } ewald_dtype;
 
@@ -85,9 +86,9 @@ typedef struct {
     int32_t fft_f64;       /* 1: FFT/CNV in FP64, 0: FP32 */
     int64_t footprint_bytes; /* device memory owned by the plan */
     int32_t near_ds;       /* 1: P2P in double-single arithmetic (pairs of FP32 values,
-                              ~44 bits) with P2G/G2P in FP64 -- EWALD_F32_BULK at
-                              1e-9 <= tol < 1e-7; 0 otherwise.  Read-only (not an
-                              override). */
+                              ~44 bits) with P2G/G2P in double-single or FP64 --
+                              EWALD_F32_BULK at 1e-9 <= tol <= 1e-7; 0 otherwise.
+                              Read-only (not an override). */
     int32_t reserved_;     /* zero */
 } ewald_params;
 
@@ -215,6 +216,14 @@ ewald_status ewald_sync_status(ewald_plan_t plan, void *stream);
  * one ewald_apply() issues with this plan, and the number of cuFFT executions. */
 ewald_status ewald_launch_counts(ewald_plan_t plan, int32_t *kernels, int32_t *ffts);
 
+/* Failure injection for tests (no counterpart in the paper): the nth next
+ * device allocation of any plan (ewald_plan workspaces, the combined apply's
+ * double-layer workspaces, the host apply's staging) fails as if the device
+ * were out of memory, so the calling entry point returns EWALD_ENOMEM and
+ * leaves the plan as it was before the call.  nth = 0 disarms it.  Process-
+ * wide host state; nothing runs on the device.  Errors: EINVAL for nth < 0. */
+ewald_status ewald_debug_fail_alloc(int32_t nth);
+
 /* ---- Measured parameter choice and batches of boxes ----------------------
  * Sec. 2.4 leaves one free parameter once every term of eq. (ese) is held
  * below the tolerance, and picks it by minimising the modelled run time
@@ -294,11 +303,16 @@ void ewald_batch_destroy(ewald_batch_t b);
  * seed div 2^32), u1, u2 from outputs 0, 1 and n_z from outputs 2, 3 as
  * (x + 1) / 2^32, Box-Muller n_x, n_y = sqrt(-2 ln u1) (cos, sin)(2 pi u2),
  * n_z = sqrt(-2 ln u3) cos(2 pi u4).  Only the last apply's velocities are
- * returned.  A scheduler thread admits queued requests first come first
- * served while the summed device footprint of the running ones (planner
- * estimate plus request buffers) stays within the budget and one of
- * `max_active` slots is free; each runs on its own stream, so requests
- * overlap on the GPU, and finished ones free their room at once. */
+ * returned.  A scheduler thread admits queued requests while the summed
+ * device footprint of the running ones (planner estimate plus request
+ * buffers) stays within the budget and one of `max_active` slots is free:
+ * shortest expected work first (N x napplies x a precision weight: FP32 1,
+ * FP32 with FP64 FFTs 1.5, double-single 5, FP64 40), except that a request
+ * queued for more than 2 s goes first (oldest first) and is not overtaken
+ * while it does not fit.  Each runs on its own stream, with a CUDA stream
+ * priority that falls with its expected work (log-spaced over the device's
+ * priority range), so requests overlap on the GPU and the small ones'
+ * kernels are scheduled first; finished ones free their room at once. */
 typedef struct ewald_server_s *ewald_server_t;
 
 typedef struct {
@@ -367,8 +381,9 @@ ewald_status ewald_window_hat(int32_t P, double h, int64_t n, const double *k, d
  * array in device memory (about 7 MB) that every GPU loading this library
  * holds until the process exits.
  *   N      points (1 .. 32768; larger N returns EWALD_EUNSUPPORTED)
- *   prm    host struct read for L, xi, rc, near_f64 (1: FP64 kernels, 0: FP32),
- *          tol (FP32 below 1e-6 uses the compensated form) and n_c (<= 0:
+ *   prm    host struct read for L, xi, rc, near_ds (1: double-single pairs),
+ *          near_f64 (with near_ds 0 -- 1: FP64 kernels, 0: FP32), tol (FP32
+ *          below 1e-6 uses the compensated form) and n_c (<= 0:
  *          floor(L / rc)); n_c must be <= 16 and the cutoff may reach at most
  *          two cells (else EWALD_EUNSUPPORTED).  ewald_get_params() of a plan
  *          gives a consistent set.
@@ -378,7 +393,8 @@ ewald_status ewald_window_hat(int32_t P, double h, int64_t n, const double *k, d
  * make it before any stream capture.  All calls share the array and it keeps
  * the last call's contents; each call clears what must start at zero on
  * `stream`, and calls that overlap on the GPU (other streams or threads)
- * race.  NaN inputs give unspecified values; they are not reported. */
+ * race.  A NaN or Inf coordinate makes every entry of u NaN (the call itself
+ * returns before the device has looked at the data). */
 ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *prm, const double *x,
                                       const double *f, double *u, void *stream);
 

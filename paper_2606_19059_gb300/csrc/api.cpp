@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -96,9 +97,26 @@ cudaMemPool_t plan_pool(int dev)
     return pools[dev];
 }
 
+// Allocation-failure injection for tests (ewald_debug_fail_alloc): when
+// positive, the countdown-th next plan allocation fails as if the device were
+// out of memory.  Host state only; no device work is involved.
+std::atomic<int> g_fail_alloc_countdown{0};
+
+bool injected_alloc_failure()
+{
+    int c = g_fail_alloc_countdown.load();
+    while (c > 0) {
+        if (g_fail_alloc_countdown.compare_exchange_weak(c, c - 1))
+            return c == 1;
+    }
+    return false;
+}
+
 template <typename T>
 cudaError_t dalloc(ewald_plan_s *p, T **ptr, size_t bytes)
 {
+    if (injected_alloc_failure())
+        return cudaErrorMemoryAllocation;
     if (bytes == 0)
         bytes = 16;
     cudaError_t e;
@@ -554,6 +572,29 @@ ewald_status graph_call(ewald_plan_s *p, int kind, const void *a, const void *b,
 
 // Apply phases for batches of plans (csrc/batch.cpp).
 namespace ewg {
+ewald_status plan_set_stream_priority(ewald_plan_s *p, int priority)
+{
+    DeviceGuard dg(p->device);
+    if (!dg.ok)
+        return EWALD_ECUDA;
+    // the plan's side streams are idle between calls: wait for anything still
+    // queued (stream-ordered frees), then replace them
+    EW_CUDA(cudaStreamSynchronize(p->s2));
+    EW_CUDA(cudaStreamSynchronize(p->s3));
+    cudaStream_t a = nullptr, b = nullptr;
+    EW_CUDA(cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, priority));
+    if (cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, priority) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(a);
+        return EWALD_ECUDA;
+    }
+    cudaStreamDestroy(p->s2);
+    cudaStreamDestroy(p->s3);
+    p->s2 = a;
+    p->s3 = b;
+    return EWALD_OK;
+}
+
 ewald_status plan_bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t s)
 {
     return bin(p, x, f, s);
@@ -695,13 +736,31 @@ ewald_status ewald_apply_combined(ewald_plan_t plan, const double *x, const doub
         return EWALD_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     if (!plan->dl_tf) {
+        // all four workspaces or none: they are committed to the plan only
+        // once every allocation succeeded (dl_tf marks the set as present)
         const size_t r4 = plan->near64 ? sizeof(dvec4) : sizeof(float4);
         const size_t gs = plan->fft64 ? sizeof(double) : sizeof(float);
-        EW_CUDA(dalloc(plan, &plan->dl_tf, 2 * r4 * (size_t)plan->N));
-        EW_CUDA(dalloc(plan, &plan->dl_grid, 2 * 3 * gs * (size_t)plan->g.nreal));
-        EW_CUDA(dalloc(plan, &plan->dl_spec, 2 * 3 * 2 * gs * (size_t)plan->g.ncplx));
-        EW_CUDA(dalloc(plan, &plan->dl_near, (3 * sizeof(dvec4) + 4 * sizeof(float4)) * (size_t)plan->N));
-        EW_CUDA(cudaStreamSynchronize(plan->s2));  // pool allocations ready for `s`
+        void *b[4] = {nullptr, nullptr, nullptr, nullptr};
+        const size_t bytes[4] = {2 * r4 * (size_t)plan->N, 2 * 3 * gs * (size_t)plan->g.nreal,
+                                 2 * 3 * 2 * gs * (size_t)plan->g.ncplx,
+                                 (3 * sizeof(dvec4) + 4 * sizeof(float4)) * (size_t)plan->N};
+        const int64_t fp0 = plan->footprint;
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            e = dalloc(plan, &b[k], bytes[k]);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(plan->s2);  // pool allocations ready for `s`
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (void *q : b)
+                dfree(plan, q);
+            plan->footprint = fp0;
+            return e == cudaErrorMemoryAllocation ? EWALD_ENOMEM : EWALD_ECUDA;
+        }
+        plan->dl_grid = b[1];
+        plan->dl_spec = b[2];
+        plan->dl_near = b[3];
+        plan->dl_tf = b[0];
     }
     rec(plan, 0, s);
     EW_ST(bin(plan, x, f, s));
@@ -887,6 +946,14 @@ ewald_status ewald_sync_status(ewald_plan_t plan, void *stream)
         EW_CUDA(cudaMemset(plan->err, 0, sizeof(int)));
         return EWALD_EINVAL;
     }
+    return EWALD_OK;
+}
+
+ewald_status ewald_debug_fail_alloc(int32_t nth)
+{
+    if (nth < 0)
+        return EWALD_EINVAL;
+    g_fail_alloc_countdown.store(nth);
     return EWALD_OK;
 }
 

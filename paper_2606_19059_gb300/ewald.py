@@ -90,6 +90,7 @@ _SIGS = [
     ("ewald_set_timing", ctypes.c_int, [_P, ctypes.c_int]),
     ("ewald_stage_times", ctypes.c_int, [_P, ctypes.POINTER(ewald_stage_timing)]),
     ("ewald_sync_status", ctypes.c_int, [_P, _P]),
+    ("ewald_debug_fail_alloc", ctypes.c_int, [ctypes.c_int32]),
     ("ewald_launch_counts", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("ewald_window_eval", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
                                          ctypes.POINTER(ctypes.c_double)]),
@@ -239,6 +240,11 @@ def ewald_stage_times(plan) -> dict:
 def ewald_sync_status(plan, stream=0) -> int:
     """Synchronise and return the device error status (EWALD_OK or EWALD_EINVAL)."""
     return int(load().ewald_sync_status(plan, stream))
+
+
+def ewald_debug_fail_alloc(nth: int) -> None:
+    """Make the nth next device allocation of any plan fail (0 disarms)."""
+    _check(load().ewald_debug_fail_alloc(int(nth)), "ewald_debug_fail_alloc")
 
 
 def ewald_launch_counts(plan):

@@ -1,5 +1,5 @@
 // k_grid_ds.cu -- steps a2 (P2G, eq. (p2g)) and a6 (G2P, eq. (g2p)) in
-// double-single arithmetic, for the FP32-bulk plans below tol 1e-7 (whose near
+// double-single arithmetic, for the FP32-bulk plans at tol <= 1e-7 (whose near
 // field is double-single too): on this GPU the FP64 pipe runs at a small
 // fraction of the FP32 one, and FP64 grid kernels were most of such an apply.
 //

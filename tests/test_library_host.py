@@ -71,8 +71,11 @@ def test_params_auto_and_precision_switches():
     assert p.near_f64 == 1 and p.fft_f64 == 1 and 4 <= p.P <= 16 and p.M % 2 == 0
     q = ewald.ewald_choose_params(100_000, 1.0, 1e-6, ewald.EWALD_F32_BULK)
     assert q.near_f64 == 0 and q.fft_f64 == 0
-    r = ewald.ewald_choose_params(100_000, 1.0, 1e-7, ewald.EWALD_F32_BULK)
-    assert r.near_f64 == 0 and r.fft_f64 == 1
+    r = ewald.ewald_choose_params(100_000, 1.0, 2e-7, ewald.EWALD_F32_BULK)
+    assert r.near_f64 == 0 and r.near_ds == 0 and r.fft_f64 == 1
+    # plain FP32 stops above 1e-7: tol 1e-7 itself takes the double-single kernels
+    r7 = ewald.ewald_choose_params(100_000, 1.0, 1e-7, ewald.EWALD_F32_BULK)
+    assert r7.near_f64 == 1 and r7.near_ds == 1 and r7.fft_f64 == 1
     s = ewald.ewald_choose_params(100_000, 1.0, 1e-9, ewald.EWALD_F32_BULK)
     assert s.near_f64 == 1  # FP32 cannot reach 1e-9
     assert 0 < p.est_err <= 1e-8 and 0 < q.est_err <= 1e-6

@@ -101,7 +101,9 @@ def default_xi(n: int, nt: int, L: float) -> float:
 
 
 def _images(reach: float, L: float):
-    m = int(np.ceil(reach / L)) + 1
+    """Lattice shifts p with |p_c| <= reach + L/2 per component: every image
+    within `reach` of a minimum-image difference (|d_c| <= L/2)."""
+    m = int(np.floor(reach / L + 0.5 + 1e-9))
     g = np.arange(-m, m + 1)
     P = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
     return P * L
@@ -109,7 +111,9 @@ def _images(reach: float, L: float):
 
 def near_field(x, D, L: float, xi: float, rc: float, targets=None) -> np.ndarray:
     """Real-space (P2P) sum of T^N over all sources and images with
-    0 < |r| <= rc, at the targets (indices into x; all points if None)."""
+    0 < |r| <= rc, at the targets (indices into x; all points if None).
+    Differences are taken to the minimum image first, so only the shifts
+    within rc + L/2 per component can reach."""
     x = np.asarray(x, dtype=np.float64)
     D = np.asarray(D, dtype=np.float64)
     tidx = np.arange(x.shape[0]) if targets is None else np.asarray(targets)
@@ -117,6 +121,7 @@ def near_field(x, D, L: float, xi: float, rc: float, targets=None) -> np.ndarray
     u = np.zeros((len(tidx), 3))
     for a, i in enumerate(tidx):
         d = x[i] - x  # (n, 3)
+        d -= L * np.round(d / L)
         for p in shifts:
             r = d + p
             rr2 = np.sum(r * r, axis=1)
@@ -219,6 +224,7 @@ def coulomb_potential(xe, y, c, L: float, xi: float) -> np.ndarray:
     phi = np.zeros(xe.shape[0])
     for a, xa in enumerate(xe):
         d = xa - y
+        d -= L * np.round(d / L)  # minimum image; shifts reach rmax + L/2
         for p in shifts:
             rr = np.sqrt(np.sum((d + p) ** 2, axis=1))
             m = (rr > 0.0) & (rr < rmax)
@@ -242,6 +248,7 @@ def coulomb_site_potential(y, c, L: float, xi: float) -> np.ndarray:
     phi = np.zeros(y.shape[0])
     for i in range(y.shape[0]):
         d = y[i] - y
+        d -= L * np.round(d / L)  # minimum image; shifts reach rmax + L/2
         for p in shifts:
             rr = np.sqrt(np.sum((d + p) ** 2, axis=1))
             m = (rr > 0.0) & (rr < rmax)

@@ -91,6 +91,64 @@ def test_double_layer_fp32_bulk_within_tolerance():
     assert l2 < 1e-6 and mx < 1e-6
 
 
+def test_double_layer_fp32_pairs_fp64_fft_two_cells_per_side():
+    # FP32 bulk at 1e-7 < tol < 1e-6: FP32 densities spread onto FP64 grids,
+    # FP64 CNV and FP64 near-field pairs; n_c = 2, so the 27 neighbour offsets
+    # reach one cell through several images
+    N, tol = 1500, 3e-7
+    x, _, q, n = _case("uniform", N, 408)
+    p = ewald.Plan(N, 1.0, tol, F32)
+    prm = p.params
+    assert prm.near_f64 == 0 and prm.near_ds == 0 and prm.fft_f64 == 1 and prm.n_c == 2
+    u = _combined(p, x, np.zeros((N, 3)), q, n)
+    tid = np.arange(0, N, 17)
+    ref = dl.ewald(x, dl.densities(q, n), 1.0, targets=tid)
+    l2, mx = errs(u[tid], ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+
+
+def test_double_layer_fp32_cutoff_reaching_two_cells():
+    # FP32 pairs with cells narrower than rc (K = 2: 125 neighbour cells)
+    N, tol = 1500, 1e-6
+    x, _, q, n = _case("uniform", N, 409)
+    rc = ewald.ewald_choose_params(N, 1.0, tol, F32).rc
+    p = ewald.Plan(N, 1.0, tol, F32, n_c=int(1.5 / rc))
+    prm = p.params
+    assert prm.fft_f64 == 0 and 1.0 < prm.rc / prm.cell <= 2.0
+    u = _combined(p, x, np.zeros((N, 3)), q, n)
+    tid = np.arange(0, N, 17)
+    ref = dl.ewald(x, dl.densities(q, n), 1.0, targets=tid)
+    l2, mx = errs(u[tid], ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+
+
+def test_combined_at_the_benchmark_workload():
+    # The combined apply as the benchmark times it (uniform N = 1e5, M = 128,
+    # P = 12, FP32 bulk, tol 1e-6) at 256 seeded targets: the Stokeslet part
+    # from the C oracle, the double layer from stored oracle values
+    # (tests/golden/make_stresslet_uniform_1e5.py, oracle/stresslet.py)
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "stresslet_uniform_1e5_256.txt")
+    tab = np.loadtxt(path)
+    idx, ref_dl = tab[:, 0].astype(np.int64), tab[:, 1:]
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS["uniform_1e5_tol1e-6_M128_P12"]
+    x, f = workloads.make(kind, N, seed, L)
+    rng = np.random.default_rng(1009)
+    q = rng.standard_normal((N, 3))
+    n = rng.standard_normal((N, 3))
+    assert np.array_equal(idx, np.sort(np.random.default_rng(7).choice(N, 256, replace=False)))
+    p = ewald.Plan(N, L, tol, F32, M=M, P=P)
+    u = _combined(p, x, f, q, n)
+    ref = oracle.ewald(x, f, L, targets=idx) + ref_dl
+    l2, mx = errs(u[idx], ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+    # the double layer alone, relative to its own size
+    ud = _combined(p, x, np.zeros((N, 3)), q, n)
+    l2, mx = errs(ud[idx], ref_dl)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+
+
 def test_double_layer_clustered_and_nonunit_box():
     N, L = 1000, 2.0
     x, _, q, n = _case("clustered", N, 404, L=L)
@@ -131,3 +189,40 @@ def test_double_layer_nan_density_sets_status():
     p = ewald.Plan(N, 1.0, 1e-6, F64)
     p.apply_combined(dev(x), dev(f), dev(q), dev(n))
     assert p.sync_status() == ewald.EWALD_EINVAL
+
+
+def test_combined_allocation_failure_leaves_the_plan_usable():
+    # The combined apply allocates its four double-layer workspaces on first
+    # use.  A failure at any of them returns ENOMEM and commits none of them,
+    # so the next call allocates afresh instead of launching on a partial set.
+    N = 1000
+    x, f, q, n = _case("uniform", N, 431)
+    ref = _combined(ewald.Plan(N, 1.0, 1e-6, F32), x, f, q, n)
+    for nth in (1, 2, 4):
+        p = ewald.Plan(N, 1.0, 1e-6, F32)
+        ewald.ewald_debug_fail_alloc(nth)
+        try:
+            with pytest.raises(ewald.EwaldError) as e:
+                _combined(p, x, f, q, n)
+        finally:
+            ewald.ewald_debug_fail_alloc(0)
+        assert e.value.status == ewald.EWALD_ENOMEM
+        assert p.sync_status() == ewald.EWALD_OK
+        u = _combined(p, x, f, q, n)  # FP32 pairs: equal to rounding (cell order may differ)
+        assert np.abs(u - ref).max() <= 1e-6 * np.abs(ref).max()
+        p.close()
+
+
+def test_plan_allocation_failure_returns_enomem():
+    ewald.ewald_debug_fail_alloc(7)
+    try:
+        with pytest.raises(ewald.EwaldError) as e:
+            ewald.Plan(2000, 1.0, 1e-6, F32)
+    finally:
+        ewald.ewald_debug_fail_alloc(0)
+    assert e.value.status == ewald.EWALD_ENOMEM
+    x, f = workloads.make("uniform", 2000, seed=432)
+    p = ewald.Plan(2000, 1.0, 1e-6, F32)
+    u = host(p.apply(dev(x), dev(f)))
+    ref = oracle.ewald(x, f, 1.0, targets=np.arange(0, 2000, 20))
+    assert errs(u[::20], ref)[0] <= 1e-6

@@ -20,8 +20,10 @@
 // (different streams, or different host threads) race on the array.
 #include <math.h>
 
+#include <algorithm>
 #include <cmath>
 
+#include "erf_rational.h"
 #include "internal.h"
 
 namespace ewg {
@@ -62,6 +64,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 unsigned char *g_scratch_addr[64] = {};
 
+// A NaN or Inf input coordinate raised the binning's error flag: every entry
+// of u becomes NaN, so the caller sees it without a status read-back.
+__global__ void k_nan_if_flagged(const int *__restrict__ err, double *__restrict__ u, int64_t n)
+{
+    if (*err == 0)
+        return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
 }  // namespace
 }  // namespace ewg
 
@@ -85,6 +97,8 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
     const int K = (int)ceil(prm->rc / cell - 1e-12);
     if (K > 2)
         return EWALD_EUNSUPPORTED;
+    if (prm->near_ds && prm->xi * prm->rc > ERFCX_DS_X)
+        return EWALD_EUNSUPPORTED;  // beyond the double-single erfcx fit
 
     // one-time set-up on this device: the array's device address
     int dev = 0;
@@ -109,7 +123,10 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
     ewald_plan_s pl;
     pl.device = dev;
     pl.N = N;
-    pl.near64 = prm->near_f64 != 0;
+    // double-single pairs (near_ds) keep FP64 sorted arrays and results, as
+    // in a plan; near_ds selects them whatever near_f64 says
+    pl.near_ds = prm->near_ds != 0;
+    pl.near64 = prm->near_f64 != 0 || pl.near_ds;
     pl.fft64 = false;
     pl.prm = *prm;
     pl.prm.n_c = nc;
@@ -147,8 +164,11 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
     pl.npos = base + kOffNpos;
     pl.nlo = base + kOffNlo;
     pl.nfrc = base + kOffNfrc;
-    // FP32 records (32 bytes a point) take the position area; FP64 uses npos
-    pl.nrec = pl.near64 ? nullptr : base + kOffNpos;
+    // FP32 records (32 bytes a point) take the position area, FP64 uses
+    // npos; the double-single force low parts (16 bytes a point) take nlo's
+    const bool recs = !pl.near64 || pl.near_ds;
+    pl.nrec = recs ? base + kOffNpos : nullptr;
+    pl.nflo = pl.near_ds ? base + kOffNlo : nullptr;
     pl.tdat = base + kOffTdat;
     pl.tfrc = base + kOffTfrc;
     pl.un = base + kOffUn;
@@ -188,6 +208,10 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
         e = launch_p2p(&pl, s);
     if (e == cudaSuccess)
         e = launch_copy_out(pl.un, pl.near64, u, 3 * N, s);
+    if (e == cudaSuccess) {
+        k_nan_if_flagged<<<(unsigned)std::min<int64_t>((3 * N + 255) / 256, 1024), 256, 0, s>>>(pl.err, u, 3 * N);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return EWALD_ECUDA;

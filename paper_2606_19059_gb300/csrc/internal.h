@@ -237,6 +237,10 @@ ewald_status plan_bin(ewald_plan_s *p, const double *x, const double *f, cudaStr
 ewald_status plan_far(ewald_plan_s *p, cudaStream_t s);
 ewald_status plan_sum(ewald_plan_s *p, double *u, cudaStream_t s);
 cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s);
+// Recreate the plan's own streams (the near-field side stream and the graph
+// capture origin) with a CUDA stream priority, for a server slot whose stream
+// has that priority.  The plan must be idle.
+ewald_status plan_set_stream_priority(ewald_plan_s *p, int priority);
 cudaError_t launch_copy_out(const void *src, bool src_f64, double *dst, int64_t n, cudaStream_t s);
 // Served requests: f <- f + a n (Philox4x32-10 normals for (point, step,
 // seed)), then f <- f - mean(f); `sums` is 3 doubles of device scratch.

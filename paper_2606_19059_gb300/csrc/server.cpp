@@ -7,15 +7,22 @@
 // from the previous forces plus a seeded perturbation (k_serve.cu).  Only the
 // last apply's velocities go back to the caller.
 //
-// A scheduler thread admits queued requests first-come first-served while the
-// sum of the admitted requests' device footprints (the planner's estimate plus
-// the request buffers) stays within the budget and a slot is free.  Each
-// admitted request runs on its own stream, so the work of different requests
-// overlaps on the GPU; the thread polls the requests' completion events,
-// releases their plans and memory, and admits the next ones as room frees up.
+// A scheduler thread admits queued requests while the sum of the admitted
+// requests' device footprints (the planner's estimate plus the request
+// buffers) stays within the budget and a slot is free.  Order: shortest
+// expected work first (N x applies x the planner's precision weight), so a
+// small request does not wait behind a large one; a request queued longer
+// than the age limit goes first (oldest first), and while such a request
+// does not fit, nothing overtakes it.  Each admitted request runs on its own
+// stream, with a CUDA stream priority that falls with its expected work, so
+// the block scheduler serves the small requests' kernels first when several
+// are ready; the work of different requests overlaps on the GPU.  The thread
+// polls the requests' completion events, releases their plans and memory, and
+// admits the next ones as room frees up.
 // The paper has no counterpart: it applies one suspension at a time.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -45,6 +52,7 @@ struct Req {
     ReqState state = kQueued;
     ewald_status status = EWALD_OK;
     int64_t footprint = 0;
+    double work = 0.0;  // expected work: N x applies x precision weight
     double t_arrival = 0.0, t_done = 0.0;
     ewald_plan_t plan = nullptr;
     double *dbuf = nullptr;  // x, f, u (9 N doubles) and 3 doubles of sums
@@ -74,8 +82,10 @@ struct ewald_server_s {
     int64_t fp_active = 0, fp_peak = 0;
     int active = 0;
     bool paused = false, stop = false;
-    std::vector<cudaStream_t> slots;   // one stream per admission slot
+    std::vector<cudaStream_t> slots;   // per admission slot, one stream per priority level
     std::vector<bool> slot_busy;
+    int prio_least = 0, prio_greatest = 0;  // CUDA stream priority range (greatest = most urgent)
+    double age_limit_s = 2.0;
     std::thread sched;
     std::vector<double> lat_ms;
     double pa = 0.0, t_first = -1.0, t_last = -1.0;
@@ -101,11 +111,13 @@ void release(Req *q)
 }
 
 // Plan, buffers, copies and every apply of one request, enqueued on `s`.
-ewald_status start(Req *q, cudaStream_t s)
+ewald_status start(Req *q, cudaStream_t s, int priority)
 {
     const ewald_request &r = q->r;
     const int64_t N = r.N;
     EW_ST_RET(ewald_plan(N, r.L, r.tol, (ewald_dtype)r.dtype, &q->plan));
+    // the plan's near-field side stream at the request's priority too
+    EW_ST_RET(plan_set_stream_priority(q->plan, priority));
     if (cudaMalloc(&q->dbuf, sizeof(double) * (9 * (size_t)N + 3)) != cudaSuccess) {
         cudaGetLastError();
         q->dbuf = nullptr;
@@ -159,6 +171,55 @@ void finish(ewald_server_s *sv, Req *q, ReqState st, ewald_status status)
     sv->cv_done.notify_all();
 }
 
+// Relative cost of one point-apply in the plan's precision (FP32 = 1), from
+// the GB300 stage weights the planner uses.
+double precision_weight(const ewald_params &p)
+{
+    if (p.near_ds)
+        return 5.0;
+    if (p.near_f64)
+        return 40.0;
+    return p.fft_f64 ? 1.5 : 1.0;
+}
+
+// Stream priority of a request: log-spaced over expected work from 2e4 (a
+// thousand points, 20 FP32 applies) to 5e9, the smallest the most urgent.
+int priority_for(const ewald_server_s *sv, double work)
+{
+    const int levels = sv->prio_least - sv->prio_greatest + 1;
+    if (levels <= 1)
+        return sv->prio_least;
+    double t = (std::log10(std::max(work, 1.0)) - std::log10(2e4)) / (std::log10(5e9) - std::log10(2e4));
+    t = std::min(1.0, std::max(0.0, t));
+    return sv->prio_greatest + (int)std::lround(t * (levels - 1));
+}
+
+// The next queued request to admit (index into sv->queue), or -1: the oldest
+// one past the age limit if any (and -1 if it does not fit, so that nothing
+// overtakes it), else the smallest expected work among those that fit.
+// Caller holds sv->mu.
+int pick_next(ewald_server_s *sv, double now)
+{
+    int oldest = -1;
+    for (int k = 0; k < (int)sv->queue.size(); ++k) {
+        const Req *q = sv->reqs[sv->queue[k]];
+        if (now - q->t_arrival > sv->age_limit_s &&
+            (oldest < 0 || q->t_arrival < sv->reqs[sv->queue[oldest]]->t_arrival))
+            oldest = k;
+    }
+    if (oldest >= 0)
+        return sv->fp_active + sv->reqs[sv->queue[oldest]]->footprint <= sv->budget ? oldest : -1;
+    int best = -1;
+    for (int k = 0; k < (int)sv->queue.size(); ++k) {
+        const Req *q = sv->reqs[sv->queue[k]];
+        if (sv->fp_active + q->footprint > sv->budget)
+            continue;
+        if (best < 0 || q->work < sv->reqs[sv->queue[best]]->work)
+            best = k;
+    }
+    return best;
+}
+
 void scheduler(ewald_server_s *sv)
 {
     cudaSetDevice(sv->device);
@@ -179,12 +240,13 @@ void scheduler(ewald_server_s *sv)
             release(q);
             finish(sv, q, e == cudaSuccess ? kDone : kFailed, e == cudaSuccess ? EWALD_OK : EWALD_ECUDA);
         }
-        // admissions: first come, first served, while the head fits
+        // admissions: shortest expected work first, the age limit first of all
         while (!sv->paused && !sv->stop && !sv->queue.empty() && sv->active < sv->max_active) {
-            Req *q = sv->reqs[sv->queue.front()];
-            if (sv->fp_active + q->footprint > sv->budget)
+            const int k = pick_next(sv, now_s());
+            if (k < 0)
                 break;
-            sv->queue.pop_front();
+            Req *q = sv->reqs[sv->queue[k]];
+            sv->queue.erase(sv->queue.begin() + k);
             int slot = 0;
             while (sv->slot_busy[slot])
                 ++slot;
@@ -194,20 +256,22 @@ void scheduler(ewald_server_s *sv)
             sv->active += 1;
             sv->fp_active += q->footprint;
             sv->fp_peak = std::max(sv->fp_peak, sv->fp_active);
+            const int prio = priority_for(sv, q->work);
+            const int levels = sv->prio_least - sv->prio_greatest + 1;
+            cudaStream_t &ss = sv->slots[slot * levels + (prio - sv->prio_greatest)];
             lk.unlock();
             ewald_status st = EWALD_OK;
-            if (!sv->slots[slot] &&
-                cudaStreamCreateWithFlags(&sv->slots[slot], cudaStreamNonBlocking) != cudaSuccess) {
+            if (!ss && cudaStreamCreateWithPriority(&ss, cudaStreamNonBlocking, prio) != cudaSuccess) {
                 cudaGetLastError();
-                sv->slots[slot] = nullptr;
+                ss = nullptr;
                 st = EWALD_ECUDA;
             }
             if (st == EWALD_OK)
-                st = start(q, sv->slots[slot]);
+                st = start(q, ss, prio);
             lk.lock();
             if (st != EWALD_OK) {
-                if (sv->slots[slot])
-                    cudaStreamSynchronize(sv->slots[slot]);
+                if (ss)
+                    cudaStreamSynchronize(ss);
                 cudaGetLastError();
                 release(q);
                 finish(sv, q, kFailed, st);
@@ -241,7 +305,12 @@ ewald_status ewald_server_create(int64_t hbm_budget_bytes, int32_t max_active, i
     sv->budget = hbm_budget_bytes;
     sv->max_active = max_active;
     sv->paused = start_paused != 0;
-    sv->slots.assign(max_active, nullptr);  // streams made at a slot's first use
+    if (cudaDeviceGetStreamPriorityRange(&sv->prio_least, &sv->prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        sv->prio_least = sv->prio_greatest = 0;
+    }
+    // streams made at a slot's first use at a priority level
+    sv->slots.assign((size_t)max_active * (sv->prio_least - sv->prio_greatest + 1), nullptr);
     sv->slot_busy.assign(max_active, false);
     try {
         sv->sched = std::thread(scheduler, sv);
@@ -270,6 +339,7 @@ ewald_status ewald_server_submit(ewald_server_t sv, const ewald_request *r, int6
         return EWALD_ENOMEM;
     q->r = *r;
     q->footprint = fp;
+    q->work = (double)r->N * r->napplies * precision_weight(prm);
     q->t_arrival = now_s();
     {
         std::lock_guard<std::mutex> lk(sv->mu);

@@ -276,6 +276,101 @@ def run_gpu(args, rank, world):
     return res
 
 
+CLUSTERED = "clustered_2e6_tol1e-7_M256_P14"
+
+
+def run_clustered(args, rank, world):
+    """The clustered workload (N = 2e6: 200 Gaussian blobs plus 20 % uniform
+    background, tol 1e-7, M = 256, P = 14): FP32-bulk applies (double-single
+    near field and grid at this tolerance, FP64 FFT), per-stage times, and the
+    plain FP64 apply beside them.  Inputs and plan workspaces (~2.5 GB) exceed
+    L2; the flush buffer is rewritten between timed steps all the same."""
+    import torch
+
+    from paper_2606_19059_gb300 import ewald, workloads
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    dev = torch.device("cuda", local)
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS[CLUSTERED]
+    x, f = workloads.make(kind, N, seed + rank, L)
+    xd, fd = torch.tensor(x, device=dev), torch.tensor(f, device=dev)
+    ud = torch.empty_like(xd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def timed(plan, steps, warmup):
+        for _ in range(warmup):
+            ewald.ewald_apply(plan.handle, xd.data_ptr(), fd.data_ptr(), ud.data_ptr(), sp)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ewald.ewald_apply(plan.handle, xd.data_ptr(), fd.data_ptr(), ud.data_ptr(), sp)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    p32 = ewald.Plan(N, L, tol, ewald.EWALD_F32_BULK, M=M, P=P)
+    ms32 = timed(p32, max(3, min(args.steps, 5)), 2)
+    if p32.sync_status() != ewald.EWALD_OK:
+        raise RuntimeError("device error during the clustered applies")
+    ewald.ewald_set_timing(p32.handle, 2)
+    flush.zero_()
+    ewald.ewald_apply(p32.handle, xd.data_ptr(), fd.data_ptr(), ud.data_ptr(), sp)
+    stages = ewald.ewald_stage_times(p32.handle)
+    ewald.ewald_set_timing(p32.handle, 0)
+    prm = p32.params.as_dict()
+    p32.close()
+    p64 = ewald.Plan(N, L, tol, ewald.EWALD_F64, M=M, P=P)
+    ms64 = timed(p64, 2, 1)
+    p64.close()
+    ms, rate = job_time_and_rate(float(np.mean(ms32)), N, world)
+    m64, rate64 = job_time_and_rate(float(np.mean(ms64)), N, world)
+    return {"ms": ms, "value": rate, "ms64": m64, "value64": rate64, "stages": stages, "params": prm,
+            "N": N, "L": L, "tol": tol, "M": M, "P": P, "x": x if rank == 0 else None, "steps": len(ms32)}
+
+
+def clustered_entry(c, peaks):
+    """The bench line's clustered object: rates, stage times, the HBM-bound
+    stages' fractions and the near field's in-range pair rate."""
+    from scipy.spatial import cKDTree
+
+    N, L, M, prm, st = c["N"], c["L"], c["M"], c["params"], c["stages"]
+    # in-range pairs (0 < |r| <= rc, periodic), estimated from 2 % of the
+    # targets against all sources (the full count takes minutes on the host)
+    xw = np.mod(c["x"], L)
+    xw[xw >= L] = 0.0
+    tree = cKDTree(xw, boxsize=L)
+    sel = np.random.default_rng(5).choice(N, N // 50, replace=False)
+    inr = (tree.count_neighbors(cKDTree(xw[sel], boxsize=L), prm["rc"]) - len(sel)) * (N / len(sel))
+    b = 8 if prm["fft_f64"] else 4
+    ncplx = M * M * (M // 2 + 1)
+    fft_bytes = 3 * M ** 3 * b + 3 * ncplx * 2 * b
+    scale_bytes = 2 * 3 * ncplx * 2 * b
+    hbm = peaks["hbm_gbs"]
+    roof = {}
+    for k, by in (("fft", fft_bytes), ("ifft", fft_bytes), ("scale", scale_bytes)):
+        gbs = by / (st[k + "_ms"] * 1e-3) / 1e9
+        roof[k] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                   "bytes_per_launch": by}
+    near = ("double-single" if prm["near_ds"] else ("FP64" if prm["near_f64"] else "FP32"))
+    roof["p2p"] = {"inrange_pairs_est": inr, "pairs_per_s": inr / (st["p2p_ms"] * 1e-3),
+                   "arithmetic": near + " pairs"}
+    for k in ("p2g", "g2p"):
+        roof[k] = {"points_per_s": N / (st[k + "_ms"] * 1e-3), "P": c["P"]}
+    return {"workload": CLUSTERED, "N": N, "tol": c["tol"], "M": M, "P": c["P"],
+            "xi": prm["xi"], "rc": prm["rc"], "n_c": prm["n_c"], "near": near,
+            "fft": "FP64" if prm["fft_f64"] else "FP32", "value": c["value"], "unit": UNIT,
+            "ms_per_step": c["ms"], "steps": c["steps"],
+            "fp64_plain": {"value": c["value64"], "unit": UNIT, "ms_per_step": c["ms64"]},
+            "stages_ms": {k: round(v, 5) for k, v in st.items()}, "stage_roofline": roof,
+            "l2": "inputs and workspaces larger than L2; 256 MB buffer rewritten between timed steps"}
+
+
 def run_batch(args, rank):
     """Many boxes (N = 10^U(3, 5), tol in {1e-4, 1e-6, 1e-8}, uniform points),
     autotuned per box, applied as one captured graph per batch step."""
@@ -350,21 +445,43 @@ def run_serving(args, rank, rate_hz):
                         "apply's u on the host; HBM budget 200 GB, 8 slots"}
 
 
-def cpu_baseline(n_targets: int, seed_shift: int = 0):
-    """The oracle, as it stands, on a bounded sample of the same workload."""
+# One oracle sample, the same for the CPU-baseline leg and every step of the
+# reference arm: the direct Ewald sum at this many sampled targets (the
+# structure factors over all N sources cost the same whatever the count, so
+# a fixed count keeps the two rates comparable).
+ORACLE_TARGETS = 1024
+
+
+def oracle_sample(seed_shift: int, x=None, f=None):
+    """One timed oracle sample (direct Ewald, FP64, all host cores) of the
+    workload: ORACLE_TARGETS targets drawn with seed 99 + seed_shift."""
     import oracle
     from paper_2606_19059_gb300 import workloads
 
     kind, N, L, tol, M, P, seed = workloads.WORKLOADS[WORKLOAD]
-    x, f = workloads.make(kind, N, seed, L)
-    idx = np.random.default_rng(99 + seed_shift).choice(N, n_targets, replace=False)
+    if x is None:
+        x, f = workloads.make(kind, N, seed, L)
+    idx = np.random.default_rng(99 + seed_shift).choice(N, ORACLE_TARGETS, replace=False)
     oracle.build()
     t = time.perf_counter()
     oracle.ewald(x, f, L, targets=idx)
-    dt = time.perf_counter() - t
-    return {"value": n_targets / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"direct Ewald (FP64) at {n_targets} sampled targets of the N={N} workload, "
-                      f"structure factors over all {N} sources", "seconds": dt}
+    return time.perf_counter() - t, oracle.num_threads(), N
+
+
+def cpu_baseline(samples: int):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    `samples` oracle samples of ORACLE_TARGETS targets each."""
+    from paper_2606_19059_gb300 import workloads
+
+    kind, N, L, tol, M, P, seed = workloads.WORKLOADS[WORKLOAD]
+    x, f = workloads.make(kind, N, seed, L)
+    dt, cores = 0.0, 0
+    for k in range(samples):
+        t, cores, _ = oracle_sample(k, x, f)
+        dt += t
+    return {"value": samples * ORACLE_TARGETS / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"direct Ewald (FP64), {samples} samples of {ORACLE_TARGETS} sampled targets of the "
+                      f"N={N} workload, structure factors over all {N} sources", "seconds": dt}
 
 
 def job_time_and_rate(ms_local: float, units_per_rank: int, world: int):
@@ -388,25 +505,25 @@ def main_reference(args, rank, world):
     from paper_2606_19059_gb300 import workloads
 
     kind, N, L, tol, M, P, seed = workloads.WORKLOADS[WORKLOAD]
-    per = 128
+    per = ORACLE_TARGETS
+    x, f = workloads.make(kind, N, seed, L)
     for w in range(args.warmup):
-        cpu_baseline(per, seed_shift=1000 + w)
+        oracle_sample(1000 + w, x, f)
     times = []
     for k in range(args.steps):
-        r = cpu_baseline(per, seed_shift=k)
-        times.append(r["seconds"])
-        cores = r["cores"]
+        t, cores, _ = oracle_sample(k, x, f)
+        times.append(t)
     total = sum(times)
     value = per * args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "ranks_timed": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "tol": tol, "M": M, "P": P,
                    "step": f"oracle direct Ewald at {per} sampled targets"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{per} sampled targets per step of the N={N} workload"},
+                         "sample": f"{per} sampled targets per step of the N={N} workload (rank 0 alone)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -418,13 +535,16 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-targets", type=int, default=4096)
+    ap.add_argument("--cpu-samples", type=int, default=4,
+                    help="oracle samples of %d targets in the CPU-baseline leg" % ORACLE_TARGETS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the many-box batched run")
     ap.add_argument("--batch-boxes", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-double-layer", action="store_true",
                     help="skip the combined single + double layer measurement")
+    ap.add_argument("--no-clustered", action="store_true",
+                    help="skip the clustered N = 2e6, tol 1e-7 workload")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rates", default="2,8",
                     help="Poisson arrival rates (requests/s), comma-separated: the first is the reported "
@@ -449,10 +569,17 @@ def main():
         if res is None:
             return
         ms_mean, value = job_time_and_rate(float(np.mean(res["ms32"])), res["N"], world)
+        N, L, tol, M, P = res["N"], res["L"], res["tol"], res["M"], res["P"]
+        ms64, rate64 = job_time_and_rate(float(np.mean(res["ms64"])), N, world)
+        e2e_ms, e2e_rate = job_time_and_rate(1e3 * float(np.median(res["e2e_s"])), N, world)
+        dl_ms = dl_rate = None
+        if res["dl"] is not None:
+            dl_ms, dl_rate = job_time_and_rate(float(np.median(res["dl"]["ms"])), N, world)
+        clus = None
+        if not args.no_clustered:
+            clus = run_clustered(args, rank, world)
         if rank != 0:
             return
-        N, L, tol, M, P = res["N"], res["L"], res["tol"], res["M"], res["P"]
-        ms64 = float(np.mean(res["ms64"]))
         peaks, peak_src = load_peaks()
         st = res["stages"]
         prm = res["params"]
@@ -514,7 +641,6 @@ def main():
         roof["algorithmic"] = {"inrange_pairs": inr, "candidate_pairs": cand,
                                "flops_per_inrange": FP32_FLOPS_PER_INRANGE,
                                "flops_per_candidate": FLOPS_PER_CANDIDATE, "flops_per_launch": p2p_flops}
-        e2e_ms = 1e3 * float(np.median(res["e2e_s"]))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mean, "higher_is_better": True, "scaling": "weak",
@@ -523,30 +649,33 @@ def main():
                        "mode": "f32_bulk", "xi": prm["xi"], "rc": prm["rc"], "n_c": prm["n_c"],
                        "poly_deg": prm["poly_deg"], "l2": "256 MB buffer rewritten between timed steps",
                        "parallelism": f"replicas x{world}"},
-            "fp64_plain": {"value": world * N / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64},
+            "fp64_plain": {"value": rate64, "unit": UNIT, "ms_per_step": ms64},
             "p50_ms": float(np.percentile(res["ms32"], 50)), "p99_ms": float(np.percentile(res["ms32"], 99)),
             "wall_s_timed": res["wall32"],
             "stages_ms": {k: round(v, 5) for k, v in st.items()},
             "stage_roofline": stage_roof,
             "dominant_stage": order[0][1],
             "roofline": roof,
-            "e2e": {"value": N / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+            "e2e": {"value": e2e_rate, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 2 * N * 3 * 8, "d2h_bytes_per_step": N * 3 * 8},
             "gpu_launches": res["kernels_per_step"] * args.steps,
             "clocks": res["clocks"],
         }
         if res["dl"] is not None:
-            dms = float(np.median(res["dl"]["ms"]))
             sd = res["dl"]["stages"]
             line["double_layer"] = {
                 "what": "combined single + double layer apply (Sec. 2.3), same points, q and n ~ N(0, 1)",
-                "value": world * N / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
+                "value": dl_rate, "unit": UNIT, "ms_per_step": dl_ms,
                 "stages_ms": {k: round(v, 5) for k, v in sd.items()},
-                # the double layer's FP64 near field runs after the sum: the
-                # difference of the two plans' sum stages is its time
+                # the double layer's near field runs after the sum: the
+                # difference of the two applies' sum stages is its time
                 "near_dl_ms": round(sd["sum_ms"] - st["sum_ms"], 5),
-                "near_dl_kernel": "k_p2p_dl (FP64, one thread per target)",
+                "near_dl_kernel": ("k_p2p_dl<double> (FP64 pairs" if prm["fft_f64"] or prm["near_f64"]
+                                   else "k_p2p_dl<float> (FP32 pairs") +
+                                  ", one warp per 32 targets, queued in-range pairs)",
             }
+        if clus is not None:
+            line["clustered"] = clustered_entry(clus, peaks)
         if not args.no_batch:
             line["batched"] = run_batch(args, rank)
         if not args.no_serve:
@@ -556,7 +685,7 @@ def main():
             line["serving"]["sweep"] = [{k: r[k] for k in ("rate_hz", "p50_ms", "p99_ms", "value", "wall_s",
                                                          "completed")} for r in runs]
         if not args.no_cpu_baseline:
-            cb = cpu_baseline(args.cpu_targets)
+            cb = cpu_baseline(args.cpu_samples)
             cb.pop("seconds", None)
             line["cpu_baseline"] = cb
         print(json.dumps(line))

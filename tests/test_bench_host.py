@@ -36,7 +36,7 @@ def test_json_line_follows_the_contract(monkeypatch, capsys, fake_result):
     run, N = fake_result
     monkeypatch.setattr(bench, "run_gpu", run)
     monkeypatch.setattr("sys.argv", ["bench.py", "--no-batch", "--no-serve", "--no-cpu-baseline",
-                                     "--steps", "10", "--warmup", "1"])
+                                     "--no-clustered", "--steps", "10", "--warmup", "1"])
     monkeypatch.delenv("WORLD_SIZE", raising=False)
     bench.main()
     lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
@@ -57,3 +57,38 @@ def test_json_line_follows_the_contract(monkeypatch, capsys, fake_result):
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
     assert d["double_layer"]["near_dl_ms"] == pytest.approx(1.95 - 0.0061, abs=1e-4)
     assert np.isfinite(d["double_layer"]["value"])
+    # FP32 FFTs at tol 1e-6: the double layer's near field runs FP32 pairs
+    assert d["double_layer"]["near_dl_kernel"].startswith("k_p2p_dl<float>")
+    assert "clustered" not in d
+
+
+def test_clustered_entry(monkeypatch, capsys, fake_result):
+    run, N = fake_result
+    kind, Nc, L, tol, M, P, seed = workloads.WORKLOADS[bench.CLUSTERED]
+    ov = ewald.ewald_params()
+    ov.M, ov.P = M, P
+    prm = ewald.ewald_choose_params(Nc, L, tol, ewald.EWALD_F32_BULK, override=ov).as_dict()
+    x = workloads.uniform(np.random.default_rng(3), 20000)  # a stand-in sample for the pair estimate
+    st = {"bin_ms": 2.4, "p2p_ms": 420.0, "p2g_ms": 20.7, "fft_ms": 5.16, "scale_ms": 0.79,
+          "ifft_ms": 5.2, "g2p_ms": 15.7, "sum_ms": 0.03, "total_ms": 470.0}
+
+    def run_c(args, rank, world):
+        return {"ms": 436.0, "value": Nc / 0.436, "ms64": 3300.0, "value64": Nc / 3.3, "stages": st,
+                "params": prm, "N": 20000, "L": L, "tol": tol, "M": M, "P": P, "x": x, "steps": 3}
+
+    monkeypatch.setattr(bench, "run_gpu", run)
+    monkeypatch.setattr(bench, "run_clustered", run_c)
+    monkeypatch.setattr("sys.argv", ["bench.py", "--no-batch", "--no-serve", "--no-cpu-baseline",
+                                     "--steps", "10", "--warmup", "1"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.main()
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    d = json.loads(lines[0])
+    c = d["clustered"]
+    assert c["workload"] == bench.CLUSTERED and c["near"] == "double-single" and c["fft"] == "FP64"
+    assert c["value"] == pytest.approx(Nc / 0.436) and c["fp64_plain"]["ms_per_step"] == 3300.0
+    r = c["stage_roofline"]
+    ncplx = M * M * (M // 2 + 1)
+    assert r["fft"]["bytes_per_launch"] == 3 * M ** 3 * 8 + 3 * ncplx * 16
+    assert r["fft"]["frac"] == pytest.approx(r["fft"]["achieved"] / r["fft"]["peak"])
+    assert r["p2p"]["inrange_pairs_est"] > 0

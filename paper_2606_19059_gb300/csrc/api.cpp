@@ -199,6 +199,7 @@ ewald_status make_plan(ewald_plan_s *p)
     g.ncplx = (int64_t)g.M * g.M * g.Mh;
     p->near64 = q.near_f64 != 0;
     p->near_ds = q.near_ds != 0;
+    p->ds_r1 = p->near_ds ? ds_split_radius(q.tol, q.xi, q.rc) : 0.0;
     p->fft64 = q.fft_f64 != 0;
     // the double-single grid kernels go with the double-single near field
     p->grid_ds = p->near_ds && grid_ds_supported(g.P, g.T, g.M);

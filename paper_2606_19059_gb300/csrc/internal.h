@@ -138,6 +138,7 @@ struct ewald_plan_s {
     void *nrec = nullptr;                         // FP32: near-sorted 32-byte source records
     void *nflo = nullptr;                         // double-single: force low parts (float4)
     bool near_ds = false;                         // P2P in double-single arithmetic
+    double ds_r1 = 0.0;                           // double-single P2P: pairs beyond this radius in FP32
     bool grid_ds = false;                         // P2G / G2P in double-single arithmetic
     void *wts = nullptr;                          // double-single window weights (tile order)
     void *tdat = nullptr, *tfrc = nullptr;        // tile-sorted window data / forces
@@ -190,6 +191,9 @@ double kb_window_hat(double k, double h, int P);          // closed-form transfo
 ewald_status fit_window(int P, int deg, WindowPoly *out, double *max_err);
 ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
                            const ewald_params *ov, ewald_params *out);
+// radius (length units) inside which a double-single plan's near-field pairs
+// run in double-single, the rest in compensated FP32 (rc: all double-single)
+double ds_split_radius(double tol, double xi, double rc);
 
 // ---- kernel launchers (defined in the .cu files) -------------------------
 struct BinArgs {

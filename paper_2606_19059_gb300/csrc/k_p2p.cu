@@ -80,7 +80,18 @@ __device__ __forceinline__ float fast_ex2(float x)
 
 struct F32Const {
     float rc2, rc2_half, rcm, xi, nxi2log2e, nxi2log2e_lo, c2, selfc;
+    // pairs with r^2 <= r1sq are left out (the double-single pass of a split
+    // near field takes them); -1 when nothing is left out
+    float r1sq;
 };
+
+// Squared pair distance (cell units) exactly as every FP32 pair form and the
+// split near field's classification compute it, so that the FP32 and the
+// double-single pass see the same r^2 for the same pair.
+__device__ __forceinline__ float pair_r2(float dx, float dy, float dz)
+{
+    return fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(dz, dz)));
+}
 
 __constant__ float c_exp2f32[EXP2_F32_N];
 
@@ -124,8 +135,8 @@ template <bool KAHAN, typename Acc>
 __device__ __forceinline__ void pair_f32(float dx, float dy, float dz, const float3 &f,
                                          const F32Const &k, Acc &ax, Acc &ay, Acc &az)
 {
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 > k.rc2)
+    float r2 = pair_r2(dx, dy, dz);
+    if (r2 > k.rc2 || r2 <= k.r1sq)
         return;
     if (r2 == 0.0f) {  // self or coincident point: the pair's far part comes out
         if constexpr (KAHAN) {
@@ -666,15 +677,18 @@ __device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg,
 // done early go on into tile o + 1; then tile o + 2 takes tile o's slot.
 // KAHAN: compensated partial sums, flushed into FP64 totals every round.
 template <bool KAHAN>
-__device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &kc, float inv_cell,
-                                             int item, WsF32 &ws, int lane)
+__device__ __forceinline__ bool p2p_f32_run(const P2PArgs &a, const F32Const &kc, int item, WsF32 &ws, int lane,
+                                            int &t_out, bool &act_out,
+                                            typename std::conditional<KAHAN, double, float>::type (&u)[3])
 {
     using Tot = typename std::conditional<KAHAN, double, float>::type;
     int c, tb, te, tsplit;
     if (!find_item(a, item, c, tb, te, tsplit))
-        return;  // whole warp: no block-wide barrier follows
+        return false;  // whole warp: no block-wide barrier follows
     const int t = tb + lane;
     const bool active = t < te;
+    t_out = t;
+    act_out = active;
     float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
     if (active) {
         const float4 *rec = (const float4 *)a.nrec;
@@ -775,12 +789,29 @@ __device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &k
             q.w3 = odd ? 0u : c1;
         }
     }
+    u[0] = ux;
+    u[1] = uy;
+    u[2] = uz;
+    return true;
+}
+
+// One work item (a chunk of <= 32 targets) by one warp: the sums of
+// p2p_f32_run, in length units, into the FP32 near result.
+template <bool KAHAN>
+__device__ __forceinline__ void p2p_f32_item(const P2PArgs &a, const F32Const &kc, float inv_cell,
+                                             int item, WsF32 &ws, int lane)
+{
+    typename std::conditional<KAHAN, double, float>::type u[3];
+    int t;
+    bool active;
+    if (!p2p_f32_run<KAHAN>(a, kc, item, ws, lane, t, active, u))
+        return;
     if (active) {
         const int i = a.permn[t];
         float *un = (float *)a.un;
-        un[3 * i] = (float)(ux * inv_cell);
-        un[3 * i + 1] = (float)(uy * inv_cell);
-        un[3 * i + 2] = (float)(uz * inv_cell);
+        un[3 * i] = (float)(u[0] * inv_cell);
+        un[3 * i + 1] = (float)(u[1] * inv_cell);
+        un[3 * i + 2] = (float)(u[2] * inv_cell);
     }
 }
 
@@ -1047,7 +1078,11 @@ __device__ __forceinline__ void pair_ds2(const float2 (&dh)[3], const float2 (&d
 {
     const dsf2 d[3] = {two_sum2(dh[0], dl[0]), two_sum2(dh[1], dl[1]), two_sum2(dh[2], dl[2])};
     const dsf2 r2 = ds_add2(ds_add2(ds_mul2(d[0], d[0]), ds_mul2(d[1], d[1])), ds_mul2(d[2], d[2]));
-    const bool in0 = r2.h.x <= k.rc2 && r2.h.x > 0.0f, in1 = r2.h.y <= k.rc2 && r2.h.y > 0.0f;
+    // inside the cutoff by the FP32 forms' r^2 (the high parts of d are the FP32
+    // kernel's d): with a split near field this pass and the FP32 one divide
+    // the pairs at r1 exactly
+    const float q0 = pair_r2(d[0].h.x, d[1].h.x, d[2].h.x), q1 = pair_r2(d[0].h.y, d[1].h.y, d[2].h.y);
+    const bool in0 = q0 <= k.rc2 && r2.h.x > 0.0f, in1 = q1 <= k.rc2 && r2.h.y > 0.0f;
     const bool z0 = r2.h.x == 0.0f, z1 = r2.h.y == 0.0f;
     const dsf2 r2s = sel(in0, in1, r2, {f2(1.0f), f2(0.f)});
     // 1/r: FP32 estimate and one Newton step carried in double-single
@@ -1121,15 +1156,17 @@ __device__ __forceinline__ void stage_ds(const P2PArgs &a, WsDS &ws, int nseg, i
 // One work item by one warp: the FP32 kernel's rounds over the ring (the
 // busiest lane's count of in-range sources per round, lanes done early going
 // on into the next tile), one double-single pair per iteration.
-__device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc, int item, WsDS &ws,
-                                            int lane)
+__device__ __forceinline__ bool p2p_ds_run(const P2PArgs &a, const DSConst &kc, int item, WsDS &ws, int lane,
+                                           int &t_out, bool &act_out, dsf (&u)[3])
 {
     const float4 *rec = (const float4 *)a.nrec;
     int c, tb, te, tsplit;
     if (!find_item(a, item, c, tb, te, tsplit))
-        return;  // past the last real item: the same for the whole warp
+        return false;  // past the last real item: the same for the whole warp
     const int t = tb + lane;
     const bool active = t < te;
+    t_out = t;
+    act_out = active;
     float3 th = make_float3(0.f, 0.f, 0.f), tl = th, fdum;
     if (active) {
         unpack_rec(rec[2 * t], rec[2 * t + 1], th, tl, fdum);
@@ -1192,15 +1229,58 @@ __device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc,
             q.w3 = odd ? 0u : c1;
         }
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        u[c] = ds_add({acc[c].h.x, acc[c].l.x}, {acc[c].h.y, acc[c].l.y});
+    return true;
+}
+
+__device__ __forceinline__ void p2p_ds_item(const P2PArgs &a, const DSConst &kc, int item, WsDS &ws,
+                                            int lane)
+{
+    dsf u[3];
+    int t;
+    bool active;
+    if (!p2p_ds_run(a, kc, item, ws, lane, t, active, u))
+        return;
     if (active) {
         const int i = a.permn[t];
         double *un = (double *)a.un;
         const double inv_cell = 1.0 / a.cell;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const dsf u = ds_add({acc[c].h.x, acc[c].l.x}, {acc[c].h.y, acc[c].l.y});
-            un[3 * i + c] = ((double)u.h + (double)u.l) * inv_cell;
-        }
+        for (int c = 0; c < 3; ++c)
+            un[3 * i + c] = ((double)u[c].h + (double)u[c].l) * inv_cell;
+    }
+}
+
+// Split near field (FP32-bulk plans at tol <= 1e-7): the pairs beyond r1 in
+// the compensated FP32 form (their terms are small: e^{-xi^2 r^2} and
+// erfc(xi r) decay, so FP32's relative error on them stays below the
+// tolerance), those within r1 -- the self term included -- in double-single;
+// both passes over the same item in one warp, summed in FP64.
+union WsSplit {
+    WsF32 f;
+    WsDS d;
+};
+
+__device__ __forceinline__ void p2p_split_item(const P2PArgs &a, const F32Const &k32, const DSConst &kds,
+                                               int item, WsSplit &ws, int lane)
+{
+    double uo[3];
+    dsf ui[3];
+    int t;
+    bool active;
+    if (!p2p_f32_run<true>(a, k32, item, ws.f, lane, t, active, uo))
+        return;
+    __syncwarp();
+    p2p_ds_run(a, kds, item, ws.d, lane, t, active, ui);
+    if (active) {
+        const int i = a.permn[t];
+        double *un = (double *)a.un;
+        const double inv_cell = 1.0 / a.cell;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            un[3 * i + c] = (((double)ui[c].h + (double)ui[c].l) + uo[c]) * inv_cell;
     }
 }
 
@@ -1216,6 +1296,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_ds(P2PArgs a, DSConst kc, i
     }
 }
 
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_split(P2PArgs a, F32Const k32, DSConst kds, int items)
+{
+    __shared__ WsSplit wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int item = blockIdx.x * kWarps + warp; item < items; item += gridDim.x * kWarps) {
+        p2p_split_item(a, k32, kds, item, wsm[warp], lane);
+        __syncwarp();
+    }
+}
+
 // ---- many boxes in one launch ---------------------------------------------
 // One persistent launch per P2P variant over the work items of every box of a
 // batch: box b owns global items [base[b], base[b + 1]) (its item upper bound,
@@ -1227,6 +1317,7 @@ struct BoxP2P {
     F32Const k32;
     DSConst kds;
     float inv_cell;
+    int split;  // double-single plans: 1 for the split near field
 };
 
 __device__ __forceinline__ int box_of(const int *base, int nbox, int g)
@@ -1248,7 +1339,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_boxes(const BoxP2P *__restr
                                                            const int *__restrict__ base, int nbox)
 {
     using WS = typename std::conditional<
-        VAR <= 1, WsF32, typename std::conditional<VAR == 2, WsDS, WsF64>::type>::type;
+        VAR <= 1, WsF32, typename std::conditional<VAR == 2, WsSplit, WsF64>::type>::type;
     __shared__ WS wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = base[nbox];
@@ -1260,8 +1351,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_boxes(const BoxP2P *__restr
             p2p_f32_item<false>(bx.a, bx.k32, bx.inv_cell, item, wsm[warp], lane);
         else if constexpr (VAR == 1)
             p2p_f32_item<true>(bx.a, bx.k32, bx.inv_cell, item, wsm[warp], lane);
-        else if constexpr (VAR == 2)
-            p2p_ds_item(bx.a, bx.kds, item, wsm[warp], lane);
+        else if constexpr (VAR == 2) {
+            if (bx.split)
+                p2p_split_item(bx.a, bx.k32, bx.kds, item, wsm[warp], lane);
+            else
+                p2p_ds_item(bx.a, bx.kds, item, wsm[warp].d, lane);
+        }
         else
             p2p_f64_item(bx.a, item, wsm[warp], lane);
         __syncwarp();
@@ -1349,10 +1444,19 @@ int64_t p2p_items(const ewald_plan_s *p)
     return (int64_t)p->g.ncells + (p->N + kP2PChunk - 1) / kP2PChunk + 1;
 }
 
+// the split near field of double-single plans (ds_split_radius): double-single
+// pairs within r1 < rc, compensated FP32 beyond
+bool p2p_split(const ewald_plan_s *p)
+{
+    return p->near_ds && p->ds_r1 < p->prm.rc;
+}
+
 // cell units: lengths / cell, xi * cell
 F32Const f32_const(const ewald_plan_s *p)
 {
     F32Const kc;
+    const double r1c = p->ds_r1 / p->g.cell;
+    kc.r1sq = p2p_split(p) ? (float)(r1c * r1c) : -1.0f;
     const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
     kc.rc2 = (float)(rcc * rcc);
     kc.rc2_half = half_threshold(rcc);
@@ -1376,7 +1480,8 @@ DSConst ds_const(const ewald_plan_s *p)
         return r;
     };
     DSConst kc;
-    const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
+    // the double-single pass reaches r1 when the near field is split
+    const double rcc = (p2p_split(p) ? p->ds_r1 : p->prm.rc) / p->g.cell, xic = p->prm.xi * p->g.cell;
     kc.rc2 = (float)(rcc * rcc);
     kc.rc2_half = half_threshold(rcc);
     kc.rcm = (float)(rcc + 1e-3);
@@ -1422,8 +1527,13 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
     case 2: {
         int dev = 0;
         cudaGetDevice(&dev);
-        const unsigned cap = resident_blocks((const void *)k_p2p_ds, dev);
-        k_p2p_ds<<<std::min(grid, cap), kWarps * 32, 0, s>>>(a, ds_const(p), (int)items);
+        if (p2p_split(p)) {
+            const unsigned cap = resident_blocks((const void *)k_p2p_split, dev);
+            k_p2p_split<<<std::min(grid, cap), kWarps * 32, 0, s>>>(a, f32_const(p), ds_const(p), (int)items);
+        } else {
+            const unsigned cap = resident_blocks((const void *)k_p2p_ds, dev);
+            k_p2p_ds<<<std::min(grid, cap), kWarps * 32, 0, s>>>(a, ds_const(p), (int)items);
+        }
         break;
     }
     case 3:
@@ -1469,6 +1579,7 @@ cudaError_t p2p_boxes_create(ewald_plan_s *const *plans, int n, P2PBoxes **out)
         BoxP2P x;
         x.a = p2p_args(p);
         x.k32 = f32_const(p);
+        x.split = p2p_split(p) ? 1 : 0;
         if (v == 2)
             x.kds = ds_const(p);
         x.inv_cell = (float)(1.0 / p->g.cell);

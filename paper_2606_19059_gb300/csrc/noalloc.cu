@@ -127,6 +127,7 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
     // in a plan; near_ds selects them whatever near_f64 says
     pl.near_ds = prm->near_ds != 0;
     pl.near64 = prm->near_f64 != 0 || pl.near_ds;
+    pl.ds_r1 = pl.near_ds ? ds_split_radius(prm->tol, prm->xi, prm->rc) : 0.0;
     pl.fft64 = false;
     pl.prm = *prm;
     pl.prm.n_c = nc;

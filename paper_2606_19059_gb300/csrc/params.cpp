@@ -186,6 +186,47 @@ static bool fft_friendly(int m)
     return m == 1;
 }
 
+// Split radius of the double-single near field (FP32-bulk plans at tol <=
+// 1e-7).  A pair's term is G^N(r) f, |G^N f|^2 averaged over directions of f
+// = |f|^2 (2 (A - B)^2 + 4 A^2) / 3 with A = erfc(x)/r, B = (2 xi/sqrt(pi))
+// e^{-x^2}, x = xi r (eq. (g-near)); its size falls off with x.  Pairs beyond
+// r1 = x1/xi are evaluated in the compensated FP32 form (relative error per
+// term ~2e-7), those within r1 in double-single.  Their random FP32 errors
+// add to ~2e-7 sqrt(sum over the pairs beyond r1 of |term|^2); x1 is the
+// smallest x for which, with pairs spread uniformly in space (density ~ x^2:
+// the case with the most weight beyond x1; clustered points put more of it
+// close), that share of sum |term|^2 stays below (tol / (10 * 2e-7))^2 -- the
+// FP32 part's error then stays near tol/10 of the near field.  Returns rc
+// when nothing is left to split off.
+double ds_split_radius(double tol, double xi, double rc)
+{
+    const double xc = xi * rc;
+    if (!(xc > 0) || !(tol > 0))
+        return rc;
+    const double target = (tol / (10.0 * 2e-7)) * (tol / (10.0 * 2e-7));
+    if (target >= 1.0)
+        return 0.0;
+    auto w = [](double x) {
+        if (x <= 0.0)
+            return 6.0;  // the limit x^2 (2 (A - B)^2 + 4 A^2) as x -> 0 (units of xi |f|)
+        const double A = erfc(x) / x, B = 1.1283791670955126 * exp(-x * x);
+        return x * x * (2.0 * (A - B) * (A - B) + 4.0 * A * A);
+    };
+    // composite Simpson on n panels, accumulated from xc down
+    const int n = 4000;
+    const double hx = xc / n;
+    std::vector<double> tail(n + 1, 0.0);  // tail[i] = integral from x_i to xc
+    for (int i = n - 1; i >= 0; --i) {
+        const double a = i * hx, b = a + hx;
+        tail[i] = tail[i + 1] + hx / 6.0 * (w(a) + 4.0 * w(0.5 * (a + b)) + w(b));
+    }
+    const double total = tail[0];
+    for (int i = 0; i <= n; ++i)
+        if (tail[i] <= target * total)
+            return i >= n ? rc : (i * hx) / xi;
+    return rc;
+}
+
 ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
                            const ewald_params *ov, ewald_params *out)
 {

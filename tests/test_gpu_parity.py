@@ -373,15 +373,18 @@ def test_stage_times_reported():
 # ------------------------------------------------- double-single near field --
 
 def test_near_field_double_single_matches_oracle():
-    # FP32 bulk at tol <= 1e-7: P2P in pairs of FP32 values (~44 bits); the
-    # positions' low parts are FP32 (2^-37 cell), so close pairs bound it
+    # FP32 bulk at tol <= 1e-7: pairs within the split radius in pairs of
+    # FP32 values (~44 bits), the small terms beyond it in compensated FP32,
+    # chosen so that their error stays near tol/10 of the near field -- the
+    # near field's share of the eq. (ese) budget the planner allots
+    tol = 1e-8
     x, f = workloads.make("uniform", 3000, seed=103)
-    p = plan(3000, 1.0, 1e-8, F32, M=32, P=8)
+    p = plan(3000, 1.0, tol, F32, M=32, P=8)
     assert p.params.near_ds == 1 and p.params.near_f64 == 1
     u = host(p.near_field(dev(x), dev(f)))
     ref = oracle.near_field(x, f, 1.0, p.params.xi, p.params.rc)
     l2, mx = errs(u, ref)
-    assert l2 <= 1e-10 and mx <= 5e-10, (l2, mx)
+    assert l2 <= tol / 5 and mx <= tol, (l2, mx)
 
 
 @pytest.mark.parametrize("kind,N,tol", [("uniform", 20000, 1e-8), ("clustered", 12000, 1e-9)])

@@ -37,7 +37,9 @@ def run(server, reqs, napplies=5):
 
 
 def close(u, v, tol):
-    bound = 2e-6 if tol > 1e-7 else 1e-11   # FP32 bulk above 1e-7, double-single at and below
+    # FP32 bulk above 1e-7; at and below, double-single with the split near
+    # field's FP32 pairs (summation order moves them by ~tol/20)
+    bound = 2e-6 if tol > 1e-7 else tol / 20
     return np.abs(u - v).max() / np.abs(v).max() <= bound
 
 
@@ -99,17 +101,21 @@ def test_bounded_wait_times_out_then_completes():
 def test_admission_takes_the_smallest_expected_work_first():
     # one slot, queued while paused: the requests run one at a time in order
     # of expected work (N x applies x precision weight), not of arrival
+    import time
+
     s = ewald.Server(BUDGET, max_active=1, start_paused=True)
     sizes = [40000, 2000, 15000, 5000]
-    tickets = []
+    tickets, t_sub = [], {}
     for i, n in enumerate(sizes):
         x, f = workloads.served_box("uniform", n, 50 + i)
+        t0 = time.perf_counter()
         tickets.append(s.submit(x, f, 1e-6, napplies=3, perturb=0.1, seed=50 + i))
+        t_sub[tickets[-1]] = t0
     s.resume()
-    lat = {}
+    done = {}
     for t in tickets:
         assert s.wait(t, 600.0) == ewald.EWALD_OK
-        lat[t] = s.poll(t)[1]
+        done[t] = t_sub[t] + 1e-3 * s.poll(t)[1]  # completion: arrival + latency
     s.close()
-    order = sorted(tickets, key=lambda t: lat[t])
+    order = sorted(tickets, key=lambda t: done[t])
     assert [sizes[tickets.index(t)] for t in order] == sorted(sizes)

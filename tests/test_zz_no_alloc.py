@@ -36,13 +36,15 @@ def _noalloc(N, prm, xd, fd):
 # (dtype, tol, bound against the plan's near field, bound against the
 # oracle's; relative to the result's size, rel_max bounds 5x): FP64 to
 # rounding against the plan and to the kernels' rational erf(x)/x (6e-12
-# evaluated) against the oracle, FP32 to its pair arithmetic, double-single to
-# its ~44 bits
+# evaluated) against the oracle, FP32 to its pair arithmetic, double-single
+# (split near field: the small terms beyond the split radius in compensated
+# FP32) to tol/5 against the oracle and to the FP32 pairs' summation order
+# against the plan
 CASES = [
     (ewald.EWALD_F64, 1e-8, 1e-12, 1e-11, False),
     (ewald.EWALD_F32_BULK, 1e-6, 2e-6, 2e-6, False),
     (ewald.EWALD_F32_BULK, 2e-7, 2e-6, 2e-6, False),
-    (ewald.EWALD_F32_BULK, 1e-8, 1e-10, 1e-10, True),
+    (ewald.EWALD_F32_BULK, 1e-8, 5e-10, 2e-9, True),
 ]
 
 

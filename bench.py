@@ -670,9 +670,10 @@ def main():
                 # the double layer's near field runs after the sum: the
                 # difference of the two applies' sum stages is its time
                 "near_dl_ms": round(sd["sum_ms"] - st["sum_ms"], 5),
-                "near_dl_kernel": ("k_p2p_dl<double> (FP64 pairs" if prm["fft_f64"] or prm["near_f64"]
-                                   else "k_p2p_dl<float> (FP32 pairs") +
-                                  ", one warp per 32 targets, queued in-range pairs)",
+                "near_dl_kernel": ("k_p2p_dl<double> (FP64 pairs, one warp per 32 targets, queued in-range "
+                                   "pairs)" if prm["fft_f64"] or prm["near_f64"]
+                                   else "k_p2p_dl32 (FP32 pairs on the Stokeslet P2P machinery: sub-cell "
+                                        "culling, FP16x2 phase 1, bit queue, two pairs per iteration)"),
             }
         if clus is not None:
             line["clustered"] = clustered_entry(clus, peaks)

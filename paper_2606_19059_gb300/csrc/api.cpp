@@ -464,8 +464,14 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         EW_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     if (mode == FULL) {
         EW_CUDA(launch_sum(p, f, u, s));
-        if (dl)  // the double layer's near field, added to u
-            EW_CUDA(launch_p2p_dl(p, dl->x, dl->q, dl->n, u, s));
+        if (dl) {  // the double layer's near field, added to u
+            if (!p->fft64 && !p->near64) {  // FP32 pairs on the Stokeslet P2P machinery
+                EW_CUDA(launch_dl_records(p, dl->q, dl->n, p->dl_near, s));
+                EW_CUDA(launch_p2p_dl32(p, p->dl_near, u, s));
+            } else {
+                EW_CUDA(launch_p2p_dl(p, dl->x, dl->q, dl->n, u, s));
+            }
+        }
     } else if (mode == NEAR_ONLY) {
         EW_CUDA(launch_copy_out(p->un, p->near64, u, 3 * p->N, s));
     } else {

@@ -21,11 +21,14 @@
 // before the one inverse FFT and G2P.  T^F is odd: no self term.
 //
 // Kernels: k_dl_densities (tile-order S, the P2G input format), k_scale_dl
-// (CNV, HBM-bound: 6 complex components in, 3 read-modify-written), k_dl_sort
-// (near-sorted copies of positions, q and n) and k_p2p_dl (near field: an FP32
-// distance filter over the (2K+1)^3 neighbour cells of the plan's cell lists,
-// then the pair arithmetic for queued in-range pairs only -- FP32 where the
-// plan's FFTs are FP32, FP64 otherwise -- summed in FP64).
+// (CNV, HBM-bound: 6 complex components in, 3 read-modify-written), and the
+// near field in two forms.  FP32 plans: k_dl_records (48-byte near-order
+// records: the Stokeslet records' cell-local position parts and S in FP32)
+// for k_p2p_dl32 in k_p2p.cu, the Stokeslet P2P machinery with the
+// double-layer pair.  Plans with FP64 FFTs or kernels: k_dl_sort (near-sorted
+// copies of positions, q and n) and k_p2p_dl (an FP32 distance filter over the
+// (2K+1)^3 neighbour cells of the plan's cell lists, then FP64 pair arithmetic
+// for queued in-range pairs only, summed in FP64).
 #include "internal.h"
 
 namespace ewg {
@@ -212,14 +215,9 @@ __device__ __forceinline__ void dl_pair(R r0, R r1, R r2, R rr2, R q0, R q1, R q
 // cell-local coordinates (threshold rc grown past FP32 rounding) and queues
 // the sources that pass; when a lane's queue is full, every lane evaluates
 // its queued pairs and sums its own target -- so the pair arithmetic runs for
-// in-range pairs only, with the warp's lanes busy, and no atomics.
-//   R = float: in cell units r = ((t_hi - o) - s_hi) + (t_lo - s_lo), o the
-//     neighbour cell offset: the hi terms are exact, so r is good to a few
-//     ulp of |r| down to near-coincident points; times the cell width, the
-//     cutoff and the pair in FP32, one FP32 partial sum per round added to
-//     the FP64 total;
-//   R = double: r from the wrapped FP64 positions and the image shift of the
-//     cell offset, the cutoff and the pair in FP64.
+// in-range pairs only, with the warp's lanes busy, and no atomics.  r from the
+// wrapped FP64 positions and the image shift of the cell offset, the cutoff
+// and the pair in FP64 (R = double).
 template <typename R>
 __global__ void __launch_bounds__(kDlWarps * 32) k_p2p_dl(DlNearArgs a)
 {
@@ -280,25 +278,13 @@ __global__ void __launch_bounds__(kDlWarps * 32) k_p2p_dl(DlNearArgs a)
             if (k < len) {
                 const int sj = w.src[k][lane], cd = w.code[k][lane];
                 const int ox = (cd & 255) - 64, oy = ((cd >> 8) & 255) - 64, oz = ((cd >> 16) & 255) - 64;
-                if constexpr (sizeof(R) == 4) {
-                    const float4 Sh = a.lhi[sj], Sl = a.llo[sj];
-                    const float r0 = (((th.x - (float)ox) - Sh.x) + (tl.x - Sl.x)) * a.w;
-                    const float r1 = (((th.y - (float)oy) - Sh.y) + (tl.y - Sl.y)) * a.w;
-                    const float r2 = (((th.z - (float)oz) - Sh.z) + (tl.z - Sl.z)) * a.w;
-                    const float rr2 = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
-                    if (rr2 <= (float)a.rc2 && rr2 > 0.f) {
-                        const float4 Q = a.q32[sj], Nn = a.n32[sj];
-                        dl_pair<float>(r0, r1, r2, rr2, Q.x, Q.y, Q.z, Nn.x, Nn.y, Nn.z, xi, c_e, v0, v1, v2);
-                    }
-                } else {
-                    const int sx = floor_div(cx + ox, nc), sy = floor_div(cy + oy, nc), sz = floor_div(cz + oz, nc);
-                    const dvec4 P = a.pos[sj];
-                    const double r0 = (t0 - a.L * sx) - P.x, r1 = (t1 - a.L * sy) - P.y, r2 = (t2 - a.L * sz) - P.z;
-                    const double rr2 = fma(r0, r0, fma(r1, r1, r2 * r2));
-                    if (rr2 <= a.rc2 && rr2 > 0.0) {
-                        const dvec4 Q = a.qs[sj], Nn = a.ns[sj];
-                        dl_pair<double>(r0, r1, r2, rr2, Q.x, Q.y, Q.z, Nn.x, Nn.y, Nn.z, xi, c_e, v0, v1, v2);
-                    }
+                const int sx = floor_div(cx + ox, nc), sy = floor_div(cy + oy, nc), sz = floor_div(cz + oz, nc);
+                const dvec4 P = a.pos[sj];
+                const double r0 = (t0 - a.L * sx) - P.x, r1 = (t1 - a.L * sy) - P.y, r2 = (t2 - a.L * sz) - P.z;
+                const double rr2 = fma(r0, r0, fma(r1, r1, r2 * r2));
+                if (rr2 <= a.rc2 && rr2 > 0.0) {
+                    const dvec4 Q = a.qs[sj], Nn = a.ns[sj];
+                    dl_pair<double>(r0, r1, r2, rr2, Q.x, Q.y, Q.z, Nn.x, Nn.y, Nn.z, xi, c_e, v0, v1, v2);
                 }
             }
         }
@@ -330,7 +316,40 @@ __global__ void __launch_bounds__(kDlWarps * 32) k_p2p_dl(DlNearArgs a)
     }
 }
 
+// Double-layer source records for the FP32 near field (k_p2p_dl32), near
+// order: the cell-local position parts of the slot's Stokeslet record (lo and
+// the packed 2^-20 lattice hi) and the symmetric part S of q (x) n in FP32:
+//   (lo.x, lo.y, lo.z, S_xx), (S_yy, S_zz, hi bits 0..31, hi bits 32..63),
+//   (S_xy, S_xz, S_yz, 0).
+__global__ void __launch_bounds__(256) k_dl_records(const double *__restrict__ q, const double *__restrict__ n,
+                                                    const int32_t *__restrict__ permn,
+                                                    const float4 *__restrict__ nrec, int64_t N,
+                                                    float4 *__restrict__ drec, int *err)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N)
+        return;
+    const int64_t j = permn[s];
+    const double q0 = q[3 * j], q1 = q[3 * j + 1], q2 = q[3 * j + 2];
+    const double n0 = n[3 * j], n1 = n[3 * j + 1], n2 = n[3 * j + 2];
+    if (!(isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(n0) && isfinite(n1) && isfinite(n2)))
+        atomicOr(err, 1);
+    const float4 A = nrec[2 * s], B = nrec[2 * s + 1];
+    drec[3 * s] = make_float4(A.x, A.y, A.z, (float)(q0 * n0));
+    drec[3 * s + 1] = make_float4((float)(q1 * n1), (float)(q2 * n2), B.z, B.w);
+    drec[3 * s + 2] = make_float4((float)(0.5 * (q0 * n1 + q1 * n0)), (float)(0.5 * (q0 * n2 + q2 * n0)),
+                                  (float)(0.5 * (q1 * n2 + q2 * n1)), 0.f);
+}
+
 }  // namespace
+
+cudaError_t launch_dl_records(ewald_plan_s *p, const double *q, const double *n, void *drec, cudaStream_t s)
+{
+    const int64_t N = p->N;
+    k_dl_records<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(q, n, p->permn, (const float4 *)p->nrec, N,
+                                                             (float4 *)drec, p->err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dl_densities(ewald_plan_s *p, const double *q, const double *n, cudaStream_t s)
 {
@@ -401,11 +420,9 @@ cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, con
     a.nc = p->g.nc;
     a.K = p->g.K;
     const unsigned nb = (unsigned)((N + 32 * kDlWarps - 1) / (32 * kDlWarps));
-    // FP32 pair arithmetic where the plan's FFTs are FP32 (tol >= 1e-6), FP64 below
-    if (p->fft64 || p->near64)
-        k_p2p_dl<double><<<nb, 32 * kDlWarps, 0, s>>>(a);
-    else
-        k_p2p_dl<float><<<nb, 32 * kDlWarps, 0, s>>>(a);
+    // FP64 pairs (plans with FP64 FFTs or FP64 kernels; FP32 plans take
+    // k_p2p_dl32 in k_p2p.cu)
+    k_p2p_dl<double><<<nb, 32 * kDlWarps, 0, s>>>(a);
     return cudaGetLastError();
 }
 

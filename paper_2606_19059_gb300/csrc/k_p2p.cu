@@ -1306,6 +1306,212 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_split(P2PArgs a, F32Const k
     }
 }
 
+// ---- double-layer near field in FP32 (Sec. 2.3) ------------------------------
+// The Stokeslet kernel's machinery -- cell-group work items, sub-cell culling,
+// strided two-tile ring, FP16x2 phase 1, bit queue, two branch-free pairs per
+// iteration -- applied to the double-layer term (reading c20):
+//   T^N(r) : S = 2 beta (r.S.r) r + 2 gamma (tr S r + 2 S r),
+//   beta  = -e^{-x^2} [3 erfcx(x) / r^5 + (2 xi/sqrt(pi)) (3/r^4 + 2 xi^2/r^2)],
+//   gamma = (2 xi^3/sqrt(pi)) e^{-x^2},   x = xi r,
+// with S the symmetric part of q (x) n of the source (T^F is odd: no self
+// term, pairs at r = 0 are skipped).  Cell units throughout (T is homogeneous
+// of degree -2, so the sum is scaled by 1/cell^2 at the end).  Source records
+// (48 bytes, near order): (lo.x, lo.y, lo.z, S_xx), (S_yy, S_zz, hi bits
+// 0..31, hi bits 32..63), (S_xy, S_xz, S_yz, 0); hi and lo as in the
+// Stokeslet records.  Ring entries: sa = (hi + colleague offset, lo.x),
+// sb = (lo.y, lo.z, S_xx, S_yy), sc = (S_zz, S_xy, S_xz, S_yz).
+struct TileDL {
+    float4 sa[4 * kGrp];
+    float4 sb[4 * kGrp];
+    float4 sc[4 * kGrp];
+    uint4 sh[2][kT32 / 2];
+};
+using WsDL = WarpSmem<TileDL>;
+
+struct DLConst {
+    float rc2, rc2_half, rcm, xi, nxi2log2e, c2, c2xi2;  // cell units; c2 = 2 xi/sqrt(pi)
+};
+
+__device__ __forceinline__ void stage_dl(const P2PArgs &a, const float4 *__restrict__ drec, WsDL &ws, int nseg,
+                                         int slot, int tile, int ntile, int total, int lane, int (&sg)[2])
+{
+    float3 hp[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h, q = tile + k * ntile;
+        if (q < total) {
+            if (tile == 0)
+                sg[h] = seg_of(ws, nseg, q);
+            else if (ws.seg_pref[sg[h] + 1] <= q)
+                ++sg[h];
+            int dx, dy, dz;
+            const int j = seg_element(ws, sg[h], q, dx, dy, dz);
+            const float4 A = drec[3 * j], B = drec[3 * j + 1], C = drec[3 * j + 2];
+            const unsigned w0 = __float_as_uint(B.z), w1 = __float_as_uint(B.w);
+            const unsigned qx = w0 & 0x1FFFFFu, qy = (w0 >> 21) | ((w1 & 0x3FFu) << 11), qz = w1 >> 10;
+            hp[h] = make_float3((float)(int)qx * (1.f / 1048576.f) + (float)dx,
+                                (float)(int)qy * (1.f / 1048576.f) + (float)dy,
+                                (float)(int)qz * (1.f / 1048576.f) + (float)dz);
+            const int e = kGrp * (2 * slot + (lane >> 4)) + 1 + (lane & 15) + 16 * h;
+            ws.tile.sa[e] = make_float4(hp[h].x, hp[h].y, hp[h].z, A.x);
+            ws.tile.sb[e] = make_float4(A.y, A.z, A.w, B.x);
+            ws.tile.sc[e] = make_float4(B.y, C.x, C.y, C.z);
+        } else {
+            hp[h] = make_float3(kFarHalf, kFarHalf, kFarHalf);
+        }
+    }
+    const __half2 hx = __floats2half2_rn(hp[0].x, hp[1].x);
+    const __half2 hy = __floats2half2_rn(hp[0].y, hp[1].y);
+    const __half2 hz = __floats2half2_rn(hp[0].z, hp[1].z);
+    ws.tile.sh[slot][lane] = make_uint4(*(const unsigned *)&hx, *(const unsigned *)&hy,
+                                        *(const unsigned *)&hz, 0u);
+}
+
+// Two double-layer pairs without branches: in range (0 < r^2 <= rc^2) the
+// term, else r^2 is replaced by 1e30, for which e^{-x^2}, 1/r^4 and 1/r^5 --
+// and with them the term -- are exactly 0.
+__device__ __forceinline__ void pair2_dl(const float3 &d0, const float4 &sb0, const float4 &sc0, const float3 &d1,
+                                         const float4 &sb1, const float4 &sc1, const DLConst &k, float3 &c0,
+                                         float3 &c1)
+{
+    const float ra = pair_r2(d0.x, d0.y, d0.z), rb = pair_r2(d1.x, d1.y, d1.z);
+    const float2 r2s = make_float2(ra <= k.rc2 && ra > 0.f ? ra : 1e30f, rb <= k.rc2 && rb > 0.f ? rb : 1e30f);
+    const float2 rinv = make_float2(fast_rsqrt(r2s.x), fast_rsqrt(r2s.y));
+    const float2 x = __fmul2_rn(make_float2(k.xi, k.xi), __fmul2_rn(r2s, rinv));
+    const float2 ea = __fmul2_rn(r2s, make_float2(k.nxi2log2e, k.nxi2log2e));
+    const float2 E = make_float2(fast_ex2(ea.x), fast_ex2(ea.y));
+    const float2 den = __ffma2_rn(make_float2((float)ERFCX_C32, (float)ERFCX_C32), x, make_float2(1.f, 1.f));
+    const float2 tt = make_float2(fast_rcp(den.x), fast_rcp(den.y));
+    float2 p = make_float2(c_erfcx32[ERFCX_F32_N - 1], c_erfcx32[ERFCX_F32_N - 1]);
+#pragma unroll
+    for (int q = ERFCX_F32_N - 2; q >= 0; --q)
+        p = __ffma2_rn(p, tt, make_float2(c_erfcx32[q], c_erfcx32[q]));
+    const float2 i2 = __fmul2_rn(rinv, rinv);
+    const float2 i4 = __fmul2_rn(i2, i2);
+    const float2 i5 = __fmul2_rn(i4, rinv);
+    // beta = -E [3 i5 erfcx + c2 (3 i4 + 2 xi^2 i2)]
+    const float2 g = __ffma2_rn(make_float2(3.f, 3.f), i4, __fmul2_rn(make_float2(2.f * k.xi * k.xi, 2.f * k.xi * k.xi), i2));
+    const float2 in = __ffma2_rn(__fmul2_rn(make_float2(3.f, 3.f), i5), __fmul2_rn(tt, p), __fmul2_rn(make_float2(k.c2, k.c2), g));
+    const float2 b2 = __fmul2_rn(make_float2(-2.f, -2.f), __fmul2_rn(E, in));        // 2 beta
+    const float2 g2 = __fmul2_rn(make_float2(2.f * k.c2xi2, 2.f * k.c2xi2), E);       // 2 gamma
+    // S r, r.S.r, tr S per pair
+    const float3 d[2] = {d0, d1};
+    const float4 sb[2] = {sb0, sb1}, sc[2] = {sc0, sc1};
+    float3 out[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const float Sxx = sb[u].z, Syy = sb[u].w, Szz = sc[u].x, Sxy = sc[u].y, Sxz = sc[u].z, Syz = sc[u].w;
+        const float sx = fmaf(Sxx, d[u].x, fmaf(Sxy, d[u].y, Sxz * d[u].z));
+        const float sy = fmaf(Sxy, d[u].x, fmaf(Syy, d[u].y, Syz * d[u].z));
+        const float sz = fmaf(Sxz, d[u].x, fmaf(Syz, d[u].y, Szz * d[u].z));
+        const float rsr = fmaf(sx, d[u].x, fmaf(sy, d[u].y, sz * d[u].z));
+        const float tr = Sxx + Syy + Szz;
+        const float bb = (u == 0 ? b2.x : b2.y) * rsr, gg = u == 0 ? g2.x : g2.y;
+        const float cr = fmaf(gg, tr, bb);  // 2 beta rSr + 2 gamma trS
+        const float g4 = 2.f * gg;           // 2 gamma x 2 S r
+        out[u] = make_float3(fmaf(cr, d[u].x, g4 * sx), fmaf(cr, d[u].y, g4 * sy), fmaf(cr, d[u].z, g4 * sz));
+    }
+    c0 = out[0];
+    c1 = out[1];
+}
+
+// One work item of the double-layer near field by one warp; adds the sums
+// (times inv_cell2) into u, user order.
+__device__ __forceinline__ void p2p_dl32_item(const P2PArgs &a, const float4 *__restrict__ drec, const DLConst &kc,
+                                              double inv_cell2, double *__restrict__ u, int item, WsDL &ws,
+                                              int lane)
+{
+    int c, tb, te, tsplit;
+    if (!find_item(a, item, c, tb, te, tsplit))
+        return;
+    const int t = tb + lane;
+    const bool active = t < te;
+    float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+    if (active) {
+        const float4 *rec = (const float4 *)a.nrec;
+        float3 hi, lo, f;
+        unpack_rec(rec[2 * t], rec[2 * t + 1], hi, lo, f);
+        th = make_float4(hi.x + (t >= tsplit ? 1.f : 0.f), hi.y, hi.z, 0.f);
+        tl = make_float4(lo.x, lo.y, lo.z, 0.f);
+    }
+    const float3 blo = make_float3(warp_min(active ? th.x : 1e30f), warp_min(active ? th.y : 1e30f),
+                                   warp_min(active ? th.z : 1e30f));
+    const float3 bhi = make_float3(warp_max(active ? th.x : -1e30f), warp_max(active ? th.y : -1e30f),
+                                   warp_max(active ? th.z : -1e30f));
+    const int nseg = build_segments(a, c, ws, lane, blo, bhi, 0.5f, kc.rcm);
+    const int total = ws.seg_pref[nseg];
+    const int ntile = (total + kT32 - 1) / kT32;
+    const __half2 tx = __float2half2_rn(th.x), ty = __float2half2_rn(th.y), tz = __float2half2_rn(th.z),
+                  lim = __float2half2_rn(kc.rc2_half);
+    if (lane < 4) {  // the groups' dummy sources: far away, S = 0
+        ws.tile.sa[kGrp * lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+        ws.tile.sb[kGrp * lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ws.tile.sc[kGrp * lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int sg[2] = {0, 0};
+    for (int tt = 0; tt < 2 && tt < ntile; ++tt)
+        stage_dl(a, drec, ws, nseg, tt, tt, ntile, total, lane, sg);
+    __syncwarp();
+    BitQueue q = {0u, 0u, 0u, 0u, 0};
+    if (active) {
+        if (ntile > 0)
+            phase1_words(ws.tile.sh[0], tx, ty, tz, lim, q.w0, q.w1);
+        if (ntile > 1)
+            phase1_words(ws.tile.sh[1], tx, ty, tz, lim, q.w2, q.w3);
+    }
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int o = 0; o < ntile; ++o) {
+        const int need = (int)__reduce_max_sync(0xffffffffu, (unsigned)q.pending());
+        float px = 0.f, py = 0.f, pz = 0.f;
+        for (int it = 0; it < (need + 1) >> 1; ++it) {
+            const int e0 = q.pop(), e1 = q.pop();
+            const float4 s0 = ws.tile.sa[e0], b0 = ws.tile.sb[e0], g0 = ws.tile.sc[e0];
+            const float4 s1 = ws.tile.sa[e1], b1 = ws.tile.sb[e1], g1 = ws.tile.sc[e1];
+            float3 c0, c1;
+            pair2_dl(make_float3((th.x - s0.x) + (tl.x - s0.w), (th.y - s0.y) + (tl.y - b0.x),
+                                 (th.z - s0.z) + (tl.z - b0.y)),
+                     b0, g0,
+                     make_float3((th.x - s1.x) + (tl.x - s1.w), (th.y - s1.y) + (tl.y - b1.x),
+                                 (th.z - s1.z) + (tl.z - b1.y)),
+                     b1, g1, kc, c0, c1);
+            px += c0.x + c1.x;
+            py += c0.y + c1.y;
+            pz += c0.z + c1.z;
+        }
+        ux += px;  // per-round FP32 partial sums into FP64 totals
+        uy += py;
+        uz += pz;
+        q.shift_if((q.g >> 1) == (o & 1));
+        q.shift_if((q.g >> 1) == (o & 1));
+        if (o + 2 < ntile) {
+            __syncwarp();
+            stage_dl(a, drec, ws, nseg, o & 1, o + 2, ntile, total, lane, sg);
+            __syncwarp();
+            unsigned c0 = 0u, c1 = 0u;
+            if (active)
+                phase1_words(ws.tile.sh[o & 1], tx, ty, tz, lim, c0, c1);
+            const bool odd = q.g & 1;
+            q.w1 = odd ? c0 : q.w1;
+            q.w2 = odd ? c1 : c0;
+            q.w3 = odd ? 0u : c1;
+        }
+    }
+    if (active) {
+        const int i = a.permn[t];
+        u[3 * i] += ux * inv_cell2;
+        u[3 * i + 1] += uy * inv_cell2;
+        u[3 * i + 2] += uz * inv_cell2;
+    }
+}
+
+__global__ void __launch_bounds__(kWarps * 32) k_p2p_dl32(P2PArgs a, const float4 *__restrict__ drec, DLConst kc,
+                                                          double inv_cell2, double *__restrict__ u)
+{
+    __shared__ WsDL wsm[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    p2p_dl32_item(a, drec, kc, inv_cell2, u, blockIdx.x * kWarps + warp, wsm[warp], lane);
+}
+
 // ---- many boxes in one launch ---------------------------------------------
 // One persistent launch per P2P variant over the work items of every box of a
 // batch: box b owns global items [base[b], base[b + 1]) (its item upper bound,
@@ -1548,6 +1754,29 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
         // less room (measured apply 0.727 against 0.710 ms)
         k_p2p_f32<false><<<grid, kWarps * 32, 0, s>>>(a, f32_const(p), (float)(1.0 / p->g.cell));
     }
+    return cudaGetLastError();
+}
+
+// Double-layer near field of an FP32 plan (records from build_dl_records),
+// added into u (user order).
+cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, double *u, cudaStream_t s)
+{
+    cudaError_t e = load_p2p_constants();
+    if (e != cudaSuccess)
+        return e;
+    const P2PArgs a = p2p_args(p);
+    const double rcc = p->prm.rc / p->g.cell, xic = p->prm.xi * p->g.cell;
+    DLConst kc;
+    kc.rc2 = (float)(rcc * rcc);
+    kc.rc2_half = half_threshold(rcc);
+    kc.rcm = (float)(rcc + 1e-3);
+    kc.xi = (float)xic;
+    kc.nxi2log2e = (float)(-xic * xic * 1.4426950408889634);
+    kc.c2 = (float)(2.0 * xic / sqrt(3.14159265358979323846));
+    kc.c2xi2 = (float)(2.0 * xic * xic * xic / sqrt(3.14159265358979323846));
+    const int64_t items = p2p_items(p);
+    const unsigned grid = (unsigned)((items + kWarps - 1) / kWarps);
+    k_p2p_dl32<<<grid, kWarps * 32, 0, s>>>(a, (const float4 *)drec, kc, 1.0 / (p->g.cell * p->g.cell), u);
     return cudaGetLastError();
 }
 

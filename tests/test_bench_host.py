@@ -58,7 +58,7 @@ def test_json_line_follows_the_contract(monkeypatch, capsys, fake_result):
     assert d["double_layer"]["near_dl_ms"] == pytest.approx(1.95 - 0.0061, abs=1e-4)
     assert np.isfinite(d["double_layer"]["value"])
     # FP32 FFTs at tol 1e-6: the double layer's near field runs FP32 pairs
-    assert d["double_layer"]["near_dl_kernel"].startswith("k_p2p_dl<float>")
+    assert d["double_layer"]["near_dl_kernel"].startswith("k_p2p_dl32")
     assert "clustered" not in d
 
 

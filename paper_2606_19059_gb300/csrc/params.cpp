@@ -296,8 +296,10 @@ ewald_status choose_params(int64_t N, double L, double tol, ewald_dtype dtype,
             // 128, P = 12: P2P 0.34, P2G + G2P 0.35, FFTs + CNV 0.10 ms;
             // double-single and FP64: N = 1e4 .. 1e6 over a range of M): one
             // unit ~5.3e-11 ms.  The FP64 pipe is 1/64 of the FP32 one, so
-            // FP64 plans move work from the near field to the grid.
-            const double wn = p.near_ds ? 5.0 : (p.near_f64 ? 48.0 : 1.0);
+            // FP64 plans move work from the near field to the grid.  The
+            // split double-single near field measured 1.8-2.6x the FP32 work
+            // rate (N = 1e5 and 1e6, tol 1e-8, M = 72 .. 392).
+            const double wn = p.near_ds ? 2.5 : (p.near_f64 ? 48.0 : 1.0);
             const double wg = p.near_ds ? 3.65 : (p.near_f64 ? 13.6 : 1.0);
             const double wf = p.fft_f64 ? 26.0 : 1.55;
             const double halo = pow((8.0 + P - 1.0) / 8.0, 3);      // staged block / tile

@@ -178,6 +178,19 @@ def run_gpu(args, rank, world):
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms, wall
 
+    if args.only_split:  # profiling runs: FP32 bulk at tol 1e-8 on the same points (split near field)
+        pds = ewald.Plan(N, L, 1e-8, ewald.EWALD_F32_BULK)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(args.warmup + args.steps):
+            if k == args.warmup:
+                torch.cuda.synchronize()
+                a.record(stream)
+            ewald.ewald_apply(pds.handle, xd.data_ptr(), fd.data_ptr(), ud.data_ptr(), sp)
+        b.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"only_split": True, "M": pds.params.M, "ms_per_step": a.elapsed_time(b) / args.steps}))
+        pds.close()
+        return None
     plan32 = ewald.Plan(N, L, tol, ewald.EWALD_F32_BULK, M=M, P=P)
     if args.only_double_layer:  # profiling runs: the combined applies alone
         rng = np.random.default_rng(seed + 7 + rank)
@@ -549,6 +562,9 @@ def main():
     ap.add_argument("--serve-rates", default="2,8",
                     help="Poisson arrival rates (requests/s), comma-separated: the first is the reported "
                          "serving run, the list the sweep toward saturation")
+    ap.add_argument("--only-split", action="store_true",
+                    help="time FP32-bulk applies at tol 1e-8 on the same points (the split double-single "
+                         "near field) and print a short line (for ncu captures)")
     ap.add_argument("--only-f32", action="store_true",
                     help="time the FP32-bulk applies only and print a short line (for ncu captures)")
     ap.add_argument("--only-double-layer", action="store_true",

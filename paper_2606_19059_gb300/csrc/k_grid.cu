@@ -22,7 +22,10 @@
 // tile's points can touch in shared memory (asynchronous copies); one warp per
 // point sums its P^3 support, lanes over (y, x) pairs walking the z planes, a
 // shuffle reduction at the end.
+#include <cuda.h>  // CUtensorMap and its enums (types only: encoded through the runtime's driver entry point)
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 #include <math.h>
+#include <string.h>
 
 #include <utility>
 
@@ -528,11 +531,34 @@ struct G2PPlanar {
     static constexpr int PS = (PC + 3) & ~3;
     static constexpr int NW = kG2PPlanarThreads / 32;
     static constexpr size_t grid_bytes = sizeof(float) * 3 * RR * RR * S;
-    static size_t smem(int deg)
+    __host__ __device__ static size_t smem_no_bar(int deg)
     {
         return grid_bytes + sizeof(int) * NR * 32 + sizeof(float) * (NW * 3 * PS + (deg + 1) * PS);
     }
+    // plus the TMA load's mbarrier (8-byte aligned)
+    __host__ __device__ static size_t bar_offset(int deg) { return (smem_no_bar(deg) + 7) & ~(size_t)7; }
+    // plus 128 bytes for aligning the staged box
+    __host__ __device__ static size_t smem(int deg) { return bar_offset(deg) + 8 + 128; }
 };
+
+// Bounded wait on phase 0 of an mbarrier: true once the phase completed,
+// false after `limit` polls (a copy that never lands: the caller skips its
+// work and raises the error flag instead of hanging the GPU).
+__device__ __forceinline__ bool mbar_wait0(unsigned bar, int limit)
+{
+    for (int it = 0; it < limit; ++it) {
+        unsigned ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(bar)
+                     : "memory");
+        if (ok)
+            return true;
+    }
+    return false;
+}
 
 // Shared-memory loads by 32-bit shared address, the offset an immediate.
 template <int OFF>
@@ -566,7 +592,8 @@ __device__ __forceinline__ void column_sum(unsigned a, const float *wz, float (&
 }
 
 template <int PC>
-__global__ void __launch_bounds__(kG2PPlanarThreads, 2) k_g2p_planar(GridArgs a)
+__global__ void __launch_bounds__(kG2PPlanarThreads, 2)
+    k_g2p_planar(GridArgs a, const __grid_constant__ CUtensorMap tmap, int use_tma, int *err)
 {
     using G = G2PPlanar<PC>;
     constexpr int T = G::T, RR = G::RR, S = G::S, NR = G::NR, NCH = G::NCH, PS = G::PS;
@@ -576,19 +603,46 @@ __global__ void __launch_bounds__(kG2PPlanarThreads, 2) k_g2p_planar(GridArgs a)
     const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
     if (s0 == s1)
         return;
-    extern __shared__ __align__(32) unsigned char smem[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    // the staged box starts on a 128-byte boundary (the tensor copy's
+    // destination alignment): the launch adds 128 bytes for the shift
+    unsigned char *smem =
+        smem_raw + ((128u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u);
     float *vs = (float *)smem;                                  // [3][RR][RR][S]
     int *tab = (int *)(smem + G::grid_bytes);                   // [NR][32]
     float *wsm = (float *)(tab + NR * 32);                      // per warp [3][PS]
     float *coef = wsm + G::NW * 3 * PS;                         // [deg+1][PS]
     const unsigned vs_a = (unsigned)__cvta_generic_to_shared(vs);
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(smem + G::bar_offset(a.deg));
     const int nt = a.nt, M = a.M, nd = a.deg + 1;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // stage: one warp per (component, z) plane, lanes over (row, 16-byte
-    // chunk); M a multiple of 8 keeps every chunk on one side of the periodic
-    // wrap and M >= P keeps one wrap enough
-    {
+    // Interior tiles (the block does not wrap around the periodic grid): one
+    // TMA tensor copy brings the whole (c, z, y, x) box of 3 x RR x RR x S
+    // floats -- the staged layout itself -- with completion on an mbarrier.
+    // The others stage with 16-byte asynchronous copies that follow the wrap.
+    const bool tma = use_tma && tx * T + S <= M && ty * T + RR <= M && tz * T + RR <= M;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                         "r"((unsigned)G::grid_bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(vs_a),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(tx * T), "r"(ty * T), "r"(tz * T), "r"(0),
+                "r"(bar_a)
+                : "memory");
+        }
+    } else {
+        // stage: one warp per (component, z) plane, lanes over (row, 16-byte
+        // chunk); M a multiple of 8 keeps every chunk on one side of the periodic
+        // wrap and M >= P keeps one wrap enough
         int rowoff[NIT], dstoff[NIT];
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
@@ -631,8 +685,16 @@ __global__ void __launch_bounds__(kG2PPlanarThreads, 2) k_g2p_planar(GridArgs a)
         const int j = i / PS, l = i - j * PS;
         coef[i] = l < PC ? ((const float *)a.wcoef)[l * nd + j] : 0.f;
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+    bool staged = true;
+    if (tma)
+        staged = mbar_wait0(bar_a, 1 << 20);
+    else
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (!__syncthreads_and(staged)) {  // the copy did not land: report, leave this tile's outputs
+        if (threadIdx.x == 0)
+            atomicOr(err, 2);
+        return;
+    }
     float *w = wsm + warp * 3 * PS;
     const unsigned w_a = (unsigned)__cvta_generic_to_shared(w);
     // this lane's pairs, block-invariant: column byte offset and weight addresses
@@ -876,28 +938,69 @@ cudaError_t run_g2p(const GridArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int PC>
-cudaError_t run_g2p_planar(const GridArgs &a, cudaStream_t s)
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to
+// the driver library); null when the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
-    const size_t sm = G2PPlanar<PC>::smem(a.deg);
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// TMA descriptor of the planar FP32 grid [3][M][M][M] for G2P's staged box of
+// (x, y, z, c) = (S, RR, RR, 3) floats: the global strides (M, M^2, M^3 floats)
+// and the box's inner extent (S floats) are multiples of 16 bytes, as the
+// tensor copy requires.  False if the descriptor cannot be made.
+bool g2p_tensor_map(const void *grid, int M, int S, int RR, CUtensorMap *m)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || M % 4 != 0 || S % 4 != 0 || ((uintptr_t)grid & 15) != 0)
+        return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)M, (cuuint64_t)M, (cuuint64_t)M, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)M * 4, (cuuint64_t)M * M * 4, (cuuint64_t)M * M * M * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)S, (cuuint32_t)RR, (cuuint32_t)RR, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(grid), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int PC>
+cudaError_t run_g2p_planar(const GridArgs &a, int *err, cudaStream_t s)
+{
+    using G = G2PPlanar<PC>;
+    const size_t sm = G::smem(a.deg);
     cudaError_t e =
         cudaFuncSetAttribute(k_g2p_planar<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess)
         return e;
-    k_g2p_planar<PC><<<a.nt * a.nt * a.nt, kG2PPlanarThreads, sm, s>>>(a);
+    CUtensorMap m;
+    memset(&m, 0, sizeof(m));
+    const int use_tma = g2p_tensor_map(a.grid, a.M, G::S, G::RR, &m) ? 1 : 0;
+    k_g2p_planar<PC><<<a.nt * a.nt * a.nt, kG2PPlanarThreads, sm, s>>>(a, m, use_tma, err);
     return cudaGetLastError();
 }
 
 // FP32, T = 8: a compile-time-P kernel for every supported P
 template <int PC>
-cudaError_t run_g2p_f32_fixed(const GridArgs &a, cudaStream_t s)
+cudaError_t run_g2p_f32_fixed(const GridArgs &a, int *err, cudaStream_t s)
 {
     if constexpr (PC > kMaxP) {
         return run_g2p<8, float, 0>(a, s);
     } else {
         if (a.P == PC)
-            return run_g2p_planar<PC>(a, s);
-        return run_g2p_f32_fixed<PC + 1>(a, s);
+            return run_g2p_planar<PC>(a, err, s);
+        return run_g2p_f32_fixed<PC + 1>(a, err, s);
     }
 }
 
@@ -951,7 +1054,7 @@ cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStre
     a.scale = scale;
     if (p->near64)
         return p->g.T == 8 ? run_g2p_direct64<8, 2>(a, s) : run_g2p_direct64<4, 2>(a, s);
-    return p->g.T == 8 ? run_g2p_f32_fixed<2>(a, s) : run_g2p<4, float, 0>(a, s);
+    return p->g.T == 8 ? run_g2p_f32_fixed<2>(a, p->err, s) : run_g2p<4, float, 0>(a, s);
 }
 
 }  // namespace ewg

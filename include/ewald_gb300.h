@@ -159,10 +159,11 @@ ewald_status ewald_apply_forces(ewald_plan_t plan, const double *f, double *u, v
  * (from cell-local hi + lo coordinates) where the plan's FFTs are FP32
  * (tol >= 1e-6), else in FP64, summed in FP64; far field in the plan's grid
  * precision.
+ * Double-single plans (FP32 bulk at tol <= 1e-7) spread the densities with
+ * their double-single P2G onto FP64 grids and evaluate the near pairs in FP64.
  * The first call allocates the double layer's workspaces (two 3-component
- * grids and spectra, tile-order densities).  Errors: EINVAL (NULL pointer),
- * EUNSUPPORTED (plans with double-single grid kernels: FP32 bulk below
- * tol 1e-7), ENOMEM, ECUDA; non-finite q or n raise the device error flag
+ * grids and spectra, tile-order densities), all or none.  Errors: EINVAL
+ * (NULL pointer), ENOMEM, ECUDA; non-finite q or n raise the device error flag
  * read by ewald_sync_status. */
 ewald_status ewald_apply_combined(ewald_plan_t plan, const double *x, const double *f, const double *q,
                                   const double *n, double *u, void *stream);

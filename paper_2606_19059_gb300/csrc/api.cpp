@@ -430,9 +430,12 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         const size_t r4 = p->near64 ? sizeof(dvec4) : sizeof(float4);
         const size_t gs = p->fft64 ? sizeof(double) : sizeof(float);
         e = launch_dl_densities(p, dl->q, dl->n, s);
-        for (int t = 0; t < 2 && e == cudaSuccess; ++t)
-            e = launch_p2g_with(p, (const char *)p->dl_tf + t * r4 * p->N,
-                                (char *)p->dl_grid + t * 3 * gs * p->g.nreal, s);
+        for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+            // each triple: N quadruples (2 N float4 pairs for double-single grids: same bytes as dvec4)
+            const char *src = (const char *)p->dl_tf + t * r4 * p->N;
+            char *dst = (char *)p->dl_grid + t * 3 * gs * p->g.nreal;
+            e = p->grid_ds ? launch_p2g_ds_with(p, src, (double *)dst, s) : launch_p2g_with(p, src, dst, s);
+        }
         return e;
     };
     if (far_first) {
@@ -736,8 +739,6 @@ ewald_status ewald_apply_combined(ewald_plan_t plan, const double *x, const doub
 {
     if (!plan || bad_ptr(x) || bad_ptr(f) || bad_ptr(q) || bad_ptr(n) || bad_ptr(u))
         return EWALD_EINVAL;
-    if (plan->grid_ds)
-        return EWALD_EUNSUPPORTED;
     DeviceGuard dg(plan->device);
     if (!dg.ok)
         return EWALD_ECUDA;

@@ -60,6 +60,36 @@ __global__ void __launch_bounds__(256) k_dl_densities(const double *__restrict__
     so[t] = b;
 }
 
+// The same densities for double-single grid kernels: per point and triple the
+// FP32 high parts and their rounding errors, (h.xyz, 0), (l.xyz, 0).
+__global__ void __launch_bounds__(256) k_dl_densities_ds(const double *__restrict__ q, const double *__restrict__ n,
+                                                         const int32_t *__restrict__ permt, int64_t N,
+                                                         float4 *__restrict__ sd, float4 *__restrict__ so, int *err)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N)
+        return;
+    const int64_t i = permt[t];
+    const double q0 = q[3 * i], q1 = q[3 * i + 1], q2 = q[3 * i + 2];
+    const double n0 = n[3 * i], n1 = n[3 * i + 1], n2 = n[3 * i + 2];
+    if (!(isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(n0) && isfinite(n1) && isfinite(n2)))
+        atomicOr(err, 1);
+    const double a[3] = {q0 * n0, q1 * n1, q2 * n2};
+    const double b[3] = {0.5 * (q0 * n1 + q1 * n0), 0.5 * (q0 * n2 + q2 * n0), 0.5 * (q1 * n2 + q2 * n1)};
+    float ah[3], bh[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ah[k] = (float)a[k];
+        bh[k] = (float)b[k];
+    }
+    sd[2 * t] = make_float4(ah[0], ah[1], ah[2], 0.f);
+    sd[2 * t + 1] = make_float4((float)(a[0] - (double)ah[0]), (float)(a[1] - (double)ah[1]),
+                                (float)(a[2] - (double)ah[2]), 0.f);
+    so[2 * t] = make_float4(bh[0], bh[1], bh[2], 0.f);
+    so[2 * t + 1] = make_float4((float)(b[0] - (double)bh[0]), (float)(b[1] - (double)bh[1]),
+                                (float)(b[2] - (double)bh[2]), 0.f);
+}
+
 template <typename R, typename C2>
 __device__ __forceinline__ C2 cmad(C2 a, R k, C2 acc)
 {
@@ -355,7 +385,10 @@ cudaError_t launch_dl_densities(ewald_plan_s *p, const double *q, const double *
 {
     const int64_t N = p->N;
     const unsigned nb = (unsigned)((N + 255) / 256);
-    if (p->near64) {
+    if (p->grid_ds) {  // two float4 per point and triple (64 bytes a point in all)
+        float4 *sd = (float4 *)p->dl_tf;
+        k_dl_densities_ds<<<nb, 256, 0, s>>>(q, n, p->permt, N, sd, sd + 2 * N, p->err);
+    } else if (p->near64) {
         dvec4 *sd = (dvec4 *)p->dl_tf;
         k_dl_densities<dvec4><<<nb, 256, 0, s>>>(q, n, p->permt, N, sd, sd + N, p->err);
     } else {

@@ -173,13 +173,22 @@ def test_double_layer_wraps_positions_and_ignores_antisymmetric_part():
     assert errs(uc, ua)[1] < 1e-12
 
 
-def test_double_layer_on_double_single_plans_is_unsupported():
-    N = 500
-    x, f, q, n = _case("uniform", N, 406)
-    p = ewald.Plan(N, 1.0, 1e-8, F32)   # double-single grid kernels
-    with pytest.raises(ewald.EwaldError) as e:
-        p.apply_combined(dev(x), dev(f), dev(q), dev(n))
-    assert e.value.status == ewald.EWALD_EUNSUPPORTED
+@pytest.mark.parametrize("kind,N,tol", [("uniform", 1500, 1e-8), ("clustered", 1200, 1e-7)])
+def test_double_layer_on_double_single_plans(kind, N, tol):
+    # FP32 bulk at tol <= 1e-7: the densities spread by the double-single P2G
+    # onto FP64 grids, FP64 FFTs and CNV, double-single G2P, FP64 near pairs
+    x, f, q, n = _case(kind, N, 406)
+    p = ewald.Plan(N, 1.0, tol, F32)
+    assert p.params.near_ds == 1 and p.params.tile == 8 and p.params.P >= 8
+    tid = np.arange(0, N, 13)
+    u = _combined(p, x, np.zeros((N, 3)), q, n)
+    ref = dl.ewald(x, dl.densities(q, n), 1.0, targets=tid)
+    l2, mx = errs(u[tid], ref)
+    assert l2 <= tol and mx <= tol, (l2, mx)
+    uc = _combined(p, x, f, q, n)  # and with the Stokeslet part
+    refc = ref + oracle.ewald(x, f, 1.0, targets=tid)
+    l2, mx = errs(uc[tid], refc)
+    assert l2 <= tol and mx <= tol, (l2, mx)
 
 
 def test_double_layer_nan_density_sets_status():

@@ -11,6 +11,8 @@
 
 #include "../../include/ewald_gb300.h"
 
+struct CUtensorMap_st;  // the driver API's TMA descriptor (cuda.h), used by the grid kernels
+
 namespace ewg {
 
 // 32-byte FP64 quadruple (CUDA 13 deprecates double4)
@@ -262,8 +264,14 @@ cudaError_t launch_grid_convert(const void *src, bool src_f64, void *dst, bool d
 // binning), P2G into the FP64 grid, G2P from a double-single copy of it (3 M^3
 // h values then 3 M^3 l values), and that copy.
 bool grid_ds_supported(int P, int T, int M);
+// TMA descriptor of a planar FP32 grid [nc][M][M][M] with boxes of (x, y, z,
+// c) = (S, RR, RR, bc) floats (k_grid.cu); false if it cannot be made
+bool grid_tensor_map(const void *grid, int M, int nc, int S, int RR, int bc, struct CUtensorMap_st *m);
 cudaError_t launch_window_ds(ewald_plan_s *p, cudaStream_t s);
 cudaError_t launch_p2g_ds(ewald_plan_s *p, cudaStream_t s);
+// P2G of three tile-order source components in the double-single force
+// format ((h.xyz, 0), (l.xyz, 0) per point) onto the 3-component FP64 grid
+cudaError_t launch_p2g_ds_with(ewald_plan_s *p, const void *tfrc, double *grid, cudaStream_t s);
 cudaError_t launch_g2p_ds(ewald_plan_s *p, const float *gds, double scale, cudaStream_t s);
 cudaError_t launch_grid_split(const double *src, float *dst, int64_t n, cudaStream_t s);
 

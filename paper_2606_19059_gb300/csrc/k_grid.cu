@@ -957,23 +957,27 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// TMA descriptor of the planar FP32 grid [3][M][M][M] for G2P's staged box of
-// (x, y, z, c) = (S, RR, RR, 3) floats: the global strides (M, M^2, M^3 floats)
-// and the box's inner extent (S floats) are multiples of 16 bytes, as the
-// tensor copy requires.  False if the descriptor cannot be made.
-bool g2p_tensor_map(const void *grid, int M, int S, int RR, CUtensorMap *m)
+}  // namespace
+
+// TMA descriptor of a planar FP32 grid [nc][M][M][M] for G2P's staged boxes of
+// (x, y, z, c) = (S, RR, RR, bc) floats: the global strides (M, M^2, M^3
+// floats) and the box's inner extent (S floats) are multiples of 16 bytes, as
+// the tensor copy requires.  False if the descriptor cannot be made.
+bool grid_tensor_map(const void *grid, int M, int nc, int S, int RR, int bc, CUtensorMap *m)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || M % 4 != 0 || S % 4 != 0 || ((uintptr_t)grid & 15) != 0)
+    if (!enc || M % 4 != 0 || S % 4 != 0 || ((uintptr_t)grid & 15) != 0 || S > 256 || RR > 256)
         return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)M, (cuuint64_t)M, (cuuint64_t)M, 3};
+    const cuuint64_t dims[4] = {(cuuint64_t)M, (cuuint64_t)M, (cuuint64_t)M, (cuuint64_t)nc};
     const cuuint64_t strides[3] = {(cuuint64_t)M * 4, (cuuint64_t)M * M * 4, (cuuint64_t)M * M * M * 4};
-    const cuuint32_t box[4] = {(cuuint32_t)S, (cuuint32_t)RR, (cuuint32_t)RR, 3};
+    const cuuint32_t box[4] = {(cuuint32_t)S, (cuuint32_t)RR, (cuuint32_t)RR, (cuuint32_t)bc};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(grid), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+namespace {
 
 template <int PC>
 cudaError_t run_g2p_planar(const GridArgs &a, int *err, cudaStream_t s)
@@ -986,7 +990,7 @@ cudaError_t run_g2p_planar(const GridArgs &a, int *err, cudaStream_t s)
         return e;
     CUtensorMap m;
     memset(&m, 0, sizeof(m));
-    const int use_tma = g2p_tensor_map(a.grid, a.M, G::S, G::RR, &m) ? 1 : 0;
+    const int use_tma = grid_tensor_map(a.grid, a.M, 3, G::S, G::RR, 3, &m) ? 1 : 0;
     k_g2p_planar<PC><<<a.nt * a.nt * a.nt, kG2PPlanarThreads, sm, s>>>(a, m, use_tma, err);
     return cudaGetLastError();
 }

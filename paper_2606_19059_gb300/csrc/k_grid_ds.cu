@@ -24,6 +24,9 @@
 //
 // G2P: from a double-single copy of the FP64 grid (h = fl32(v), l = fl32(v -
 // h)), staged per tile and component in shared memory (below).
+#include <cuda.h>  // CUtensorMap (the type; descriptors are encoded by k_grid.cu's helper)
+#include <string.h>
+
 #include "internal.h"
 
 namespace ewg {
@@ -339,25 +342,33 @@ struct G2PDs {
     static constexpr int T = kT, RR = T + PC - 1, S = g2p_stride(PC), NR = g2p_rounds(PC, S);
     static constexpr int NCH = (RR + 3) / 4;  // 16-byte chunks per staged row
     static constexpr int PLANE = RR * S, VOL = RR * PLANE;
+    static constexpr int VOLP = (VOL + 31) & ~31;  // the l block starts on a 128-byte boundary
     static constexpr int NW = kG2PDsThreads / 32;
-    static constexpr size_t smem = sizeof(float) * (2 * (size_t)VOL + NW * 6 * 16) + sizeof(int) * NR * 32;
+    // h and l blocks, per-warp weights, the dealt pairs, the TMA mbarrier, and
+    // 128 bytes for aligning the h block
+    static constexpr size_t smem =
+        sizeof(float) * (2 * (size_t)VOLP + NW * 6 * 16) + sizeof(int) * NR * 32 + 8 + 128;
 };
 
 template <int PC>
-__global__ void __launch_bounds__(kG2PDsThreads, 2) k_g2p_ds(GridDsArgs a)
+__global__ void __launch_bounds__(kG2PDsThreads, 2)
+    k_g2p_ds(GridDsArgs a, const __grid_constant__ CUtensorMap tmap, int use_tma, int *err)
 {
     using G = G2PDs<PC>;
     constexpr int T = G::T, RR = G::RR, S = G::S, NR = G::NR, NCH = G::NCH, PLANE = G::PLANE,
-                  VOL = G::VOL, NW = G::NW;
+                  VOLP = G::VOLP, NW = G::NW;
     const int tile = blockIdx.x;
     const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
     if (s0 == s1)
         return;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem =
+        smem_raw + ((128u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u);
     float *vh = (float *)smem;       // [RR][RR][S] h values of the component
-    float *vl = vh + VOL;            // l values
-    float *wsm = vl + VOL;           // per warp [6][16]: x h, x l, y h, y l, z h, z l
+    float *vl = vh + VOLP;           // l values
+    float *wsm = vl + VOLP;          // per warp [6][16]: x h, x l, y h, y l, z h, z l
     int *tab = (int *)(wsm + NW * 6 * 16);  // [NR][32] bank-dealt pairs
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(tab + NR * 32);  // 8-byte aligned: 128-byte rows
     const int nt = a.nt, M = a.M, PW = a.PW;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -374,24 +385,67 @@ __global__ void __launch_bounds__(kG2PDsThreads, 2) k_g2p_ds(GridDsArgs a)
     const int64_t M2 = (int64_t)M * M, M3 = M2 * M;
     const unsigned vh_a = (unsigned)__cvta_generic_to_shared(vh);
     float *w = wsm + warp * 6 * 16;
-    for (int c = 0; c < 3; ++c) {
-        // stage component c: threads over (plane h/l, z, y, chunk)
-        const float *srch = a.gds + c * M3, *srcl = a.gds + (3 + c) * M3;
-        for (int t = threadIdx.x; t < 2 * RR * RR * NCH; t += kG2PDsThreads) {
-            const int half = t / (RR * RR * NCH), r = t - half * (RR * RR * NCH);
-            const int row = r / NCH, ch = r - row * NCH;
-            const int z = row / RR, y = row - z * RR;
-            int gx = tx * T + 4 * ch, gy = ty * T + y, gz = tz * T + z;
-            gx -= gx >= M ? M : 0;
-            gy -= gy >= M ? M : 0;
-            gz -= gz >= M ? M : 0;
-            const float *src = (half ? srcl : srch) + (gz * M2 + (int64_t)gy * M + gx);
-            const unsigned dst = vh_a + 4 * (half * VOL + row * S + 4 * ch);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+    // Interior tiles: each component's h and l blocks come by two TMA tensor
+    // copies (boxes of S x RR x RR floats of the [6][M][M][M] double-single
+    // grid, the staged layout itself), completing phase c of one mbarrier;
+    // blocks that wrap around the periodic grid use 16-byte asynchronous copies.
+    const bool tma = use_tma && tx * T + S <= M && ty * T + RR <= M && tz * T + RR <= M;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-        asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
+    }
+    for (int c = 0; c < 3; ++c) {
+        bool staged = true;
+        if (tma) {
+            if (threadIdx.x == 0) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                             "r"((unsigned)(2 * sizeof(float) * G::VOL))
+                             : "memory");
+#pragma unroll
+                for (int half = 0; half < 2; ++half)
+                    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(vh_a + 4 * half * VOLP),
+                                 "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(tx * T), "r"(ty * T), "r"(tz * T),
+                                 "r"(c + 3 * half), "r"(bar_a)
+                                 : "memory");
+            }
+            for (int it = 0, done = 0; !done; ++it) {  // phase c of the barrier, bounded
+                unsigned ok;
+                asm volatile("{\n\t.reg .pred p;\n\t"
+                             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                             "selp.u32 %0, 1, 0, p;\n\t}"
+                             : "=r"(ok)
+                             : "r"(bar_a), "r"(c & 1)
+                             : "memory");
+                done = ok || it >= (1 << 20);
+                staged = ok;
+            }
+        } else {
+            // stage component c: threads over (plane h/l, z, y, chunk)
+            const float *srch = a.gds + c * M3, *srcl = a.gds + (3 + c) * M3;
+            for (int t = threadIdx.x; t < 2 * RR * RR * NCH; t += kG2PDsThreads) {
+                const int half = t / (RR * RR * NCH), r = t - half * (RR * RR * NCH);
+                const int row = r / NCH, ch = r - row * NCH;
+                const int z = row / RR, y = row - z * RR;
+                int gx = tx * T + 4 * ch, gy = ty * T + y, gz = tz * T + z;
+                gx -= gx >= M ? M : 0;
+                gy -= gy >= M ? M : 0;
+                gz -= gz >= M ? M : 0;
+                const float *src = (half ? srcl : srch) + (gz * M2 + (int64_t)gy * M + gx);
+                const unsigned dst = vh_a + 4 * (half * VOLP + row * S + 4 * ch);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+            }
+            asm volatile("cp.async.commit_group;\n" ::);
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        if (!__syncthreads_and(staged)) {  // the copies did not land: report and leave the tile
+            if (threadIdx.x == 0)
+                atomicOr(err, 2);
+            return;
+        }
         // this lane's pairs
         int roff[NR], ry[NR], rx[NR];
 #pragma unroll
@@ -504,19 +558,25 @@ cudaError_t run_p2g_ds(const GridDsArgs &a, cudaStream_t s)
 }
 
 template <int PC>
-cudaError_t run_g2p_ds(const GridDsArgs &a, cudaStream_t s)
+cudaError_t run_g2p_ds(const GridDsArgs &a, int *err, cudaStream_t s)
 {
     if constexpr (PC > kMaxP) {
         return cudaErrorInvalidValue;
     } else {
         if (a.P != PC)
-            return run_g2p_ds<PC + 1>(a, s);
-        constexpr size_t sm = G2PDs<PC>::smem;
+            return run_g2p_ds<PC + 1>(a, err, s);
+        using G = G2PDs<PC>;
+        constexpr size_t sm = G::smem;
         const cudaError_t e =
             cudaFuncSetAttribute(k_g2p_ds<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess)
             return e;
-        k_g2p_ds<PC><<<a.nt * a.nt * a.nt, kG2PDsThreads, sm, s>>>(a);
+        // the double-single grid as [6][M][M][M] (h planes, then l planes);
+        // one box is one component's S x RR x RR block
+        CUtensorMap m;
+        memset(&m, 0, sizeof(m));
+        const int use_tma = grid_tensor_map(a.gds, a.M, 6, G::S, G::RR, 1, &m) ? 1 : 0;
+        k_g2p_ds<PC><<<a.nt * a.nt * a.nt, kG2PDsThreads, sm, s>>>(a, m, use_tma, err);
         return cudaGetLastError();
     }
 }
@@ -546,12 +606,20 @@ cudaError_t launch_p2g_ds(ewald_plan_s *p, cudaStream_t s)
     return run_p2g_ds<kGridDsMinP>(ds_args(p), s);
 }
 
+cudaError_t launch_p2g_ds_with(ewald_plan_s *p, const void *tfrc, double *grid, cudaStream_t s)
+{
+    GridDsArgs a = ds_args(p);
+    a.tfrc = (const float4 *)tfrc;
+    a.grid = grid;
+    return run_p2g_ds<kGridDsMinP>(a, s);
+}
+
 cudaError_t launch_g2p_ds(ewald_plan_s *p, const float *gds, double scale, cudaStream_t s)
 {
     GridDsArgs a = ds_args(p);
     a.gds = gds;
     a.scale = scale;
-    return run_g2p_ds<kGridDsMinP>(a, s);
+    return run_g2p_ds<kGridDsMinP>(a, p->err, s);
 }
 
 cudaError_t launch_grid_split(const double *src, float *dst, int64_t n, cudaStream_t s)

@@ -565,6 +565,8 @@ def main():
     ap.add_argument("--only-split", action="store_true",
                     help="time FP32-bulk applies at tol 1e-8 on the same points (the split double-single "
                          "near field) and print a short line (for ncu captures)")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run the batched many-box workload alone and print a short line (for ncu captures)")
     ap.add_argument("--only-f32", action="store_true",
                     help="time the FP32-bulk applies only and print a short line (for ncu captures)")
     ap.add_argument("--only-double-layer", action="store_true",
@@ -580,6 +582,12 @@ def main():
     try:
         if args.impl == "reference":
             main_reference(args, rank, world)
+            return
+        if args.only_batch:  # profiling runs: the batched boxes alone
+            r = run_batch(args, rank)
+            if rank == 0:
+                print(json.dumps({"only_batch": True, "ms_per_step": r["ms_per_step"],
+                                  "kernels_per_step": r["kernels_per_step"]}))
             return
         res = run_gpu(args, rank, world)
         if res is None:

@@ -266,10 +266,13 @@ void ewald_autotune_clear(void);
  * tuning.  The batch owns device buffers for every box's x, f (read) and u
  * (written), N x 3 FP64 each, reached through ewald_batch_buffers(); the
  * caller fills x and f there (any stream, ordered before the apply).
- * `nstreams` (1..64) streams carry the boxes concurrently.  Errors: EINVAL
- * for nbox < 1, NULL arrays, a bad N/L/tol entry, nstreams out of range;
- * then as ewald_plan_ex / ewald_autotune.  Nothing is left allocated on
- * failure. */
+ * Boxes that share a grid size and FFT precision keep their grids side by
+ * side in one batch-owned buffer (the boxes' plans use slices of it) and are
+ * transformed by one batched cuFFT plan.  `nstreams` (1..64) is checked and
+ * otherwise unused: every stage runs as one launch over all boxes.  Errors:
+ * EINVAL for nbox < 1, NULL arrays, a bad N/L/tol entry, nstreams out of
+ * range; then as ewald_plan_ex / ewald_autotune.  Nothing is left allocated
+ * on failure. */
 typedef struct ewald_batch_s *ewald_batch_t;
 ewald_status ewald_batch_create(int32_t nbox, const int64_t *N, const double *L, const double *tol,
                                 ewald_dtype dtype, int32_t tune_mode, int32_t nstreams,
@@ -280,13 +283,14 @@ ewald_status ewald_batch_get_params(ewald_batch_t b, int32_t box, ewald_params *
 /* The plan of one box (owned by the batch; valid until ewald_batch_destroy). */
 ewald_status ewald_batch_plan(ewald_batch_t b, int32_t box, ewald_plan_t *out);
 /* Apply every box: u = apply(x, f) per box, as ewald_apply would give with
- * the box's plan.  The first call records the batch into one CUDA graph:
- * binning, far field and sum of each box (boxes by decreasing N dealt
- * round-robin over the streams), and the near field of all boxes as one
- * persistent launch per P2P variant (FP32, compensated FP32, double-single,
- * FP64) whose warps stride over every box's work items; every call launches
- * that graph on `stream`, asynchronously.  Calls on one batch must not
- * overlap in time. */
+ * the box's plan.  The first call records the batch into one CUDA graph in
+ * which every stage covers all boxes: binning (counters, keys, scans,
+ * scatter), P2G and G2P (one launch per kernel instantiation: precision,
+ * tile, support P), CNV, the grid copies G2P reads, the sums -- a block finds
+ * its box by binary search -- the grouped FFTs, and, on a second stream, the
+ * near field of all boxes as one persistent launch per P2P variant (FP32,
+ * compensated FP32, double-single, FP64); every call launches that graph on
+ * `stream`, asynchronously.  Calls on one batch must not overlap in time. */
 ewald_status ewald_batch_apply(ewald_batch_t b, void *stream);
 /* Kernel launches (this library's own kernels) and cuFFT executions in one
  * ewald_batch_apply. */

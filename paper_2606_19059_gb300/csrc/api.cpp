@@ -149,10 +149,14 @@ void free_plan(ewald_plan_s *p)
         cufftDestroy(p->inv);
     void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
                     p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec, p->nflo,
-                    p->tdat, p->tfrc, p->un, p->uf, p->grid, p->spec, p->tab, p->wcoef_dev,
+                    p->tdat, p->tfrc, p->un, p->uf, p->tab, p->wcoef_dev,
                     p->err, p->hx, p->hf, p->hu, p->fftwork, p->wts, p->dl_tf, p->dl_grid, p->dl_spec, p->dl_near};
     for (void *b : bufs)
         dfree(p, b);
+    if (!p->ext_grid) {  // a batch's grouped FFT buffers belong to the batch
+        dfree(p, p->grid);
+        dfree(p, p->spec);
+    }
     if (p->own_grid_g2p && p->grid_g2p)
         dfree(p, p->grid_g2p);
     for (auto &g : p->graphs) {
@@ -582,6 +586,26 @@ ewald_status graph_call(ewald_plan_s *p, int kind, const void *a, const void *b,
 
 // Apply phases for batches of plans (csrc/batch.cpp).
 namespace ewg {
+ewald_status plan_adopt_grid(ewald_plan_s *p, void *grid, void *spec)
+{
+    DeviceGuard dg(p->device);
+    if (!dg.ok)
+        return EWALD_ECUDA;
+    EW_CUDA(cudaStreamSynchronize(p->s2));
+    const bool alias = p->grid_g2p == p->grid;
+    if (!p->ext_grid) {
+        dfree(p, p->grid);
+        dfree(p, p->spec);
+    }
+    EW_CUDA(cudaStreamSynchronize(p->s2));
+    p->grid = grid;
+    p->spec = spec;
+    if (alias)
+        p->grid_g2p = grid;
+    p->ext_grid = true;
+    return EWALD_OK;
+}
+
 ewald_status plan_set_stream_priority(ewald_plan_s *p, int priority)
 {
     DeviceGuard dg(p->device);
@@ -605,26 +629,6 @@ ewald_status plan_set_stream_priority(ewald_plan_s *p, int priority)
     return EWALD_OK;
 }
 
-ewald_status plan_bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t s)
-{
-    return bin(p, x, f, s);
-}
-
-ewald_status plan_far(ewald_plan_s *p, cudaStream_t s)
-{
-    const double h3 = p->g.h * p->g.h * p->g.h;
-    EW_CUDA(launch_p2g(p, s));
-    EW_ST(fgc(p, 8.0 * kPi * h3 / (double)p->g.nreal, s));
-    EW_CUDA(prep_g2p_grid(p, p->grid, s));
-    EW_CUDA(launch_g2p(p, p->grid_g2p, 1.0, s));
-    return EWALD_OK;
-}
-
-ewald_status plan_sum(ewald_plan_s *p, double *u, cudaStream_t s)
-{
-    EW_CUDA(launch_sum(p, nullptr, u, s));
-    return EWALD_OK;
-}
 }  // namespace ewg
 
 extern "C" {

@@ -10,11 +10,15 @@
 // every candidate meets the same error bound, so the fastest one wins.
 //
 // A batch holds one plan per box (each with its own N, L, tol and tuned
-// parameters) and device buffers for the boxes' x, f and u.  The first apply
-// captures the whole batch into one CUDA graph: binning, far field and sum per
-// box over several capture streams (small boxes run side by side), and the
-// near field of all boxes as one persistent launch per P2P variant; later
-// applies replay the graph with one launch.
+// parameters) and device buffers for the boxes' x, f and u.  Every stage runs
+// for all boxes at once: one launch per kernel (per kernel instantiation for
+// the grid stages, which fix P at compile time), a block finding its box by
+// binary search over the boxes' block offsets; the near field of all boxes is
+// one persistent launch per P2P variant on a second stream; and the boxes
+// that share a grid size and FFT precision keep their grids side by side in
+// one buffer, transformed by one batched cuFFT plan.  The first apply
+// captures all of it into one CUDA graph; later applies replay the graph with
+// one launch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -169,6 +173,17 @@ ewald_status time_candidate(int64_t N, double L, double tol, ewald_dtype dtype,
 
 using namespace ewg;
 
+// Boxes with the same grid size and FFT precision: their grids and half
+// spectra side by side, one batched forward and one inverse cuFFT plan.
+struct FftGroup {
+    int M = 0;
+    bool f64 = false;
+    int nb = 0;
+    void *grid = nullptr, *spec = nullptr;
+    cufftHandle fwd = 0, inv = 0;
+    bool have_fwd = false, have_inv = false;
+};
+
 struct ewald_batch_s {
     int device = 0;
     int nbox = 0;
@@ -176,13 +191,19 @@ struct ewald_batch_s {
     std::vector<int64_t> N;
     std::vector<size_t> off;  // per box: offset (in doubles) of its x, f, u in `buf`
     double *buf = nullptr;    // x, f, u of every box: 9 N doubles a box
-    std::vector<cudaStream_t> streams;
-    cudaStream_t cap = nullptr;
+    std::vector<FftGroup> ffts;
+    cudaStream_t cap = nullptr, side = nullptr;  // capture origin (far fields with FP64 FFTs), near field
+    cudaStream_t far32 = nullptr;                // far fields with FP32 FFTs
+    cudaEvent_t far32_done = nullptr;
     cudaEvent_t fork = nullptr;
-    std::vector<cudaEvent_t> joins;
-    std::vector<cudaEvent_t> binned;  // per stream: its boxes binned
+    cudaEvent_t binned = nullptr;     // every box binned
     cudaEvent_t near_done = nullptr;  // the batched near field finished
     P2PBoxes *near = nullptr;         // one persistent P2P launch per variant
+    BinBoxes *bin = nullptr;          // binning and sums
+    GridBoxes *grids = nullptr;       // P2G and G2P (FP32 and FP64 grid kernels)
+    DsGridBoxes *dsgrids = nullptr;   // the double-single grid stages
+    ScaleBoxes *scale = nullptr;      // CNV
+    ConvBoxes *conv = nullptr;        // FP64 grids -> FP32 copies for G2P
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -201,72 +222,172 @@ void free_batch(ewald_batch_s *b)
         ewald_destroy(p);
     if (b->buf)
         cudaFree(b->buf);
-    for (cudaStream_t s : b->streams)
-        if (s)
-            cudaStreamDestroy(s);
+    for (FftGroup &g : b->ffts) {
+        if (g.have_fwd)
+            cufftDestroy(g.fwd);
+        if (g.have_inv)
+            cufftDestroy(g.inv);
+        if (g.grid)
+            cudaFree(g.grid);
+        if (g.spec)
+            cudaFree(g.spec);
+    }
     if (b->cap)
         cudaStreamDestroy(b->cap);
-    if (b->fork)
-        cudaEventDestroy(b->fork);
-    for (cudaEvent_t e : b->joins)
+    if (b->side)
+        cudaStreamDestroy(b->side);
+    if (b->far32)
+        cudaStreamDestroy(b->far32);
+    for (cudaEvent_t e : {b->fork, b->binned, b->near_done, b->far32_done})
         if (e)
             cudaEventDestroy(e);
-    for (cudaEvent_t e : b->binned)
-        if (e)
-            cudaEventDestroy(e);
-    if (b->near_done)
-        cudaEventDestroy(b->near_done);
     p2p_boxes_destroy(b->near);
+    bin_boxes_destroy(b->bin);
+    grid_boxes_destroy(b->grids);
+    ds_grid_boxes_destroy(b->dsgrids);
+    scale_boxes_destroy(b->scale);
+    conv_boxes_destroy(b->conv);
     delete b;
 }
 
-// Record every box's apply into one graph: boxes by decreasing N, dealt
-// round-robin over the capture streams.  Each stream bins its boxes; one
-// persistent near-field launch per P2P variant then covers every box's work
-// items while the streams run their boxes' far fields; each box's sum waits
-// for both.
+// Group the boxes' FFTs by (M, precision), move each plan's grid and half
+// spectrum into its group's buffer, and build the multi-box launches.
+ewald_status setup_stages(ewald_batch_s *b)
+{
+    std::map<std::pair<int, int>, std::vector<int>> groups;
+    for (int i = 0; i < b->nbox; ++i)
+        groups[{b->plans[i]->g.M, b->plans[i]->fft64 ? 1 : 0}].push_back(i);
+    std::vector<void *> grid(b->nbox), spec(b->nbox), g2p(b->nbox);
+    for (auto &kv : groups) {
+        FftGroup g;
+        g.M = kv.first.first;
+        g.f64 = kv.first.second != 0;
+        g.nb = (int)kv.second.size();
+        const ewald_plan_s *p0 = b->plans[kv.second[0]];
+        const size_t fs = g.f64 ? 8 : 4;
+        const int64_t nreal = p0->g.nreal, ncplx = p0->g.ncplx;
+        b->ffts.push_back(g);
+        FftGroup &G = b->ffts.back();
+        if (cudaMalloc(&G.grid, 3 * fs * (size_t)nreal * G.nb) != cudaSuccess ||
+            cudaMalloc(&G.spec, 3 * 2 * fs * (size_t)ncplx * G.nb) != cudaSuccess) {
+            cudaGetLastError();
+            return EWALD_ENOMEM;
+        }
+        int n3[3] = {G.M, G.M, G.M}, er[3] = {G.M, G.M, G.M}, ec[3] = {G.M, G.M, G.M / 2 + 1};
+        size_t ws = 0;
+        if (cufftCreate(&G.fwd) != CUFFT_SUCCESS)
+            return EWALD_ECUFFT;
+        G.have_fwd = true;
+        if (cufftMakePlanMany(G.fwd, 3, n3, er, 1, (int)nreal, ec, 1, (int)ncplx, G.f64 ? CUFFT_D2Z : CUFFT_R2C,
+                              3 * G.nb, &ws) != CUFFT_SUCCESS)
+            return EWALD_ECUFFT;
+        if (cufftCreate(&G.inv) != CUFFT_SUCCESS)
+            return EWALD_ECUFFT;
+        G.have_inv = true;
+        if (cufftMakePlanMany(G.inv, 3, n3, ec, 1, (int)ncplx, er, 1, (int)nreal, G.f64 ? CUFFT_Z2D : CUFFT_C2R,
+                              3 * G.nb, &ws) != CUFFT_SUCCESS)
+            return EWALD_ECUFFT;
+        for (int k = 0; k < G.nb; ++k) {
+            const int i = kv.second[k];
+            void *gk = (char *)G.grid + 3 * fs * (size_t)nreal * k;
+            void *sk = (char *)G.spec + 3 * 2 * fs * (size_t)ncplx * k;
+            TUNE_ST(plan_adopt_grid(b->plans[i], gk, sk));
+            grid[i] = gk;
+            spec[i] = sk;
+            g2p[i] = b->plans[i]->grid_g2p;
+        }
+    }
+    std::vector<const double *> xs(b->nbox), fs(b->nbox);
+    std::vector<double *> us(b->nbox), grid64(b->nbox);
+    std::vector<float *> gds(b->nbox);
+    std::vector<const void *> csrc;
+    std::vector<void *> cdst;
+    std::vector<int64_t> cn;
+    for (int i = 0; i < b->nbox; ++i) {
+        double *x = b->buf + b->off[i];
+        xs[i] = x;
+        fs[i] = x + 3 * b->N[i];
+        us[i] = x + 6 * b->N[i];
+        ewald_plan_s *p = b->plans[i];
+        grid64[i] = (double *)grid[i];
+        gds[i] = (float *)p->grid_g2p;
+        if (p->own_grid_g2p && !p->grid_ds) {  // FP64 FFT, FP32 kernels: G2P reads an FP32 copy
+            csrc.push_back(grid[i]);
+            cdst.push_back(p->grid_g2p);
+            cn.push_back(3 * p->g.nreal);
+        }
+    }
+    if (bin_boxes_create(b->plans.data(), xs.data(), fs.data(), us.data(), b->nbox, &b->bin) != cudaSuccess ||
+        grid_boxes_create(b->plans.data(), grid.data(), g2p.data(), b->nbox, &b->grids) != cudaSuccess ||
+        ds_grid_boxes_create(b->plans.data(), grid64.data(), gds.data(), b->nbox, &b->dsgrids) != cudaSuccess ||
+        scale_boxes_create(b->plans.data(), spec.data(), b->nbox, &b->scale) != cudaSuccess ||
+        conv_boxes_create(csrc, cdst, cn, &b->conv) != cudaSuccess) {
+        cudaGetLastError();
+        return EWALD_ECUDA;
+    }
+    return EWALD_OK;
+}
+
+#define BATCH_CUDA(call)                                 \
+    do {                                                 \
+        if (st == EWALD_OK && (call) != cudaSuccess)     \
+            st = EWALD_ECUDA;                            \
+    } while (0)
+
+// Record one batched apply into a graph: binning of every box; then three
+// branches side by side -- the near field of every box (persistent P2P
+// launches), and the far fields of the boxes with FP64 FFTs and with FP32
+// FFTs, each as P2G, the grouped forward FFTs, CNV, the grouped inverse FFTs,
+// the G2P grid copies and G2P -- joined before the sums.
 ewald_status capture(ewald_batch_s *b)
 {
-    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    cudaStream_t s = b->cap;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess)
         return EWALD_ECUDA;
     ewald_status st = EWALD_OK;
-    if (cudaEventRecord(b->fork, b->cap) != cudaSuccess)
-        st = EWALD_ECUDA;
-    for (size_t k = 0; k < b->streams.size() && st == EWALD_OK; ++k)
-        if (cudaStreamWaitEvent(b->streams[k], b->fork, 0) != cudaSuccess)
-            st = EWALD_ECUDA;
-    std::vector<int> order(b->nbox);
-    for (int i = 0; i < b->nbox; ++i)
-        order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->N[a] > b->N[c]; });
-    const size_t ns = b->streams.size();
-    for (int r = 0; r < b->nbox && st == EWALD_OK; ++r) {
-        const int i = order[r];
-        double *x = b->buf + b->off[i];
-        st = plan_bin(b->plans[i], x, x + 3 * b->N[i], b->streams[r % ns]);
+    BATCH_CUDA(bin_boxes_launch(b->bin, s));
+    BATCH_CUDA(ds_grid_boxes_launch(b->dsgrids, 0, s));
+    BATCH_CUDA(cudaEventRecord(b->binned, s));
+    BATCH_CUDA(cudaStreamWaitEvent(b->side, b->binned, 0));
+    BATCH_CUDA(cudaStreamWaitEvent(b->far32, b->binned, 0));
+    BATCH_CUDA(p2p_boxes_launch(b->near, b->side));
+    BATCH_CUDA(cudaEventRecord(b->near_done, b->side));
+    for (int f64 = 1; f64 >= 0 && st == EWALD_OK; --f64) {
+        cudaStream_t fs = f64 ? s : b->far32;
+        BATCH_CUDA(grid_boxes_launch(b->grids, 0, fs, f64));
+        if (f64)
+            BATCH_CUDA(ds_grid_boxes_launch(b->dsgrids, 1, fs));
+        for (FftGroup &g : b->ffts) {
+            if (st != EWALD_OK || g.f64 != (f64 != 0))
+                continue;
+            if (cufftSetStream(g.fwd, fs) != CUFFT_SUCCESS ||
+                (g.f64 ? cufftExecD2Z(g.fwd, (cufftDoubleReal *)g.grid, (cufftDoubleComplex *)g.spec)
+                       : cufftExecR2C(g.fwd, (cufftReal *)g.grid, (cufftComplex *)g.spec)) != CUFFT_SUCCESS)
+                st = EWALD_ECUFFT;
+        }
+        BATCH_CUDA(scale_boxes_launch(b->scale, fs, f64));
+        for (FftGroup &g : b->ffts) {
+            if (st != EWALD_OK || g.f64 != (f64 != 0))
+                continue;
+            if (cufftSetStream(g.inv, fs) != CUFFT_SUCCESS ||
+                (g.f64 ? cufftExecZ2D(g.inv, (cufftDoubleComplex *)g.spec, (cufftDoubleReal *)g.grid)
+                       : cufftExecC2R(g.inv, (cufftComplex *)g.spec, (cufftReal *)g.grid)) != CUFFT_SUCCESS)
+                st = EWALD_ECUFFT;
+        }
+        if (f64) {
+            BATCH_CUDA(conv_boxes_launch(b->conv, fs));
+            BATCH_CUDA(ds_grid_boxes_launch(b->dsgrids, 2, fs));
+        }
+        BATCH_CUDA(grid_boxes_launch(b->grids, 1, fs, f64));
+        if (f64)
+            BATCH_CUDA(ds_grid_boxes_launch(b->dsgrids, 3, fs));
     }
-    for (size_t k = 0; k < ns && st == EWALD_OK; ++k)
-        if (cudaEventRecord(b->binned[k], b->streams[k]) != cudaSuccess ||
-            cudaStreamWaitEvent(b->cap, b->binned[k], 0) != cudaSuccess)
-            st = EWALD_ECUDA;
-    if (st == EWALD_OK && (p2p_boxes_launch(b->near, b->cap) != cudaSuccess ||
-                           cudaEventRecord(b->near_done, b->cap) != cudaSuccess))
-        st = EWALD_ECUDA;
-    for (int r = 0; r < b->nbox && st == EWALD_OK; ++r)
-        st = plan_far(b->plans[order[r]], b->streams[r % ns]);
-    for (size_t k = 0; k < ns && st == EWALD_OK; ++k)
-        if (cudaStreamWaitEvent(b->streams[k], b->near_done, 0) != cudaSuccess)
-            st = EWALD_ECUDA;
-    for (int r = 0; r < b->nbox && st == EWALD_OK; ++r) {
-        const int i = order[r];
-        st = plan_sum(b->plans[i], b->buf + b->off[i] + 6 * b->N[i], b->streams[r % ns]);
-    }
-    for (size_t k = 0; k < b->streams.size() && st == EWALD_OK; ++k)
-        if (cudaEventRecord(b->joins[k], b->streams[k]) != cudaSuccess ||
-            cudaStreamWaitEvent(b->cap, b->joins[k], 0) != cudaSuccess)
-            st = EWALD_ECUDA;
+    BATCH_CUDA(cudaEventRecord(b->far32_done, b->far32));
+    BATCH_CUDA(cudaStreamWaitEvent(s, b->far32_done, 0));
+    BATCH_CUDA(cudaStreamWaitEvent(s, b->near_done, 0));
+    BATCH_CUDA(sum_boxes_launch(b->bin, s));
     cudaGraph_t g = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+    const cudaError_t ee = cudaStreamEndCapture(s, &g);
     if (st == EWALD_OK && ee != cudaSuccess)
         st = EWALD_ECUDA;
     if (st != EWALD_OK) {
@@ -431,22 +552,23 @@ ewald_status ewald_batch_create(int32_t nbox, const int64_t *N, const double *L,
     }
     if (st == EWALD_OK && cudaMemset(b->buf, 0, sizeof(double) * total) != cudaSuccess)
         st = EWALD_ECUDA;
-    b->streams.assign(std::min(nstreams, nbox), nullptr);
-    b->joins.assign(b->streams.size(), nullptr);
-    b->binned.assign(b->streams.size(), nullptr);
-    for (size_t k = 0; k < b->streams.size() && st == EWALD_OK; ++k)
-        if (cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->joins[k], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->binned[k], cudaEventDisableTiming) != cudaSuccess)
-            st = EWALD_ECUDA;
+    (void)nstreams;  // every stage is one launch over all boxes now
     if (st == EWALD_OK && (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaStreamCreateWithFlags(&b->far32, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&b->far32_done, cudaEventDisableTiming) != cudaSuccess ||
                            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&b->binned, cudaEventDisableTiming) != cudaSuccess ||
                            cudaEventCreateWithFlags(&b->near_done, cudaEventDisableTiming) != cudaSuccess))
         st = EWALD_ECUDA;
     if (st == EWALD_OK && p2p_boxes_create(b->plans.data(), nbox, &b->near) != cudaSuccess) {
         cudaGetLastError();
         st = EWALD_ECUDA;
     }
+    if (st == EWALD_OK)
+        st = setup_stages(b);
+    if (st == EWALD_OK && cudaDeviceSynchronize() != cudaSuccess)
+        st = EWALD_ECUDA;
     if (st != EWALD_OK) {
         free_batch(b);
         return st;
@@ -507,15 +629,10 @@ ewald_status ewald_batch_launch_counts(ewald_batch_t b, int32_t *kernels, int32_
 {
     if (!b || !kernels || !ffts)
         return EWALD_EINVAL;
-    int32_t k = 0, f = 0;
-    for (ewald_plan_t p : b->plans) {
-        int32_t kp = 0, fp = 0;
-        ewald_launch_counts(p, &kp, &fp);
-        k += kp - 1;  // each box's own P2P launch is replaced ...
-        f += fp;
-    }
-    *kernels = k + p2p_boxes_launches(b->near);  // ... by one per variant
-    *ffts = f;
+    *kernels = bin_boxes_launches(b->bin) + sum_boxes_launches(b->bin) + p2p_boxes_launches(b->near) +
+               grid_boxes_launches(b->grids) + ds_grid_boxes_launches(b->dsgrids) +
+               scale_boxes_launches(b->scale) + conv_boxes_launches(b->conv);
+    *ffts = 2 * (int32_t)b->ffts.size();
     return EWALD_OK;
 }
 

@@ -61,6 +61,21 @@ __host__ __device__ inline int p2p_group_cell(int g, int nc, int K, int &ncg)
     return row * nc + x0;
 }
 
+// The box of global block (or element) index g among many plans launched
+// together: base[b] <= g < base[b + 1] (base holds nbox + 1 prefix offsets).
+__device__ __forceinline__ int find_box(const int *base, int nbox, int g)
+{
+    int lo = 0, hi = nbox;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= g)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 // double-single window weights: bins of one axis padded to a multiple of 4
 inline int ds_window_stride(int P) { return (P + 3) & ~3; }
 
@@ -146,6 +161,7 @@ struct ewald_plan_s {
     void *tdat = nullptr, *tfrc = nullptr;        // tile-sorted window data / forces
     void *un = nullptr, *uf = nullptr;            // near / far results, user order
     void *grid = nullptr;                         // 3 M^3 real
+    bool ext_grid = false;                        // grid and spec belong to a batch's grouped FFT
     void *grid_g2p = nullptr;                     // G2P input in the kernels' precision (may alias grid)
     bool own_grid_g2p = false;
     // double layer (Sec. 2.3), allocated by the first combined apply: the
@@ -242,11 +258,46 @@ cudaError_t p2p_boxes_create(ewald_plan_s *const *plans, int n, P2PBoxes **out);
 cudaError_t p2p_boxes_launch(const P2PBoxes *b, cudaStream_t s);
 int p2p_boxes_launches(const P2PBoxes *b);
 void p2p_boxes_destroy(P2PBoxes *b);
-// Apply phases for batches: binning (positions and forces), the far field into
-// the plan's u^F, and the final sum (after the near field has run).
-ewald_status plan_bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t s);
-ewald_status plan_far(ewald_plan_s *p, cudaStream_t s);
-ewald_status plan_sum(ewald_plan_s *p, double *u, cudaStream_t s);
+// Batches: every box's binning, sum and FP64 -> FP32 grid copies as one
+// launch per kernel (k_bin.cu); x, f, u per box are its batch buffers.
+struct BinBoxes;
+cudaError_t bin_boxes_create(ewald_plan_s *const *plans, const double *const *x, const double *const *f,
+                             double *const *u, int n, BinBoxes **out);
+cudaError_t bin_boxes_launch(const BinBoxes *b, cudaStream_t s);
+cudaError_t sum_boxes_launch(const BinBoxes *b, cudaStream_t s);
+int bin_boxes_launches(const BinBoxes *b);
+int sum_boxes_launches(const BinBoxes *b);
+void bin_boxes_destroy(BinBoxes *b);
+struct ConvBoxes;
+cudaError_t conv_boxes_create(const std::vector<const void *> &src, const std::vector<void *> &dst,
+                              const std::vector<int64_t> &n, ConvBoxes **out);
+cudaError_t conv_boxes_launch(const ConvBoxes *b, cudaStream_t s);
+int conv_boxes_launches(const ConvBoxes *b);
+void conv_boxes_destroy(ConvBoxes *b);
+// P2G (kind 0) and G2P (kind 1) of many plans: one launch per kernel
+// instantiation (k_grid.cu; plans with double-single grid kernels excluded)
+struct GridBoxes;
+cudaError_t grid_boxes_create(ewald_plan_s *const *plans, void *const *grid, void *const *g2p, int n, GridBoxes **out);
+cudaError_t grid_boxes_launch(const GridBoxes *b, int kind, cudaStream_t s, int fft64);
+int grid_boxes_launches(const GridBoxes *b);
+void grid_boxes_destroy(GridBoxes *b);
+// the double-single grid stages of many plans (k_grid_ds.cu): stage 0 window
+// weights, 1 P2G, 2 the double-single grid copies, 3 G2P
+struct DsGridBoxes;
+cudaError_t ds_grid_boxes_create(ewald_plan_s *const *plans, double *const *grid, float *const *gds, int n,
+                                 DsGridBoxes **out);
+cudaError_t ds_grid_boxes_launch(const DsGridBoxes *b, int stage, cudaStream_t s);
+int ds_grid_boxes_launches(const DsGridBoxes *b);
+void ds_grid_boxes_destroy(DsGridBoxes *b);
+// the CNV of many plans in one launch per precision (k_fgc.cu)
+struct ScaleBoxes;
+cudaError_t scale_boxes_create(ewald_plan_s *const *plans, void *const *spec, int n, ScaleBoxes **out);
+cudaError_t scale_boxes_launch(const ScaleBoxes *b, cudaStream_t s, int fft64);
+int scale_boxes_launches(const ScaleBoxes *b);
+void scale_boxes_destroy(ScaleBoxes *b);
+// Batches: the plan's real grid and half spectrum replaced by slices of a
+// batch-owned buffer (its own are freed; the batch frees the new ones).
+ewald_status plan_adopt_grid(ewald_plan_s *p, void *grid, void *spec);
 cudaError_t launch_sum(ewald_plan_s *p, const double *f, double *u, cudaStream_t s);
 // Recreate the plan's own streams (the near-field side stream and the graph
 // capture origin) with a CUDA stream priority, for a server slot whose stream

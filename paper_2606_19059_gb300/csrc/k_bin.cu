@@ -11,6 +11,9 @@
 // inputs cost no padding.
 #include <math.h>
 
+#include <new>
+#include <vector>
+
 #include "internal.h"
 
 namespace ewg {
@@ -78,9 +81,8 @@ __device__ __forceinline__ Bin compute_bin(const KeyArgs &k, int64_t i)
     return b;
 }
 
-__global__ void k_bin_keys(KeyArgs k)
+__device__ __forceinline__ void bin_keys_body(const KeyArgs &k, int64_t i)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= k.N)
         return;
     Bin b = compute_bin(k, i);
@@ -96,9 +98,8 @@ __global__ void k_bin_keys(KeyArgs k)
 }
 
 template <typename R, typename R4>
-__global__ void k_bin_scatter(KeyArgs k)
+__device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= k.N)
         return;
     Bin b = compute_bin(k, i);
@@ -236,10 +237,9 @@ __device__ __forceinline__ int scan_value(const ScanJob &j, int i)
     return (cnt + j.chunk - 1) / j.chunk;
 }
 
-__global__ void __launch_bounds__(1024) k_scan(ScanJob j0, ScanJob j1, ScanJob j2)
+__device__ __forceinline__ void scan_body(const ScanJob &j)
 {
     __shared__ int32_t wsum[32];
-    const ScanJob j = blockIdx.x == 0 ? j0 : (blockIdx.x == 1 ? j1 : j2);
     const int n = j.n;
     int32_t *__restrict__ out = j.out;
     int tid = threadIdx.x, nthr = blockDim.x;
@@ -282,6 +282,51 @@ __global__ void __launch_bounds__(1024) k_scan(ScanJob j0, ScanJob j1, ScanJob j
         out[n] = run;
 }
 
+__global__ void k_bin_keys(KeyArgs k)
+{
+    bin_keys_body(k, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <typename R, typename R4>
+__global__ void k_bin_scatter(KeyArgs k)
+{
+    bin_scatter_body<R, R4>(k, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void __launch_bounds__(1024) k_scan(ScanJob j0, ScanJob j1, ScanJob j2)
+{
+    scan_body(blockIdx.x == 0 ? j0 : (blockIdx.x == 1 ? j1 : j2));
+}
+
+// Many plans' boxes in one launch: a block finds its box by binary search over
+// the boxes' block offsets (base) and runs the same body on that box's data.
+__global__ void k_bin_keys_boxes(const KeyArgs *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    bin_keys_body(boxes[b], (int64_t)((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x);
+}
+template <typename R, typename R4>
+__global__ void k_bin_scatter_boxes(const KeyArgs *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    bin_scatter_body<R, R4>(boxes[b], (int64_t)((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x);
+}
+__global__ void __launch_bounds__(1024) k_scan_jobs(const ScanJob *__restrict__ jobs)
+{
+    scan_body(jobs[blockIdx.x]);
+}
+// zero n[k] int32 values at p[k] for every job k (threads over the
+// concatenated ranges, base = prefix offsets in blocks of 256)
+struct ZeroJob {
+    int32_t *p;
+    int n;
+};
+__global__ void k_zero_jobs(const ZeroJob *__restrict__ jobs, const int *__restrict__ base, int njob)
+{
+    const int b = find_box(base, njob, (int)blockIdx.x);
+    const int i = ((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x;
+    if (i < jobs[b].n)
+        jobs[b].p[i] = 0;
+}
+
 // Step a7 (Algorithm 1, SUM): u = u^N + u^F in FP64, user order (the self
 // term is already in u^N, see k_p2p.cu).
 template <typename R>
@@ -292,6 +337,32 @@ __global__ void k_sum(const R *__restrict__ un, const R *__restrict__ uf, double
     if (i >= n3)
         return;
     u[i] = (double)un[i] + (double)uf[i];
+}
+
+// elementwise jobs of many boxes: the sum (src = u^N, src2 = u^F), or a copy
+// with conversion (src2 unused)
+struct EltJob {
+    const void *src, *src2;
+    void *dst;
+    int64_t n;
+};
+template <typename R>
+__global__ void k_sum_jobs(const EltJob *__restrict__ jobs, const int *__restrict__ base, int njob)
+{
+    const int b = find_box(base, njob, (int)blockIdx.x);
+    const EltJob &j = jobs[b];
+    const int64_t i = (int64_t)((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x;
+    if (i < j.n)
+        ((double *)j.dst)[i] = (double)((const R *)j.src)[i] + (double)((const R *)j.src2)[i];
+}
+template <typename A, typename B>
+__global__ void k_convert_jobs(const EltJob *__restrict__ jobs, const int *__restrict__ base, int njob)
+{
+    const int b = find_box(base, njob, (int)blockIdx.x);
+    const EltJob &j = jobs[b];
+    const int64_t i = (int64_t)((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x;
+    if (i < j.n)
+        ((B *)j.dst)[i] = (B)((const A *)j.src)[i];
 }
 
 template <typename R>
@@ -441,6 +512,206 @@ cudaError_t launch_grid_convert(const void *src, bool src_f64, void *dst, bool d
     else
         k_convert<float, float><<<nb, 256, 0, s>>>((const float *)src, (float *)dst, n);
     return cudaGetLastError();
+}
+
+// ---- many plans' binning and sums in one launch per kernel (batches) -------
+namespace {
+template <typename T>
+cudaError_t upload(const std::vector<T> &v, T **d)
+{
+    *d = nullptr;
+    if (v.empty())
+        return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)d, sizeof(T) * v.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+// prefix offsets (in blocks of 256) over per-box element counts
+std::vector<int> block_base(const std::vector<int64_t> &n, unsigned &grid)
+{
+    std::vector<int> b(1, 0);
+    for (int64_t v : n)
+        b.push_back(b.back() + (int)((v + 255) / 256));
+    grid = (unsigned)b.back();
+    return b;
+}
+}  // namespace
+
+struct BinBoxes {
+    KeyArgs *keys = nullptr, *scat[2] = {nullptr, nullptr};  // scat[0]: FP32 records, [1]: FP64
+    int *keys_base = nullptr, *scat_base[2] = {nullptr, nullptr}, *zero_base = nullptr;
+    int nkeys = 0, nscat[2] = {0, 0}, nzero = 0, njobs = 0;
+    unsigned keys_grid = 0, scat_grid[2] = {0, 0}, zero_grid = 0;
+    ScanJob *jobs = nullptr;
+    ZeroJob *zero = nullptr;
+    // sums (u = u^N + u^F), by result precision: [0] FP32, [1] FP64
+    EltJob *sum[2] = {nullptr, nullptr};
+    int *sum_base[2] = {nullptr, nullptr}, nsum[2] = {0, 0};
+    unsigned sum_grid[2] = {0, 0};
+};
+
+cudaError_t bin_boxes_create(ewald_plan_s *const *plans, const double *const *x, const double *const *f,
+                             double *const *u, int n, BinBoxes **out)
+{
+    BinBoxes *b = new (std::nothrow) BinBoxes;
+    if (!b)
+        return cudaErrorMemoryAllocation;
+    std::vector<KeyArgs> keys, scat[2];
+    std::vector<int64_t> nk, ns[2], nz, nsum[2];
+    std::vector<ScanJob> jobs;
+    std::vector<ZeroJob> zero;
+    std::vector<EltJob> sum[2];
+    for (int i = 0; i < n; ++i) {
+        ewald_plan_s *p = plans[i];
+        const Geometry &g = p->g;
+        BinArgs a;
+        a.x = x[i];
+        a.f = f[i];
+        a.N = p->N;
+        a.L = p->prm.L;
+        a.cell = g.cell;
+        a.h = g.h;
+        a.nc = g.nc;
+        a.M = g.M;
+        a.P = g.P;
+        a.T = g.T;
+        a.nt = g.nt;
+        a.f64 = p->near64;
+        a.tf_ds = p->grid_ds;
+        const KeyArgs k = key_args(p, a);
+        keys.push_back(k);
+        nk.push_back(p->N);
+        scat[a.f64 ? 1 : 0].push_back(k);
+        ns[a.f64 ? 1 : 0].push_back(p->N);
+        jobs.push_back(ScanJob{p->cntn, p->startn, g.nkeys, 0, 0, 0});
+        jobs.push_back(ScanJob{p->cntt, p->startt, g.ntiles, 0, 0, 0});
+        jobs.push_back(ScanJob{p->cntn, p->item_off, p2p_groups(g.nc, g.K), kP2PChunk, g.nc, g.K});
+        zero.push_back(ZeroJob{p->cntn, g.nkeys});
+        nz.push_back(g.nkeys);
+        zero.push_back(ZeroJob{p->cntt, g.ntiles});
+        nz.push_back(g.ntiles);
+        const int r = p->near64 ? 1 : 0;
+        sum[r].push_back(EltJob{p->un, p->uf, u[i], 3 * p->N});
+        nsum[r].push_back(3 * p->N);
+        p->positions_valid = true;
+    }
+    cudaError_t e = cudaSuccess;
+    std::vector<int> kb = block_base(nk, b->keys_grid), zb = block_base(nz, b->zero_grid);
+    b->nkeys = (int)keys.size();
+    b->nzero = (int)zero.size();
+    b->njobs = (int)jobs.size();
+    if (e == cudaSuccess) e = upload(keys, &b->keys);
+    if (e == cudaSuccess) e = upload(kb, &b->keys_base);
+    if (e == cudaSuccess) e = upload(jobs, &b->jobs);
+    if (e == cudaSuccess) e = upload(zero, &b->zero);
+    if (e == cudaSuccess) e = upload(zb, &b->zero_base);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        std::vector<int> sb = block_base(ns[r], b->scat_grid[r]), ub = block_base(nsum[r], b->sum_grid[r]);
+        b->nscat[r] = (int)scat[r].size();
+        b->nsum[r] = (int)sum[r].size();
+        e = upload(scat[r], &b->scat[r]);
+        if (e == cudaSuccess) e = upload(sb, &b->scat_base[r]);
+        if (e == cudaSuccess) e = upload(sum[r], &b->sum[r]);
+        if (e == cudaSuccess) e = upload(ub, &b->sum_base[r]);
+    }
+    if (e != cudaSuccess) {
+        bin_boxes_destroy(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+// counters zeroed, keys, the three scans per box, scatter: every box's
+// binning in four launches (five with both record precisions)
+cudaError_t bin_boxes_launch(const BinBoxes *b, cudaStream_t s)
+{
+    if (b->nzero)
+        k_zero_jobs<<<b->zero_grid, 256, 0, s>>>(b->zero, b->zero_base, b->nzero);
+    if (b->nkeys)
+        k_bin_keys_boxes<<<b->keys_grid, 256, 0, s>>>(b->keys, b->keys_base, b->nkeys);
+    if (b->njobs)
+        k_scan_jobs<<<b->njobs, 1024, 0, s>>>(b->jobs);
+    if (b->nscat[0])
+        k_bin_scatter_boxes<float, float4><<<b->scat_grid[0], 256, 0, s>>>(b->scat[0], b->scat_base[0], b->nscat[0]);
+    if (b->nscat[1])
+        k_bin_scatter_boxes<double, dvec4><<<b->scat_grid[1], 256, 0, s>>>(b->scat[1], b->scat_base[1], b->nscat[1]);
+    return cudaGetLastError();
+}
+
+cudaError_t sum_boxes_launch(const BinBoxes *b, cudaStream_t s)
+{
+    if (b->nsum[0])
+        k_sum_jobs<float><<<b->sum_grid[0], 256, 0, s>>>(b->sum[0], b->sum_base[0], b->nsum[0]);
+    if (b->nsum[1])
+        k_sum_jobs<double><<<b->sum_grid[1], 256, 0, s>>>(b->sum[1], b->sum_base[1], b->nsum[1]);
+    return cudaGetLastError();
+}
+
+int bin_boxes_launches(const BinBoxes *b)
+{
+    return (b->nzero ? 1 : 0) + (b->nkeys ? 1 : 0) + (b->njobs ? 1 : 0) + (b->nscat[0] ? 1 : 0) +
+           (b->nscat[1] ? 1 : 0);
+}
+int sum_boxes_launches(const BinBoxes *b) { return (b->nsum[0] ? 1 : 0) + (b->nsum[1] ? 1 : 0); }
+
+void bin_boxes_destroy(BinBoxes *b)
+{
+    if (!b)
+        return;
+    void *ptrs[] = {b->keys, b->scat[0], b->scat[1], b->keys_base, b->scat_base[0], b->scat_base[1], b->zero_base,
+                    b->jobs, b->zero, b->sum[0], b->sum[1], b->sum_base[0], b->sum_base[1]};
+    for (void *q : ptrs)
+        if (q)
+            cudaFree(q);
+    delete b;
+}
+
+// FP64 grids -> FP32 copies for G2P, many boxes (jobs: src FP64, dst FP32, n)
+struct ConvBoxes {
+    EltJob *jobs = nullptr;
+    int *base = nullptr, n = 0;
+    unsigned grid = 0;
+};
+cudaError_t conv_boxes_create(const std::vector<const void *> &src, const std::vector<void *> &dst,
+                              const std::vector<int64_t> &n, ConvBoxes **out)
+{
+    ConvBoxes *b = new (std::nothrow) ConvBoxes;
+    if (!b)
+        return cudaErrorMemoryAllocation;
+    std::vector<EltJob> jobs;
+    for (size_t i = 0; i < src.size(); ++i)
+        jobs.push_back(EltJob{src[i], nullptr, dst[i], n[i]});
+    std::vector<int> base = block_base(n, b->grid);
+    b->n = (int)jobs.size();
+    cudaError_t e = upload(jobs, &b->jobs);
+    if (e == cudaSuccess)
+        e = upload(base, &b->base);
+    if (e != cudaSuccess) {
+        conv_boxes_destroy(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+cudaError_t conv_boxes_launch(const ConvBoxes *b, cudaStream_t s)
+{
+    if (b->n)
+        k_convert_jobs<double, float><<<b->grid, 256, 0, s>>>(b->jobs, b->base, b->n);
+    return cudaGetLastError();
+}
+int conv_boxes_launches(const ConvBoxes *b) { return b && b->n ? 1 : 0; }
+
+void conv_boxes_destroy(ConvBoxes *b)
+{
+    if (!b)
+        return;
+    if (b->jobs)
+        cudaFree(b->jobs);
+    if (b->base)
+        cudaFree(b->base);
+    delete b;
 }
 
 }  // namespace ewg

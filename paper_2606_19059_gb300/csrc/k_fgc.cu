@@ -9,16 +9,18 @@
 // Nyquist plane of even M) and C = 8 pi h^3 / M^3 carrying the h^3 of
 // eq. (g2p) and the 1/M^3 of the inverse FFT.  k = 0 is dropped.  One pass
 // over the three components, read once and written once: HBM bound.
+#include <new>
+#include <vector>
+
 #include "internal.h"
 
 namespace ewg {
 namespace {
 
 template <typename R, typename C2>
-__global__ void __launch_bounds__(256) k_scale(C2 *__restrict__ spec, const R *__restrict__ tab,
-                                               int M, int Mh, int64_t ncplx, R kfac, R inv4xi2, R C)
+__device__ __forceinline__ void scale_elem(C2 *__restrict__ spec, const R *__restrict__ tab, int M, int Mh,
+                                           int64_t ncplx, R kfac, R inv4xi2, R C, int64_t idx)
 {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ncplx)
         return;
     int ix = (int)(idx % Mh);
@@ -47,6 +49,31 @@ __global__ void __launch_bounds__(256) k_scale(C2 *__restrict__ spec, const R *_
     spec[2 * ncplx + idx] = o2;
 }
 
+template <typename R, typename C2>
+__global__ void __launch_bounds__(256) k_scale(C2 *__restrict__ spec, const R *__restrict__ tab,
+                                               int M, int Mh, int64_t ncplx, R kfac, R inv4xi2, R C)
+{
+    scale_elem<R, C2>(spec, tab, M, Mh, ncplx, kfac, inv4xi2, C, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// many boxes' CNV in one launch (a block finds its box by binary search)
+struct ScaleJob {
+    void *spec;
+    const void *tab;
+    int M, Mh;
+    int64_t ncplx;
+    double kfac, inv4xi2, C;
+};
+template <typename R, typename C2>
+__global__ void __launch_bounds__(256) k_scale_jobs(const ScaleJob *__restrict__ jobs, const int *__restrict__ base,
+                                                    int njob)
+{
+    const int b = find_box(base, njob, (int)blockIdx.x);
+    const ScaleJob &j = jobs[b];
+    scale_elem<R, C2>((C2 *)j.spec, (const R *)j.tab, j.M, j.Mh, j.ncplx, (R)j.kfac, (R)j.inv4xi2, (R)j.C,
+                      (int64_t)((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x);
+}
+
 }  // namespace
 
 cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s)
@@ -63,6 +90,83 @@ cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s)
                                                   p->g.Mh, n, (float)kfac, (float)inv4xi2,
                                                   (float)C);
     return cudaGetLastError();
+}
+
+struct ScaleBoxes {
+    ScaleJob *jobs[2] = {nullptr, nullptr};  // [0] FP32 spectra, [1] FP64
+    int *base[2] = {nullptr, nullptr}, n[2] = {0, 0};
+    unsigned grid[2] = {0, 0};
+};
+
+// The CNV of many plans in one launch per precision; spec[i] is plan i's
+// half spectrum (its own or its slice of a grouped FFT's buffer).
+cudaError_t scale_boxes_create(ewald_plan_s *const *plans, void *const *spec, int n, ScaleBoxes **out)
+{
+    ScaleBoxes *b = new (std::nothrow) ScaleBoxes;
+    if (!b)
+        return cudaErrorMemoryAllocation;
+    std::vector<ScaleJob> jobs[2];
+    std::vector<int> base[2] = {std::vector<int>(1, 0), std::vector<int>(1, 0)};
+    for (int i = 0; i < n; ++i) {
+        ewald_plan_s *p = plans[i];
+        const int r = p->fft64 ? 1 : 0;
+        const double h3 = p->g.h * p->g.h * p->g.h;
+        ScaleJob j;
+        j.spec = spec[i];
+        j.tab = p->tab;
+        j.M = p->g.M;
+        j.Mh = p->g.Mh;
+        j.ncplx = p->g.ncplx;
+        j.kfac = 2.0 * 3.14159265358979323846 / p->prm.L;
+        j.inv4xi2 = 1.0 / (4.0 * p->prm.xi * p->prm.xi);
+        j.C = 8.0 * 3.14159265358979323846 * h3 / (double)p->g.nreal;  // as the plan's own CNV
+        jobs[r].push_back(j);
+        base[r].push_back(base[r].back() + (int)((j.ncplx + 255) / 256));
+    }
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        b->n[r] = (int)jobs[r].size();
+        b->grid[r] = (unsigned)base[r].back();
+        if (!b->n[r])
+            continue;
+        e = cudaMalloc(&b->jobs[r], sizeof(ScaleJob) * jobs[r].size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->jobs[r], jobs[r].data(), sizeof(ScaleJob) * jobs[r].size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&b->base[r], sizeof(int) * base[r].size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->base[r], base[r].data(), sizeof(int) * base[r].size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        scale_boxes_destroy(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+cudaError_t scale_boxes_launch(const ScaleBoxes *b, cudaStream_t s, int fft64)
+{
+    if (!fft64 && b->n[0])
+        k_scale_jobs<float, float2><<<b->grid[0], 256, 0, s>>>(b->jobs[0], b->base[0], b->n[0]);
+    if (fft64 && b->n[1])
+        k_scale_jobs<double, double2><<<b->grid[1], 256, 0, s>>>(b->jobs[1], b->base[1], b->n[1]);
+    return cudaGetLastError();
+}
+
+int scale_boxes_launches(const ScaleBoxes *b) { return (b->n[0] ? 1 : 0) + (b->n[1] ? 1 : 0); }
+
+void scale_boxes_destroy(ScaleBoxes *b)
+{
+    if (!b)
+        return;
+    for (int r = 0; r < 2; ++r) {
+        if (b->jobs[r])
+            cudaFree(b->jobs[r]);
+        if (b->base[r])
+            cudaFree(b->base[r]);
+    }
+    delete b;
 }
 
 }  // namespace ewg

@@ -27,7 +27,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <new>
 #include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -72,7 +76,7 @@ __device__ __forceinline__ int wrapi(int i, int n)
 // thread -- every bin shares z = 2 delta - 1, so the coefficient loads are
 // warp-uniform broadcasts and the P Horner chains run side by side.
 template <int T, typename R, typename G, int PC>
-__global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(GridArgs a)
+__device__ __forceinline__ void p2g_body(const GridArgs &a, const int tile)
 {
     using R4 = typename Vec4<R>::T;
     constexpr int NT = kP2GThreads;
@@ -99,7 +103,6 @@ __global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(Gri
 
     const int nt = a.nt, P = PC > 0 ? PC : a.P, nd = a.deg + 1, KT = a.KT;
     const int side = KT + 1, nseg = side * side * side;
-    const int tile = blockIdx.x;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     if constexpr (PC > 0) {
         for (int i = threadIdx.x; i < nd * PS; i += NT) {
@@ -388,10 +391,9 @@ constexpr int kMaxRounds = (kMaxP * kMaxP + 31) / 32;
 // PC > 0 fixes P at compile time (every offset into the staged block becomes
 // an immediate and the loops unroll); PC = 0 reads P at run time.
 template <int T, typename R, int PC>
-__global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
+__device__ __forceinline__ void g2p_body(const GridArgs &a, const int tile)
 {
     using R4 = typename Vec4<R>::T;
-    const int tile = blockIdx.x;
     const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
     if (s0 == s1)
         return;
@@ -592,14 +594,13 @@ __device__ __forceinline__ void column_sum(unsigned a, const float *wz, float (&
 }
 
 template <int PC>
-__global__ void __launch_bounds__(kG2PPlanarThreads, 2)
-    k_g2p_planar(GridArgs a, const __grid_constant__ CUtensorMap tmap, int use_tma, int *err)
+__device__ __forceinline__ void g2p_planar_body(const GridArgs &a, const int tile, const CUtensorMap *tm,
+                                                int use_tma, int *err)
 {
     using G = G2PPlanar<PC>;
     constexpr int T = G::T, RR = G::RR, S = G::S, NR = G::NR, NCH = G::NCH, PS = G::PS;
     constexpr int PLANE = RR * S, VOL = RR * PLANE;
     constexpr int NIT = (RR * NCH + 31) / 32;  // staging: lane iterations per plane
-    const int tile = blockIdx.x;
     const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
     if (s0 == s1)
         return;
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kG2PPlanarThreads, 2)
             asm volatile(
                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(vs_a),
-                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(tx * T), "r"(ty * T), "r"(tz * T), "r"(0),
+                "l"(reinterpret_cast<uint64_t>(tm)), "r"(tx * T), "r"(ty * T), "r"(tz * T), "r"(0),
                 "r"(bar_a)
                 : "memory");
         }
@@ -778,10 +779,9 @@ __global__ void __launch_bounds__(kG2PPlanarThreads, 2)
 constexpr int kG2PDirectThreads = 256;
 
 template <int T, int PC>
-__global__ void __launch_bounds__(kG2PDirectThreads, 2) k_g2p_direct64(GridArgs a)
+__device__ __forceinline__ void g2p_direct64_body(const GridArgs &a, const int tile)
 {
     constexpr int NW = kG2PDirectThreads / 32, NR = (PC * PC + 31) / 32;
-    const int tile = blockIdx.x;
     const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
     if (s0 == s1)
         return;
@@ -857,6 +857,67 @@ __global__ void __launch_bounds__(kG2PDirectThreads, 2) k_g2p_direct64(GridArgs 
             uf[3 * i + 2] = u2 * a.scale;
         }
     }
+}
+
+// ---- kernels: one plan (the tile is the block index), or many plans'
+// boxes in one launch (a block finds its box by binary search over the
+// boxes' block offsets and runs the same body on that box's arguments) ----
+struct GridBox {
+    GridArgs a;
+    const CUtensorMap *tm;  // G2P's TMA descriptor of the box's grid (global memory)
+    int use_tma;
+    int *err;
+};
+
+template <int T, typename R, typename G, int PC>
+__global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1) k_p2g(GridArgs a)
+{
+    p2g_body<T, R, G, PC>(a, blockIdx.x);
+}
+template <int T, typename R, typename G, int PC>
+__global__ void __launch_bounds__(kP2GThreads, sizeof(R) == 4 ? 3 : 1)
+    k_p2g_boxes(const GridBox *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    p2g_body<T, R, G, PC>(boxes[b].a, (int)blockIdx.x - base[b]);
+}
+template <int T, typename R, int PC>
+__global__ void __launch_bounds__(kG2PThreads) k_g2p(GridArgs a)
+{
+    g2p_body<T, R, PC>(a, blockIdx.x);
+}
+template <int T, typename R, int PC>
+__global__ void __launch_bounds__(kG2PThreads)
+    k_g2p_boxes(const GridBox *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    g2p_body<T, R, PC>(boxes[b].a, (int)blockIdx.x - base[b]);
+}
+template <int PC>
+__global__ void __launch_bounds__(kG2PPlanarThreads, 2)
+    k_g2p_planar(GridArgs a, const __grid_constant__ CUtensorMap tmap, int use_tma, int *err)
+{
+    g2p_planar_body<PC>(a, blockIdx.x, &tmap, use_tma, err);
+}
+template <int PC>
+__global__ void __launch_bounds__(kG2PPlanarThreads, 2)
+    k_g2p_planar_boxes(const GridBox *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    const GridBox &x = boxes[b];
+    g2p_planar_body<PC>(x.a, (int)blockIdx.x - base[b], x.tm, x.use_tma, x.err);
+}
+template <int T, int PC>
+__global__ void __launch_bounds__(kG2PDirectThreads, 2) k_g2p_direct64(GridArgs a)
+{
+    g2p_direct64_body<T, PC>(a, blockIdx.x);
+}
+template <int T, int PC>
+__global__ void __launch_bounds__(kG2PDirectThreads, 2)
+    k_g2p_direct64_boxes(const GridBox *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    g2p_direct64_body<T, PC>(boxes[b].a, (int)blockIdx.x - base[b]);
 }
 
 template <int T, int PC>
@@ -1059,6 +1120,232 @@ cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStre
     if (p->near64)
         return p->g.T == 8 ? run_g2p_direct64<8, 2>(a, s) : run_g2p_direct64<4, 2>(a, s);
     return p->g.T == 8 ? run_g2p_f32_fixed<2>(a, p->err, s) : run_g2p<4, float, 0>(a, s);
+}
+
+// ---- the grid stages of many plans, one launch per kernel variant -------
+namespace {
+
+// one launch: boxes of one kernel instantiation
+struct GridGroup {
+    int kind;       // 0 P2G, 1 G2P
+    int fft64;      // the boxes' FFT precision (launches are issued per FFT precision)
+    int prec;       // P2G: 0 (FP32, FP32 grid), 1 (FP32, FP64 grid), 2 (FP64); G2P: 0 FP32, 2 FP64
+    int T, P, deg;  // tile, support, largest window degree of the group's boxes
+    GridBox *boxes = nullptr;
+    int *base = nullptr;
+    int n = 0;
+    unsigned grid = 0;
+};
+
+template <int T, typename R, int PC>
+size_t p2g_smem(int P, int deg)
+{
+    constexpr int B = kP2GThreads * kP2GCandidates;
+    const size_t ncoef = PC > 0 ? (size_t)(deg + 1) * ((PC + 3) & ~3) : (size_t)P * (deg + 1);
+    const size_t stage = sizeof(R) * ((size_t)B * (3 * T + 7) + ncoef);
+    const size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * T;
+    return stage > red ? stage : red;
+}
+
+template <int T, typename R, typename G, int PC>
+cudaError_t p2g_group(const GridGroup &g, cudaStream_t s)
+{
+    const size_t sm = p2g_smem<T, R, PC>(g.P, g.deg);
+    cudaError_t e = cudaFuncSetAttribute(k_p2g_boxes<T, R, G, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess)
+        return e;
+    k_p2g_boxes<T, R, G, PC><<<g.grid, kP2GThreads, sm, s>>>(g.boxes, g.base, g.n);
+    return cudaGetLastError();
+}
+template <typename R, typename G, int PC>
+cudaError_t p2g_group_fixed(const GridGroup &g, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return p2g_group<8, R, G, 0>(g, s);
+    } else {
+        if (g.P == PC)
+            return p2g_group<8, R, G, PC>(g, s);
+        return p2g_group_fixed<R, G, PC + 1>(g, s);
+    }
+}
+template <int T, typename R, int PC>
+cudaError_t g2p_group_generic(const GridGroup &g, cudaStream_t s)
+{
+    using R4 = typename Vec4<R>::T;
+    const int RR = T + g.P - 1;
+    const size_t sm = sizeof(R4) * (size_t)RR * RR * RR +
+                      sizeof(R) * ((size_t)g.P * (g.deg + 1) + (size_t)(kG2PThreads / 32) * 3 * kMaxP) +
+                      sizeof(int) * kMaxRounds * 32;
+    cudaError_t e = cudaFuncSetAttribute(k_g2p_boxes<T, R, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess)
+        return e;
+    k_g2p_boxes<T, R, PC><<<g.grid, kG2PThreads, sm, s>>>(g.boxes, g.base, g.n);
+    return cudaGetLastError();
+}
+template <int PC>
+cudaError_t g2p_group_planar(const GridGroup &g, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return g2p_group_generic<8, float, 0>(g, s);
+    } else {
+        if (g.P != PC)
+            return g2p_group_planar<PC + 1>(g, s);
+        const size_t sm = G2PPlanar<PC>::smem(g.deg);
+        cudaError_t e = cudaFuncSetAttribute(k_g2p_planar_boxes<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess)
+            return e;
+        k_g2p_planar_boxes<PC><<<g.grid, kG2PPlanarThreads, sm, s>>>(g.boxes, g.base, g.n);
+        return cudaGetLastError();
+    }
+}
+template <int T, int PC>
+cudaError_t g2p_group_direct64(const GridGroup &g, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (g.P != PC)
+            return g2p_group_direct64<T, PC + 1>(g, s);
+        const size_t sm = sizeof(double) * ((size_t)PC * (g.deg + 1) + (kG2PDirectThreads / 32) * 3 * PC);
+        k_g2p_direct64_boxes<T, PC><<<g.grid, kG2PDirectThreads, sm, s>>>(g.boxes, g.base, g.n);
+        return cudaGetLastError();
+    }
+}
+
+cudaError_t launch_group(const GridGroup &g, cudaStream_t s)
+{
+    if (g.kind == 0) {  // P2G
+        if (g.T == 8) {
+            if (g.prec == 2)
+                return p2g_group<8, double, double, 0>(g, s);
+            return g.prec == 1 ? p2g_group_fixed<float, double, 2>(g, s) : p2g_group_fixed<float, float, 2>(g, s);
+        }
+        if (g.prec == 2)
+            return p2g_group<4, double, double, 0>(g, s);
+        return g.prec == 1 ? p2g_group<4, float, double, 0>(g, s) : p2g_group<4, float, float, 0>(g, s);
+    }
+    if (g.prec == 2)  // FP64 G2P from the grid in L2
+        return g.T == 8 ? g2p_group_direct64<8, 2>(g, s) : g2p_group_direct64<4, 2>(g, s);
+    return g.T == 8 ? g2p_group_planar<2>(g, s) : g2p_group_generic<4, float, 0>(g, s);
+}
+
+}  // namespace
+
+struct GridBoxes {
+    std::vector<GridGroup> groups;  // P2G groups first, then G2P groups
+    int np2g = 0;
+    CUtensorMap *maps = nullptr;    // G2P TMA descriptors, one per box (device)
+};
+
+// grid[i]: box i's P2G output (FP32 or FP64 as its plan's FFT); g2p[i]: its
+// G2P input (FP32 for FP32 kernels, FP64 for FP64 ones).  Plans with
+// double-single grid kernels are left to ds_grid_boxes_create.
+cudaError_t grid_boxes_create(ewald_plan_s *const *plans, void *const *grid, void *const *g2p, int n, GridBoxes **out)
+{
+    GridBoxes *b = new (std::nothrow) GridBoxes;
+    if (!b)
+        return cudaErrorMemoryAllocation;
+    struct Key {
+        int kind, prec, T, P, fft64;
+        bool operator<(const Key &o) const
+        {
+            return std::make_pair(std::make_pair(std::make_pair(kind, prec), std::make_pair(T, P)), fft64) <
+                   std::make_pair(std::make_pair(std::make_pair(o.kind, o.prec), std::make_pair(o.T, o.P)), o.fft64);
+        }
+    };
+    std::map<Key, std::vector<int>> members;
+    std::vector<CUtensorMap> maps(n);
+    std::vector<int> use(n, 0);
+    for (int i = 0; i < n; ++i) {
+        ewald_plan_s *p = plans[i];
+        if (p->grid_ds)
+            continue;
+        const int prec = p->near64 ? 2 : (p->fft64 ? 1 : 0), f64 = p->fft64 ? 1 : 0;
+        members[Key{0, prec, p->g.T, p->g.P, f64}].push_back(i);
+        members[Key{1, p->near64 ? 2 : 0, p->g.T, p->g.P, f64}].push_back(i);
+        memset(&maps[i], 0, sizeof(CUtensorMap));
+        if (!p->near64 && p->g.T == 8 && p->g.P <= kMaxP)
+            use[i] = grid_tensor_map(g2p[i], p->g.M, 3, g2p_stride(p->g.P), 8 + p->g.P - 1, 3, &maps[i]) ? 1 : 0;
+    }
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMalloc(&b->maps, sizeof(CUtensorMap) * n);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice);
+    }
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass)
+        for (auto &kv : members) {
+            if (kv.first.kind != pass)
+                continue;
+            GridGroup g;
+            g.kind = kv.first.kind;
+            g.prec = kv.first.prec;
+            g.T = kv.first.T;
+            g.P = kv.first.P;
+            g.fft64 = kv.first.fft64;
+            g.deg = 0;
+            std::vector<GridBox> hb;
+            std::vector<int> base(1, 0);
+            for (int i : kv.second) {
+                ewald_plan_s *p = plans[i];
+                GridBox x;
+                x.a = grid_args(p);
+                x.a.grid = pass == 0 ? grid[i] : g2p[i];
+                x.a.scale = 1.0;
+                x.tm = b->maps + i;
+                x.use_tma = use[i];
+                x.err = p->err;
+                hb.push_back(x);
+                base.push_back(base.back() + p->g.ntiles);
+                g.deg = std::max(g.deg, p->wpoly.deg);
+            }
+            g.n = (int)hb.size();
+            g.grid = (unsigned)base.back();
+            e = cudaMalloc(&g.boxes, sizeof(GridBox) * hb.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(g.boxes, hb.data(), sizeof(GridBox) * hb.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMalloc(&g.base, sizeof(int) * base.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(g.base, base.data(), sizeof(int) * base.size(), cudaMemcpyHostToDevice);
+            b->groups.push_back(g);
+            if (pass == 0)
+                b->np2g++;
+        }
+    if (e != cudaSuccess) {
+        grid_boxes_destroy(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+cudaError_t grid_boxes_launch(const GridBoxes *b, int kind, cudaStream_t s, int fft64)
+{
+    for (const GridGroup &g : b->groups)
+        if (g.kind == kind && g.fft64 == fft64) {
+            const cudaError_t e = launch_group(g, s);
+            if (e != cudaSuccess)
+                return e;
+        }
+    return cudaSuccess;
+}
+
+int grid_boxes_launches(const GridBoxes *b) { return (int)b->groups.size(); }
+
+void grid_boxes_destroy(GridBoxes *b)
+{
+    if (!b)
+        return;
+    for (GridGroup &g : b->groups) {
+        if (g.boxes)
+            cudaFree(g.boxes);
+        if (g.base)
+            cudaFree(g.base);
+    }
+    if (b->maps)
+        cudaFree(b->maps);
+    delete b;
 }
 
 }  // namespace ewg

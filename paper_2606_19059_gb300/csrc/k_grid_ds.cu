@@ -27,6 +27,10 @@
 #include <cuda.h>  // CUtensorMap (the type; descriptors are encoded by k_grid.cu's helper)
 #include <string.h>
 
+#include <map>
+#include <new>
+#include <vector>
+
 #include "internal.h"
 
 namespace ewg {
@@ -107,10 +111,10 @@ struct GridDsArgs {
 };
 
 // ---- window weights ---------------------------------------------------------
-__global__ void k_window_ds(const dvec4 *__restrict__ tdat, const double *__restrict__ coef,
-                            float *__restrict__ wts, int64_t N, int P, int deg, int PW)
+__device__ __forceinline__ void window_ds_body(const dvec4 *__restrict__ tdat, const double *__restrict__ coef,
+                                               float *__restrict__ wts, int64_t N, int P, int deg, int PW,
+                                               int64_t q)  // (point, axis)
 {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (point, axis)
     if (q >= 3 * N)
         return;
     const int64_t p = q / 3;
@@ -133,6 +137,45 @@ __global__ void k_window_ds(const dvec4 *__restrict__ tdat, const double *__rest
     }
 }
 
+__global__ void k_window_ds(const dvec4 *__restrict__ tdat, const double *__restrict__ coef,
+                            float *__restrict__ wts, int64_t N, int P, int deg, int PW)
+{
+    window_ds_body(tdat, coef, wts, N, P, deg, PW, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// many boxes' window weights and double-single grid copies in one launch each
+struct WindowJob {
+    const dvec4 *tdat;
+    const double *coef;
+    float *wts;
+    int64_t N;
+    int P, deg, PW;
+};
+__global__ void k_window_ds_jobs(const WindowJob *__restrict__ jobs, const int *__restrict__ base, int njob)
+{
+    const int b = find_box(base, njob, (int)blockIdx.x);
+    const WindowJob &j = jobs[b];
+    window_ds_body(j.tdat, j.coef, j.wts, j.N, j.P, j.deg, j.PW,
+                   (int64_t)((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x);
+}
+struct SplitJob {
+    const double *src;
+    float *dst;
+    int64_t n;
+};
+__global__ void k_grid_split_jobs(const SplitJob *__restrict__ jobs, const int *__restrict__ base, int njob)
+{
+    const int b = find_box(base, njob, (int)blockIdx.x);
+    const SplitJob &j = jobs[b];
+    const int64_t i = (int64_t)((int)blockIdx.x - base[b]) * blockDim.x + threadIdx.x;
+    if (i >= j.n)
+        return;
+    float h, l;
+    ds_split(j.src[i], h, l);
+    j.dst[i] = h;
+    j.dst[j.n + i] = l;
+}
+
 // ---- P2G --------------------------------------------------------------------
 constexpr int kT = 8, kH = 4;
 constexpr int kP2GDsThreads = 256;
@@ -147,7 +190,7 @@ __device__ __forceinline__ int wrapi(int i, int n)
 }
 
 template <int PC>
-__global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
+__device__ __forceinline__ void p2g_ds_body(const GridDsArgs &a, const int tile)
 {
     constexpr int NT = kP2GDsThreads, B = NT, T = kT, H = kH, SL = kDsSlices, T3 = T * T * T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -158,7 +201,6 @@ __global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
     __shared__ int scount;
 
     const int nt = a.nt, KT = a.KT, side = KT + 1, nseg = side * side * side;
-    const int tile = blockIdx.x;
     const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
     // the neighbour tiles (dz, dy, dx) in [-KT, 0]^3 whose anchors can reach
     // this tile: their point ranges, concatenated
@@ -351,13 +393,12 @@ struct G2PDs {
 };
 
 template <int PC>
-__global__ void __launch_bounds__(kG2PDsThreads, 2)
-    k_g2p_ds(GridDsArgs a, const __grid_constant__ CUtensorMap tmap, int use_tma, int *err)
+__device__ __forceinline__ void g2p_ds_body(const GridDsArgs &a, const int tile, const CUtensorMap *tm,
+                                            int use_tma, int *err)
 {
     using G = G2PDs<PC>;
     constexpr int T = G::T, RR = G::RR, S = G::S, NR = G::NR, NCH = G::NCH, PLANE = G::PLANE,
                   VOLP = G::VOLP, NW = G::NW;
-    const int tile = blockIdx.x;
     const int s0 = a.startt[tile], s1 = a.startt[tile + 1];
     if (s0 == s1)
         return;
@@ -408,7 +449,7 @@ __global__ void __launch_bounds__(kG2PDsThreads, 2)
                 for (int half = 0; half < 2; ++half)
                     asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                                  " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(vh_a + 4 * half * VOLP),
-                                 "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(tx * T), "r"(ty * T), "r"(tz * T),
+                                 "l"(reinterpret_cast<uint64_t>(tm)), "r"(tx * T), "r"(ty * T), "r"(tz * T),
                                  "r"(c + 3 * half), "r"(bar_a)
                                  : "memory");
             }
@@ -506,6 +547,41 @@ __global__ void __launch_bounds__(kG2PDsThreads, 2)
         }
         __syncthreads();  // before the next component overwrites the block
     }
+}
+
+// ---- kernels: one plan, or many plans' boxes in one launch (as k_grid.cu) ----
+struct GridDsBox {
+    GridDsArgs a;
+    const CUtensorMap *tm;  // G2P's TMA descriptor of the box's double-single grid
+    int use_tma;
+    int *err;
+};
+
+template <int PC>
+__global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
+{
+    p2g_ds_body<PC>(a, blockIdx.x);
+}
+template <int PC>
+__global__ void __launch_bounds__(kP2GDsThreads, 2)
+    k_p2g_ds_boxes(const GridDsBox *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    p2g_ds_body<PC>(boxes[b].a, (int)blockIdx.x - base[b]);
+}
+template <int PC>
+__global__ void __launch_bounds__(kG2PDsThreads, 2)
+    k_g2p_ds(GridDsArgs a, const __grid_constant__ CUtensorMap tmap, int use_tma, int *err)
+{
+    g2p_ds_body<PC>(a, blockIdx.x, &tmap, use_tma, err);
+}
+template <int PC>
+__global__ void __launch_bounds__(kG2PDsThreads, 2)
+    k_g2p_ds_boxes(const GridDsBox *__restrict__ boxes, const int *__restrict__ base, int nbox)
+{
+    const int b = find_box(base, nbox, (int)blockIdx.x);
+    const GridDsBox &x = boxes[b];
+    g2p_ds_body<PC>(x.a, (int)blockIdx.x - base[b], x.tm, x.use_tma, x.err);
 }
 
 // FP64 grid -> double-single planes (all h values, then all l values)
@@ -628,6 +704,175 @@ cudaError_t launch_grid_split(const double *src, float *dst, int64_t n, cudaStre
         return cudaSuccess;
     k_grid_split<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, n);
     return cudaGetLastError();
+}
+
+// ---- the double-single grid stages of many plans -----------------------------
+namespace {
+template <typename T>
+cudaError_t upload_ds(const std::vector<T> &v, T **d)
+{
+    *d = nullptr;
+    if (v.empty())
+        return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)d, sizeof(T) * v.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+struct DsGroup {
+    int kind, P;  // 0 P2G, 1 G2P
+    GridDsBox *boxes = nullptr;
+    int *base = nullptr, n = 0;
+    unsigned grid = 0;
+};
+template <int PC>
+cudaError_t ds_group_launch(const DsGroup &g, cudaStream_t s)
+{
+    if constexpr (PC > kMaxP) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (g.P != PC)
+            return ds_group_launch<PC + 1>(g, s);
+        if (g.kind == 0) {
+            cudaError_t e = cudaFuncSetAttribute(k_p2g_ds_boxes<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kP2GDsSmem);
+            if (e != cudaSuccess)
+                return e;
+            k_p2g_ds_boxes<PC><<<g.grid, kP2GDsThreads, kP2GDsSmem, s>>>(g.boxes, g.base, g.n);
+        } else {
+            constexpr size_t sm = G2PDs<PC>::smem;
+            cudaError_t e = cudaFuncSetAttribute(k_g2p_ds_boxes<PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess)
+                return e;
+            k_g2p_ds_boxes<PC><<<g.grid, kG2PDsThreads, sm, s>>>(g.boxes, g.base, g.n);
+        }
+        return cudaGetLastError();
+    }
+}
+}  // namespace
+
+struct DsGridBoxes {
+    WindowJob *win = nullptr;
+    int *win_base = nullptr, nwin = 0;
+    unsigned win_grid = 0;
+    SplitJob *split = nullptr;
+    int *split_base = nullptr, nsplit = 0;
+    unsigned split_grid = 0;
+    std::vector<DsGroup> groups;
+    CUtensorMap *maps = nullptr;
+};
+
+// The double-single plans among `plans`: grid[i] is box i's FP64 P2G output
+// (its FFT input), gds[i] its double-single G2P copy.
+cudaError_t ds_grid_boxes_create(ewald_plan_s *const *plans, double *const *grid, float *const *gds, int n,
+                                 DsGridBoxes **out)
+{
+    DsGridBoxes *b = new (std::nothrow) DsGridBoxes;
+    if (!b)
+        return cudaErrorMemoryAllocation;
+    std::vector<WindowJob> win;
+    std::vector<SplitJob> split;
+    std::vector<int> wb(1, 0), sb(1, 0);
+    std::map<std::pair<int, int>, std::vector<int>> members;
+    std::vector<CUtensorMap> maps(n);
+    std::vector<int> use(n, 0);
+    for (int i = 0; i < n; ++i) {
+        ewald_plan_s *p = plans[i];
+        if (!p->grid_ds)
+            continue;
+        win.push_back(WindowJob{(const dvec4 *)p->tdat, (const double *)p->wcoef_dev, (float *)p->wts, p->N, p->g.P,
+                                p->wpoly.deg, ds_window_stride(p->g.P)});
+        wb.push_back(wb.back() + (int)blocks_for(3 * p->N, 256));
+        split.push_back(SplitJob{grid[i], gds[i], 3 * p->g.nreal});
+        sb.push_back(sb.back() + (int)blocks_for(3 * p->g.nreal, 256));
+        members[{0, p->g.P}].push_back(i);
+        members[{1, p->g.P}].push_back(i);
+        memset(&maps[i], 0, sizeof(CUtensorMap));
+        use[i] = grid_tensor_map(gds[i], p->g.M, 6, g2p_stride(p->g.P), kT + p->g.P - 1, 1, &maps[i]) ? 1 : 0;
+    }
+    b->nwin = (int)win.size();
+    b->nsplit = (int)split.size();
+    b->win_grid = (unsigned)wb.back();
+    b->split_grid = (unsigned)sb.back();
+    cudaError_t e = upload_ds(win, &b->win);
+    if (e == cudaSuccess) e = upload_ds(wb, &b->win_base);
+    if (e == cudaSuccess) e = upload_ds(split, &b->split);
+    if (e == cudaSuccess) e = upload_ds(sb, &b->split_base);
+    if (e == cudaSuccess) e = upload_ds(maps, &b->maps);
+    for (auto &kv : members) {
+        if (e != cudaSuccess)
+            break;
+        DsGroup g;
+        g.kind = kv.first.first;
+        g.P = kv.first.second;
+        std::vector<GridDsBox> hb;
+        std::vector<int> base(1, 0);
+        for (int i : kv.second) {
+            ewald_plan_s *p = plans[i];
+            GridDsBox x;
+            x.a = ds_args(p);
+            x.a.grid = grid[i];
+            x.a.gds = gds[i];
+            x.a.scale = 1.0;
+            x.tm = b->maps + i;
+            x.use_tma = use[i];
+            x.err = p->err;
+            hb.push_back(x);
+            base.push_back(base.back() + p->g.ntiles);
+        }
+        g.n = (int)hb.size();
+        g.grid = (unsigned)base.back();
+        e = upload_ds(hb, &g.boxes);
+        if (e == cudaSuccess)
+            e = upload_ds(base, &g.base);
+        b->groups.push_back(g);
+    }
+    if (e != cudaSuccess) {
+        ds_grid_boxes_destroy(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+// stage 0: window weights (after binning); 1: P2G; 2: the double-single copy
+// of the grids (after the inverse FFT); 3: G2P
+cudaError_t ds_grid_boxes_launch(const DsGridBoxes *b, int stage, cudaStream_t s)
+{
+    if (stage == 0 && b->nwin)
+        k_window_ds_jobs<<<b->win_grid, 256, 0, s>>>(b->win, b->win_base, b->nwin);
+    if (stage == 2 && b->nsplit)
+        k_grid_split_jobs<<<b->split_grid, 256, 0, s>>>(b->split, b->split_base, b->nsplit);
+    if (stage == 1 || stage == 3)
+        for (const DsGroup &g : b->groups)
+            if (g.kind == (stage == 1 ? 0 : 1)) {
+                const cudaError_t e = ds_group_launch<kGridDsMinP>(g, s);
+                if (e != cudaSuccess)
+                    return e;
+            }
+    return cudaGetLastError();
+}
+
+int ds_grid_boxes_launches(const DsGridBoxes *b)
+{
+    return (b->nwin ? 1 : 0) + (b->nsplit ? 1 : 0) + (int)b->groups.size();
+}
+
+void ds_grid_boxes_destroy(DsGridBoxes *b)
+{
+    if (!b)
+        return;
+    void *ptrs[] = {b->win, b->win_base, b->split, b->split_base, b->maps};
+    for (void *q : ptrs)
+        if (q)
+            cudaFree(q);
+    for (DsGroup &g : b->groups) {
+        if (g.boxes)
+            cudaFree(g.boxes);
+        if (g.base)
+            cudaFree(g.base);
+    }
+    delete b;
 }
 
 }  // namespace ewg

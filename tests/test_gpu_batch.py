@@ -116,13 +116,15 @@ def test_autotune_picks_a_candidate_and_caches():
     assert (q2.M, q2.tile, ms2) == (q.M, q.tile, ms)
 
 
-def test_batch_near_field_is_one_launch_per_variant(batch):
+def test_batch_is_one_launch_per_stage_and_variant(batch):
+    # every stage of every box in one launch per kernel instantiation, the FFTs
+    # of the boxes that share a grid size and precision in one batched plan
     b, N, tol, data = batch
     k, f = b.launch_counts()
-    per_box = [ewald.ewald_launch_counts(_plan(b, i)) for i in range(len(N))]
-    variants = {(b.params(i).near_ds, b.params(i).near_f64, b.params(i).tol < 1e-6) for i in range(len(N))}
-    assert f == sum(pf for _, pf in per_box)
-    assert k == sum(pk - 1 for pk, _ in per_box) + len(variants)
+    groups = {(b.params(i).M, b.params(i).fft_f64) for i in range(len(N))}
+    assert f == 2 * len(groups)
+    per_box = sum(ewald.ewald_launch_counts(_plan(b, i))[0] for i in range(len(N)))
+    assert k <= 40 and k < per_box, (k, per_box)
 
 
 def _plan(b, i):

@@ -418,13 +418,65 @@ def run_batch(args, rank):
     kern = b.launch_counts()[0]
     b.close()
     ms_med = float(np.median(ms))
+    per_tol = [_batch_class(seed, N, tol, t, stream) for t in sorted(set(tol.tolist()), reverse=True)]
     return {"boxes": int(len(N)), "particles": int(N.sum()), "ms_per_step": ms_med,
             "value": float(N.sum()) / (ms_med * 1e-3), "unit": UNIT,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "steps": steps, "tune_and_plan_s": t_create, "distinct_tuned_grids": len(tuned),
-            "kernels_per_step": int(kern), "graph_launches_per_step": 1,
+            "kernels_per_step": int(kern), "graph_launches_per_step": 1, "per_tol": per_tol,
             "workload": "512 boxes, N = round(10^U(3,5)), tol uniform in {1e-4, 1e-6, 1e-8}, uniform points, "
                         "FP32 bulk, autotuned (measured) per half-octave of N; inputs larger than L2"}
+
+
+def _batch_class(seed, N, tol, t, stream):
+    """The boxes of one tolerance class of the batch: as a batch of their own
+    (one graph launch a step) and as one plan per box applied one after the
+    other on the same stream (the single-apply form), with the same tuned
+    parameters (the autotuner's cache from the full batch)."""
+    import torch
+
+    from paper_2606_19059_gb300 import ewald, workloads
+
+    idx = np.flatnonzero(tol == t)
+    sb = ewald.Batch(N[idx], 1.0, tol[idx], ewald.EWALD_F32_BULK, tune=ewald.EWALD_TUNE_MEASURE)
+    for j, i in enumerate(idx):
+        x, f = workloads.batch_box(seed, int(i), int(N[i]))
+        bx, bf, _ = sb.buffers(j)
+        bx.copy_(torch.as_tensor(x, device=bx.device))
+        bf.copy_(torch.as_tensor(f, device=bf.device))
+
+    def timed(run, reps=3):
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, e in evs:
+            a.record(stream)
+            run()
+            e.record(stream)
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(e) for a, e in evs]))
+
+    bms = timed(lambda: sb.apply(stream))
+    plans, io = [], []
+    for j in range(len(idx)):
+        q = sb.params(j)
+        plans.append(ewald.Plan(int(N[idx[j]]), 1.0, t, ewald.EWALD_F32_BULK, M=q.M, P=q.P, tile=q.tile))
+        bx, bf, _ = sb.buffers(j)
+        io.append((bx, bf, torch.empty_like(bx)))
+
+    def singles():
+        for p, (bx, bf, u) in zip(plans, io):
+            p.apply(bx, bf, out=u, stream=stream)
+
+    sms = timed(singles)
+    for p in plans:
+        p.close()
+    sb.close()
+    n = float(N[idx].sum())
+    return {"tol": t, "boxes": int(len(idx)), "particles": int(n), "batched_ms": bms,
+            "batched_value": n / (bms * 1e-3), "single_apply_ms": sms, "single_apply_value": n / (sms * 1e-3),
+            "unit": UNIT}
 
 
 def run_serving(args, rank, rate_hz):
@@ -587,7 +639,7 @@ def main():
             r = run_batch(args, rank)
             if rank == 0:
                 print(json.dumps({"only_batch": True, "ms_per_step": r["ms_per_step"],
-                                  "kernels_per_step": r["kernels_per_step"]}))
+                                  "kernels_per_step": r["kernels_per_step"], "per_tol": r["per_tol"]}))
             return
         res = run_gpu(args, rank, world)
         if res is None:

@@ -424,6 +424,9 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
     // a small double-single P2P launch is latency-bound and the far field
     // submitted before it stretched it (tol 1e-8, N = 1e4: 0.66 -> 1.47 ms).
     const bool far_first = overlap && !p->near_ds && !p->near64;
+    // FP32 plans with FP32 FFTs: the double layer's near field in FP32 pairs
+    // on the Stokeslet P2P machinery, on the near-field branch
+    const bool dl32 = dl && !p->fft64 && !p->near64;
     if (overlap)  // binning done: both branches may start (P2P waits on this)
         EW_CUDA(cudaEventRecord(p->ev_fork, s));
     // P2G of the Stokeslet forces, then of the double layer's six densities
@@ -453,6 +456,12 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         rec(p, 7, sn);
         EW_CUDA(launch_p2p(p, sn));
         rec(p, 8, sn);
+        // the double layer's FP32 near field on the same branch, added into
+        // the near result before the sum reads it
+        if (dl && mode == FULL && dl32) {
+            EW_CUDA(launch_dl_records(p, dl->q, dl->n, p->dl_near, sn));
+            EW_CUDA(launch_p2p_dl32(p, p->dl_near, sn));
+        }
         if (overlap)
             EW_CUDA(cudaEventRecord(p->ev_join, p->s2));
     }
@@ -471,14 +480,8 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         EW_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     if (mode == FULL) {
         EW_CUDA(launch_sum(p, f, u, s));
-        if (dl) {  // the double layer's near field, added to u
-            if (!p->fft64 && !p->near64) {  // FP32 pairs on the Stokeslet P2P machinery
-                EW_CUDA(launch_dl_records(p, dl->q, dl->n, p->dl_near, s));
-                EW_CUDA(launch_p2p_dl32(p, p->dl_near, u, s));
-            } else {
-                EW_CUDA(launch_p2p_dl(p, dl->x, dl->q, dl->n, u, s));
-            }
-        }
+        if (dl && !dl32)  // the double layer's FP64 near field, added to u
+            EW_CUDA(launch_p2p_dl(p, dl->x, dl->q, dl->n, u, s));
     } else if (mode == NEAR_ONLY) {
         EW_CUDA(launch_copy_out(p->un, p->near64, u, 3 * p->N, s));
     } else {

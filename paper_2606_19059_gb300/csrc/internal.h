@@ -243,7 +243,8 @@ cudaError_t launch_scale_dl(ewald_plan_s *p, double C, cudaStream_t s);
 // Stokeslet P2P machinery -- 48-byte near-order source records (positions
 // from the plan's FP32 records, S = sym(q (x) n)), then the sum into u
 cudaError_t launch_dl_records(ewald_plan_s *p, const double *q, const double *n, void *drec, cudaStream_t s);
-cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, double *u, cudaStream_t s);
+// adds the double layer's FP32 near field into p->un (FP32 plans: after the Stokeslet P2P, same stream)
+cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, cudaStream_t s);
 cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, const double *n, double *u,
                           cudaStream_t s);
 cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);

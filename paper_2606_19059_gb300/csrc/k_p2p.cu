@@ -1416,9 +1416,10 @@ __device__ __forceinline__ void pair2_dl(const float3 &d0, const float4 &sb0, co
 }
 
 // One work item of the double-layer near field by one warp; adds the sums
-// (times inv_cell2) into u, user order.
+// (times inv_cell2) into the plan's FP32 near result un, user order, which
+// the Stokeslet P2P wrote before it on the same stream.
 __device__ __forceinline__ void p2p_dl32_item(const P2PArgs &a, const float4 *__restrict__ drec, const DLConst &kc,
-                                              double inv_cell2, double *__restrict__ u, int item, WsDL &ws,
+                                              double inv_cell2, float *__restrict__ u, int item, WsDL &ws,
                                               int lane)
 {
     int c, tb, te, tsplit;
@@ -1498,14 +1499,14 @@ __device__ __forceinline__ void p2p_dl32_item(const P2PArgs &a, const float4 *__
     }
     if (active) {
         const int i = a.permn[t];
-        u[3 * i] += ux * inv_cell2;
-        u[3 * i + 1] += uy * inv_cell2;
-        u[3 * i + 2] += uz * inv_cell2;
+        u[3 * i] = (float)((double)u[3 * i] + ux * inv_cell2);
+        u[3 * i + 1] = (float)((double)u[3 * i + 1] + uy * inv_cell2);
+        u[3 * i + 2] = (float)((double)u[3 * i + 2] + uz * inv_cell2);
     }
 }
 
 __global__ void __launch_bounds__(kWarps * 32) k_p2p_dl32(P2PArgs a, const float4 *__restrict__ drec, DLConst kc,
-                                                          double inv_cell2, double *__restrict__ u)
+                                                          double inv_cell2, float *__restrict__ u)
 {
     __shared__ WsDL wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1759,7 +1760,7 @@ cudaError_t launch_p2p(ewald_plan_s *p, cudaStream_t s)
 
 // Double-layer near field of an FP32 plan (records from build_dl_records),
 // added into u (user order).
-cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, double *u, cudaStream_t s)
+cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, cudaStream_t s)
 {
     cudaError_t e = load_p2p_constants();
     if (e != cudaSuccess)
@@ -1776,7 +1777,8 @@ cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, double *u, cudaSt
     kc.c2xi2 = (float)(2.0 * xic * xic * xic / sqrt(3.14159265358979323846));
     const int64_t items = p2p_items(p);
     const unsigned grid = (unsigned)((items + kWarps - 1) / kWarps);
-    k_p2p_dl32<<<grid, kWarps * 32, 0, s>>>(a, (const float4 *)drec, kc, 1.0 / (p->g.cell * p->g.cell), u);
+    k_p2p_dl32<<<grid, kWarps * 32, 0, s>>>(a, (const float4 *)drec, kc, 1.0 / (p->g.cell * p->g.cell),
+                                            (float *)p->un);
     return cudaGetLastError();
 }
 

@@ -431,6 +431,10 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
         EW_CUDA(cudaEventRecord(p->ev_fork, s));
     // P2G of the Stokeslet forces, then of the double layer's six densities
     auto p2g = [&]() -> cudaError_t {
+        if (dl && p2g9_supported(p)) {  // all nine components in one pass
+            cudaError_t e = launch_dl_densities(p, dl->q, dl->n, s);
+            return e == cudaSuccess ? launch_p2g9(p, p->dl_tf, p->dl_grid, s) : e;
+        }
         cudaError_t e = launch_p2g(p, s);
         if (e != cudaSuccess || !dl)
             return e;

@@ -243,6 +243,11 @@ cudaError_t launch_scale_dl(ewald_plan_s *p, double C, cudaStream_t s);
 // Stokeslet P2P machinery -- 48-byte near-order source records (positions
 // from the plan's FP32 records, S = sym(q (x) n)), then the sum into u
 cudaError_t launch_dl_records(ewald_plan_s *p, const double *q, const double *n, void *drec, cudaStream_t s);
+// P2G of the Stokeslet forces and the double layer's two density triples
+// (dl_tf: 2 N float4 in tile order) in one pass onto p->grid and the two
+// 3-component grids at dl_grid (FP32-kernel plans with 8^3 tiles)
+bool p2g9_supported(const ewald_plan_s *p);
+cudaError_t launch_p2g9(ewald_plan_s *p, const void *dl_tf, void *dl_grid, cudaStream_t s);
 // adds the double layer's FP32 near field into p->un (FP32 plans: after the Stokeslet P2P, same stream)
 cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, cudaStream_t s);
 cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, const double *n, double *u,

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "p2g_common.h"
 
 namespace ewg {
 namespace {
@@ -61,15 +62,7 @@ template <typename R> struct Vec4;
 template <> struct Vec4<float> { using T = float4; };
 template <> struct Vec4<double> { using T = dvec4; };
 
-constexpr int kP2GThreads = 256;
-constexpr int kP2GCandidates = 2;  // candidates per thread and round (512 a round)
-constexpr int kMaxSeg = 125;  // (KT+1)^3 with KT <= 4 (T = 4, P = 16)
-
-__device__ __forceinline__ int wrapi(int i, int n)
-{
-    i %= n;
-    return i < 0 ? i + n : i;
-}
+__device__ __forceinline__ int wrapi(int i, int n) { return p2g_wrapi(i, n); }
 
 // P2G: R = accumulation precision, G = grid element type.  PC > 0 fixes P at
 // compile time: (B) then evaluates all P bins of one (point, axis) in one
@@ -98,7 +91,7 @@ __device__ __forceinline__ void p2g_body(const GridArgs &a, const int tile)
     R *sd = sf + B * 4;             // [B][3] fractional offsets delta
     R *coef = sd + B * 3;           // PC = 0: [P][deg+1]; PC > 0: [deg+1][PS]
     __shared__ int soff[B];         // packed anchor offsets relative to the tile (biased)
-    __shared__ int seg_start[kMaxSeg], seg_pref[kMaxSeg + 1];
+    __shared__ int seg_start[kP2GMaxSeg], seg_pref[kP2GMaxSeg + 1];
     __shared__ int scount;
 
     const int nt = a.nt, P = PC > 0 ? PC : a.P, nd = a.deg + 1, KT = a.KT;
@@ -113,31 +106,7 @@ __device__ __forceinline__ void p2g_body(const GridArgs &a, const int tile)
         for (int i = threadIdx.x; i < P * nd; i += NT)
             coef[i] = ((const R *)a.wcoef)[i];
     }
-    // segment table: neighbour tile s = (dz, dy, dx) in [-KT, 0]^3
-    if (threadIdx.x < 32) {
-        int carry = 0;
-        for (int s0 = 0; s0 < nseg; s0 += 32) {
-            int s = s0 + threadIdx.x, len = 0;
-            if (s < nseg) {
-                int dx = s % side - KT, dy = (s / side) % side - KT, dz = s / (side * side) - KT;
-                int nb = (wrapi(tz + dz, nt) * nt + wrapi(ty + dy, nt)) * nt + wrapi(tx + dx, nt);
-                seg_start[s] = a.startt[nb];
-                len = a.startt[nb + 1] - a.startt[nb];
-            }
-            int v = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(0xffffffffu, v, o);
-                if ((int)threadIdx.x >= o)
-                    v += u;
-            }
-            if (s < nseg)
-                seg_pref[s + 1] = carry + v;
-            carry += __shfl_sync(0xffffffffu, v, 31);
-        }
-        if (threadIdx.x == 0)
-            seg_pref[0] = 0;
-    }
+    p2g_segment_table(a.startt, nt, KT, tx, ty, tz, seg_start, seg_pref);
     const int row = threadIdx.x % ROWS, slice = threadIdx.x / ROWS;
     const int y = row % T, z = row / T;  // rows (y, z) and (y, z + T/2)
     // FP32: the sums of x and x + 1 packed for FP32x2 FMAs, acc2[h][x / 2][c]
@@ -173,17 +142,8 @@ __device__ __forceinline__ void p2g_body(const GridArgs &a, const int tile)
         R4 td;
         int j = 0, ox = 0, oy = 0, oz = 0;
         if (q < total) {
-            int lo = 0, hi = nseg;  // seg_pref[lo] <= q < seg_pref[hi]
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (seg_pref[mid] <= q)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            const int s = lo;
-            j = seg_start[s] + (q - seg_pref[s]);
-            const int dx = s % side - KT, dy = (s / side) % side - KT, dz = s / (side * side) - KT;
+            int dx, dy, dz;
+            j = p2g_candidate(seg_start, seg_pref, nseg, KT, q, dx, dy, dz);
             td = tdat[j];
             int packed = (int)td.w;
             ox = dx * T + (packed & 15);

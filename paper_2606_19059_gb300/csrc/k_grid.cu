@@ -317,14 +317,16 @@ __device__ __forceinline__ void p2g_body(const GridArgs &a, const int tile)
         __syncthreads();
     }
     // reduce the slices through shared memory and store the tile
-    R *red = (R *)smem;  // [SL][3][T][T][T]  (reuses the staging area)
+    // [SL][3][T][T][T + 1] (reuses the staging area): rows padded by one so
+    // that the 32 rows (y, z) a warp writes at one x fall in 32 banks
+    R *red = (R *)smem;
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int x = 0; x < T; ++x)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                red[((slice * 3 + c) * T + z + h * H) * T * T + y * T + x] =
+                red[(((slice * 3 + c) * T + z + h * H) * T + y) * (T + 1) + x] =
                     kPack ? (x & 1 ? acc2[h][x / 2][c].y : acc2[h][x / 2][c].x) : acc[kPack ? 0 : h][kPack ? 0 : x][c];
     __syncthreads();
     G *grid = (G *)a.grid;
@@ -334,7 +336,7 @@ __device__ __forceinline__ void p2g_body(const GridArgs &a, const int tile)
         R s = 0;
 #pragma unroll
         for (int qq = 0; qq < SL; ++qq)
-            s += red[((qq * 3 + c) * T + zz) * T * T + yy * T + x];
+            s += red[(((qq * 3 + c) * T + zz) * T + yy) * (T + 1) + x];
         const int64_t gx = tx * T + x, gy = ty * T + yy, gz = tz * T + zz;
         grid[c * M3 + (gz * M + gy) * M + gx] = (G)s;
     }
@@ -920,7 +922,7 @@ cudaError_t run_p2g(const GridArgs &a, cudaStream_t s)
     constexpr int B = kP2GThreads * kP2GCandidates;
     const size_t ncoef = PC > 0 ? (size_t)(a.deg + 1) * ((PC + 3) & ~3) : (size_t)a.P * (a.deg + 1);
     size_t stage = sizeof(R) * ((size_t)B * (3 * T + 7) + ncoef);
-    size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * T;
+    size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * (T + 1);
     size_t sm = stage > red ? stage : red;
     cudaError_t e = cudaFuncSetAttribute(k_p2g<T, R, G, PC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1103,7 +1105,7 @@ size_t p2g_smem(int P, int deg)
     constexpr int B = kP2GThreads * kP2GCandidates;
     const size_t ncoef = PC > 0 ? (size_t)(deg + 1) * ((PC + 3) & ~3) : (size_t)P * (deg + 1);
     const size_t stage = sizeof(R) * ((size_t)B * (3 * T + 7) + ncoef);
-    const size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * T;
+    const size_t red = sizeof(R) * (size_t)(kP2GThreads / (T * T / 2)) * 3 * T * T * (T + 1);
     return stage > red ? stage : red;
 }
 

@@ -174,12 +174,12 @@ __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g9(P2G9Args a)
     }
     // reduce the slices through shared memory (reusing the staging area) and
     // store the three tiles
-    float *red = (float *)smem;  // [kSl9][kNc9][T][T][T]
+    float *red = (float *)smem;  // [kSl9][kNc9][T][T][T + 1]: rows padded by one (bank-conflict-free writes)
 #pragma unroll
     for (int x = 0; x < T; ++x)
 #pragma unroll
         for (int c = 0; c < kNc9; ++c)
-            red[((slice * kNc9 + c) * T + z) * T * T + y * T + x] = (x & 1) ? acc[x / 2][c].y : acc[x / 2][c].x;
+            red[(((slice * kNc9 + c) * T + z) * T + y) * (T + 1) + x] = (x & 1) ? acc[x / 2][c].y : acc[x / 2][c].x;
     __syncthreads();
     const int64_t M = a.M, M3 = M * M * M;
     for (int o = threadIdx.x; o < kNc9 * T * T * T; o += NT) {
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g9(P2G9Args a)
         float s = 0.f;
 #pragma unroll
         for (int qq = 0; qq < kSl9; ++qq)
-            s += red[((qq * kNc9 + c) * T + zz) * T * T + yy * T + x];
+            s += red[(((qq * kNc9 + c) * T + zz) * T + yy) * (T + 1) + x];
         const int64_t gx = tx * T + x, gy = ty * T + yy, gz = tz * T + zz;
         const int t = c / 3, cc = c - 3 * t;
         G *gp = (G *)(t == 0 ? a.grid[0] : (t == 1 ? a.grid[1] : a.grid[2]));  // no dynamic parameter index
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g9(P2G9Args a)
 size_t p2g9_smem(int PS, int deg)
 {
     const size_t stage = sizeof(float) * ((size_t)kB9 * (3 * kT9 + 12 + 3) + (size_t)(deg + 1) * PS);
-    const size_t red = sizeof(float) * (size_t)kSl9 * kNc9 * kT9 * kT9 * kT9;
+    const size_t red = sizeof(float) * (size_t)kSl9 * kNc9 * kT9 * kT9 * (kT9 + 1);
     return stage > red ? stage : red;
 }
 

@@ -743,9 +743,9 @@ def main():
                 "what": "combined single + double layer apply (Sec. 2.3), same points, q and n ~ N(0, 1)",
                 "value": dl_rate, "unit": UNIT, "ms_per_step": dl_ms,
                 "stages_ms": {k: round(v, 5) for k, v in sd.items()},
-                # the double layer's near field runs after the sum: the
-                # difference of the two applies' sum stages is its time
-                "near_dl_ms": round(sd["sum_ms"] - st["sum_ms"], 5),
+                # the FP32 double-layer pairs run after the Stokeslet P2P (in
+                # its stage), the FP64 ones after the sum (in that stage)
+                "near_dl_ms": round(sd["p2p_ms"] - st["p2p_ms"] + sd["sum_ms"] - st["sum_ms"], 5),
                 "near_dl_kernel": ("k_p2p_dl<double> (FP64 pairs, one warp per 32 targets, queued in-range "
                                    "pairs)" if prm["fft_f64"] or prm["near_f64"]
                                    else "k_p2p_dl32 (FP32 pairs on the Stokeslet P2P machinery: sub-cell "

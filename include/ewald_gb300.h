@@ -94,7 +94,10 @@ typedef struct {
 
 /* Per-stage device times (ms) of the most recent apply with timing enabled
  * (ewald_set_timing).  P2P runs on a second stream concurrently with the far
- * field, so the stages do not add up to total_ms. */
+ * field, so the stages do not add up to total_ms.  In a combined apply
+ * (ewald_apply_combined) p2p_ms includes the double layer's FP32 near field
+ * (FP32 plans) and sum_ms its FP64 near field (the other plans); p2g_ms
+ * covers the spreading of all nine components. */
 typedef struct {
     float bin_ms, p2p_ms, p2g_ms, fft_ms, scale_ms, ifft_ms, g2p_ms, sum_ms, total_ms;
 } ewald_stage_timing;

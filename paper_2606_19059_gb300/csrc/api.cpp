@@ -459,13 +459,13 @@ ewald_status compute(ewald_plan_s *p, const double *f, double *u, Mode mode, cud
             EW_CUDA(cudaStreamWaitEvent(p->s2, p->ev_fork, 0));
         rec(p, 7, sn);
         EW_CUDA(launch_p2p(p, sn));
-        rec(p, 8, sn);
         // the double layer's FP32 near field on the same branch, added into
-        // the near result before the sum reads it
+        // the near result before the sum reads it (timed with P2P)
         if (dl && mode == FULL && dl32) {
             EW_CUDA(launch_dl_records(p, dl->q, dl->n, p->dl_near, sn));
             EW_CUDA(launch_p2p_dl32(p, p->dl_near, sn));
         }
+        rec(p, 8, sn);
         if (overlap)
             EW_CUDA(cudaEventRecord(p->ev_join, p->s2));
     }

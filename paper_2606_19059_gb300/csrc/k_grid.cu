@@ -678,8 +678,21 @@ __device__ __forceinline__ void g2p_planar_body(const GridArgs &a, const int til
     const int c0 = ok0 ? l0 : 0, c1 = ok1 ? l1 : 0;
     const float4 *tdat = (const float4 *)a.tdat;
     float *uf = (float *)a.uf;
+    // each warp's next point record and output index are loaded one point
+    // ahead, so their L2 latency overlaps the current point's sums
+    float4 td_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    int i_next = 0;
+    if (s0 + warp < s1) {
+        td_next = tdat[s0 + warp];
+        i_next = a.permt[s0 + warp];
+    }
     for (int p = s0 + warp; p < s1; p += G::NW) {
-        const float4 td = tdat[p];
+        const float4 td = td_next;
+        const int i = i_next;
+        if (p + G::NW < s1) {
+            td_next = tdat[p + G::NW];
+            i_next = a.permt[p + G::NW];
+        }
         const int packed = (int)td.w;
         const int ox = packed & 15, oy = (packed >> 4) & 15, oz = (packed >> 8) & 15;
         __syncwarp();
@@ -721,7 +734,6 @@ __device__ __forceinline__ void g2p_planar_body(const GridArgs &a, const int til
             u2 += __shfl_xor_sync(0xffffffffu, u2, o);
         }
         if (lane == 0) {
-            const int i = a.permt[p];
             const float sc = (float)a.scale;
             uf[3 * i] = u0 * sc;
             uf[3 * i + 1] = u1 * sc;

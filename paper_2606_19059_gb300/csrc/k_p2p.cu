@@ -225,14 +225,18 @@ __device__ __forceinline__ float fast_rsqrt(float x)  // x >= 1e-30: no denormal
 // the skipped pair, -selfc f (r2 + 1e-30 keeps 1/r finite there, and d = 0
 // zeroes the r (r.f) part).  Beyond rc (what passes the FP16 test's margin,
 // and the dummy entries): r2 is replaced by 1e30, for which e^{-xi^2 r^2}, and
-// with it every factor of the term, is exactly 0.
+// with it every factor of the term, is exactly 0.  SPLIT (the outer pass of a
+// split near field): pairs with r2 <= r1sq, r = 0 among them, are left to the
+// double-single pass and get r2 = 1e30 too.
+template <bool SPLIT>
 __device__ __forceinline__ void pair2_f32_bulk(const float3 &d0, const float3 &f0, const float3 &d1,
                                                const float3 &f1, const F32Const &k, float3 &c0,
                                                float3 &c1)
 {
-    const float ra = fmaf(d0.x, d0.x, fmaf(d0.y, d0.y, d0.z * d0.z));
-    const float rb = fmaf(d1.x, d1.x, fmaf(d1.y, d1.y, d1.z * d1.z));
-    const float2 r2s = make_float2(ra <= k.rc2 ? ra + 1e-30f : 1e30f, rb <= k.rc2 ? rb + 1e-30f : 1e30f);
+    const float ra = pair_r2(d0.x, d0.y, d0.z);
+    const float rb = pair_r2(d1.x, d1.y, d1.z);
+    const bool ina = ra <= k.rc2 && (!SPLIT || ra > k.r1sq), inb = rb <= k.rc2 && (!SPLIT || rb > k.r1sq);
+    const float2 r2s = make_float2(ina ? ra + 1e-30f : 1e30f, inb ? rb + 1e-30f : 1e30f);
     const float2 rinv = make_float2(fast_rsqrt(r2s.x), fast_rsqrt(r2s.y));
     const float2 x = __fmul2_rn(make_float2(k.xi, k.xi), __fmul2_rn(r2s, rinv));
     const float2 ea = __fmul2_rn(r2s, make_float2(k.nxi2log2e, k.nxi2log2e));
@@ -248,8 +252,10 @@ __device__ __forceinline__ void pair2_f32_bulk(const float3 &d0, const float3 &f
     const float2 nB = __fmul2_rn(make_float2(-k.c2, -k.c2), E);
     float2 amb = __ffma2_rn(E, Ar, nB);
     const float2 apb = __ffma2_rn(E, Ar, B);
-    amb.x = ra == 0.0f ? -k.selfc : amb.x;
-    amb.y = rb == 0.0f ? -k.selfc : amb.y;
+    if constexpr (!SPLIT) {
+        amb.x = ra == 0.0f ? -k.selfc : amb.x;
+        amb.y = rb == 0.0f ? -k.selfc : amb.y;
+    }
     const float2 rf = make_float2(fmaf(d0.x, f0.x, fmaf(d0.y, f0.y, d0.z * f0.z)),
                                   fmaf(d1.x, f1.x, fmaf(d1.y, f1.y, d1.z * f1.z)));
     const float2 co = __fmul2_rn(__fmul2_rn(apb, rf), __fmul2_rn(rinv, rinv));
@@ -675,8 +681,10 @@ __device__ __forceinline__ void stage_f32(const P2PArgs &a, WsF32 &ws, int nseg,
 // over the tiles: round o runs until every lane has evaluated its in-range
 // sources of tile o -- the busiest lane's count, known up front -- while lanes
 // done early go on into tile o + 1; then tile o + 2 takes tile o's slot.
-// KAHAN: compensated partial sums, flushed into FP64 totals every round.
-template <bool KAHAN>
+// KAHAN: compensated partial sums, flushed into FP64 totals every round, of
+// the tight pair form -- or, with BULK2 (the outer pass of a split near
+// field), of the two-pair bulk form without the pairs within r1.
+template <bool KAHAN, bool BULK2 = false>
 __device__ __forceinline__ bool p2p_f32_run(const P2PArgs &a, const F32Const &kc, int item, WsF32 &ws, int lane,
                                             int &t_out, bool &act_out,
                                             typename std::conditional<KAHAN, double, float>::type (&u)[3])
@@ -732,7 +740,27 @@ __device__ __forceinline__ bool p2p_f32_run(const P2PArgs &a, const F32Const &kc
     for (int o = 0; o < ntile; ++o) {
         const int need = (int)__reduce_max_sync(0xffffffffu, (unsigned)q.pending());
         typename std::conditional<KAHAN, KSum, float>::type px{}, py{}, pz{};
-        if constexpr (KAHAN) {
+        if constexpr (KAHAN && BULK2) {
+            for (int it = 0; it < (need + 1) >> 1; ++it) {
+                const int e0 = q.pop(), e1 = q.pop();
+                const float4 s0 = ws.tile.sa[e0], b0 = ws.tile.sb[e0];
+                const float4 s1 = ws.tile.sa[e1], b1 = ws.tile.sb[e1];
+                const float f0 = ws.tile.sc[e0], f1 = ws.tile.sc[e1];
+                float3 c0, c1;
+                pair2_f32_bulk<true>(make_float3((th.x - s0.x) + (tl.x - s0.w), (th.y - s0.y) + (tl.y - b0.x),
+                                                 (th.z - s0.z) + (tl.z - b0.y)),
+                                     make_float3(b0.z, b0.w, f0),
+                                     make_float3((th.x - s1.x) + (tl.x - s1.w), (th.y - s1.y) + (tl.y - b1.x),
+                                                 (th.z - s1.z) + (tl.z - b1.y)),
+                                     make_float3(b1.z, b1.w, f1), kc, c0, c1);
+                px.add(c0.x);
+                px.add(c1.x);
+                py.add(c0.y);
+                py.add(c1.y);
+                pz.add(c0.z);
+                pz.add(c1.z);
+            }
+        } else if constexpr (KAHAN) {
             for (int it = 0; it < need; ++it) {
                 const int e = q.pop();
                 const float4 s = ws.tile.sa[e], b = ws.tile.sb[e];
@@ -749,7 +777,7 @@ __device__ __forceinline__ bool p2p_f32_run(const P2PArgs &a, const F32Const &kc
                 const float4 s1 = ws.tile.sa[e1], b1 = ws.tile.sb[e1];
                 const float f0 = ws.tile.sc[e0], f1 = ws.tile.sc[e1];
                 float3 c0, c1;
-                pair2_f32_bulk(make_float3((th.x - s0.x) + (tl.x - s0.w), (th.y - s0.y) + (tl.y - b0.x),
+                pair2_f32_bulk<false>(make_float3((th.x - s0.x) + (tl.x - s0.w), (th.y - s0.y) + (tl.y - b0.x),
                                            (th.z - s0.z) + (tl.z - b0.y)),
                                make_float3(b0.z, b0.w, f0),
                                make_float3((th.x - s1.x) + (tl.x - s1.w), (th.y - s1.y) + (tl.y - b1.x),
@@ -1270,7 +1298,7 @@ __device__ __forceinline__ void p2p_split_item(const P2PArgs &a, const F32Const 
     dsf ui[3];
     int t;
     bool active;
-    if (!p2p_f32_run<true>(a, k32, item, ws.f, lane, t, active, uo))
+    if (!p2p_f32_run<true, true>(a, k32, item, ws.f, lane, t, active, uo))
         return;
     __syncwarp();
     p2p_ds_run(a, kds, item, ws.d, lane, t, active, ui);

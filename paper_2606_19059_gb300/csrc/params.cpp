@@ -190,37 +190,45 @@ static bool fft_friendly(int m)
 // 1e-7).  A pair's term is G^N(r) f, |G^N f|^2 averaged over directions of f
 // = |f|^2 (2 (A - B)^2 + 4 A^2) / 3 with A = erfc(x)/r, B = (2 xi/sqrt(pi))
 // e^{-x^2}, x = xi r (eq. (g-near)); its size falls off with x.  Pairs beyond
-// r1 = x1/xi are evaluated in the compensated FP32 form (relative error per
-// term ~2e-7), those within r1 in double-single.  Their random FP32 errors
-// add to ~2e-7 sqrt(sum over the pairs beyond r1 of |term|^2); x1 is the
-// smallest x for which, with pairs spread uniformly in space (density ~ x^2:
-// the case with the most weight beyond x1; clustered points put more of it
-// close), that share of sum |term|^2 stays below (tol / (10 * 2e-7))^2 -- the
-// FP32 part's error then stays near tol/10 of the near field.  Returns rc
+// r1 = x1/xi are evaluated in the two-pair FP32 bulk form with compensated
+// sums, those within r1 in double-single.  The bulk form's relative error per
+// term is eps(x) = sqrt(eps0^2 + (eps1 x^2)^2): eps0 = 3e-7 from the erfcx fit
+// and the hardware rsqrt, ex2 and rcp approximations, and eps1 x^2 (eps1 =
+// 1.2e-7) from e^{-x^2} = 2^a with a = -x^2 log2(e) computed from the FP32
+// r^2 (two units in the last place of a, times |a| ln 2).  Their random
+// errors add to ~sqrt(sum over the pairs beyond r1 of eps^2 |term|^2); x1 is
+// the smallest x for which, with pairs spread uniformly in space (density ~
+// x^2: the case with the most weight beyond x1; clustered points put more of
+// it close), that sum stays below (tol/5)^2 sum |term|^2 -- the FP32 part's
+// error then stays near tol/5 of the near field, which with the three eq.
+// (ese) terms held at tol/10 each keeps the total within tol.  Returns rc
 // when nothing is left to split off.
 double ds_split_radius(double tol, double xi, double rc)
 {
     const double xc = xi * rc;
     if (!(xc > 0) || !(tol > 0))
         return rc;
-    const double target = (tol / (10.0 * 2e-7)) * (tol / (10.0 * 2e-7));
-    if (target >= 1.0)
-        return 0.0;
+    constexpr double eps0 = 3e-7, eps1 = 1.2e-7;
+    const double target = (tol / 5.0) * (tol / 5.0);
     auto w = [](double x) {
         if (x <= 0.0)
             return 6.0;  // the limit x^2 (2 (A - B)^2 + 4 A^2) as x -> 0 (units of xi |f|)
         const double A = erfc(x) / x, B = 1.1283791670955126 * exp(-x * x);
         return x * x * (2.0 * (A - B) * (A - B) + 4.0 * A * A);
     };
+    auto ew = [&](double x) { return (eps0 * eps0 + eps1 * eps1 * x * x * x * x) * w(x); };
     // composite Simpson on n panels, accumulated from xc down
     const int n = 4000;
     const double hx = xc / n;
-    std::vector<double> tail(n + 1, 0.0);  // tail[i] = integral from x_i to xc
+    std::vector<double> tail(n + 1, 0.0);  // tail[i] = integral of eps^2 w from x_i to xc
+    double total = 0.0;                     // integral of w from 0 to xc
     for (int i = n - 1; i >= 0; --i) {
-        const double a = i * hx, b = a + hx;
-        tail[i] = tail[i + 1] + hx / 6.0 * (w(a) + 4.0 * w(0.5 * (a + b)) + w(b));
+        const double a = i * hx, b = a + hx, m = 0.5 * (a + b);
+        tail[i] = tail[i + 1] + hx / 6.0 * (ew(a) + 4.0 * ew(m) + ew(b));
+        total += hx / 6.0 * (w(a) + 4.0 * w(m) + w(b));
     }
-    const double total = tail[0];
+    if (tail[0] <= target * total)
+        return 0.0;  // the bulk form holds everywhere: nothing to split off
     for (int i = 0; i <= n; ++i)
         if (tail[i] <= target * total)
             return i >= n ? rc : (i * hx) / xi;

@@ -181,24 +181,7 @@ __device__ __forceinline__ void p2g_body(const GridArgs &a, const int tile)
                 const R zz = (R)2 * sd[k * 3 + d] - (R)1;
                 R pv[PS];
                 if constexpr (sizeof(R) == 4) {
-                    // bins in pairs: packed FP32x2 Horner, one instruction per two bins
-                    float2 pv2[PS / 2];
-                    const float2 z2 = make_float2(zz, zz);
-                    const float2 *cd = (const float2 *)(coef + (nd - 1) * PS);
-#pragma unroll
-                    for (int l = 0; l < PS / 2; ++l)
-                        pv2[l] = cd[l];
-                    for (int jj = nd - 2; jj >= 0; --jj) {
-                        const float2 *cj = (const float2 *)(coef + jj * PS);
-#pragma unroll
-                        for (int l = 0; l < PS / 2; ++l)
-                            pv2[l] = __ffma2_rn(pv2[l], z2, cj[l]);
-                    }
-#pragma unroll
-                    for (int l = 0; l < PS / 2; ++l) {
-                        pv[2 * l] = pv2[l].x;
-                        pv[2 * l + 1] = pv2[l].y;
-                    }
+                    window_bins_sym<PC, PS>(coef, nd, zz, pv);
                 } else {
                     const R *cd = coef + (nd - 1) * PS;
 #pragma unroll

@@ -117,18 +117,8 @@ __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g9(P2G9Args a)
             const int k = w / 3, d = w - 3 * k;
             const int o = ((soff[k] >> (6 * d)) & 63) - 32;
             const float zz = 2.f * sd[k * 3 + d] - 1.f;
-            float2 pv2[PS / 2];
-            const float2 z2 = make_float2(zz, zz);
-            const float2 *cd = (const float2 *)(coef + (nd - 1) * PS);
-#pragma unroll
-            for (int l = 0; l < PS / 2; ++l)
-                pv2[l] = cd[l];
-            for (int jj = nd - 2; jj >= 0; --jj) {
-                const float2 *cj = (const float2 *)(coef + jj * PS);
-#pragma unroll
-                for (int l = 0; l < PS / 2; ++l)
-                    pv2[l] = __ffma2_rn(pv2[l], z2, cj[l]);
-            }
+            float pv[PS];
+            window_bins_sym<PC, PS>(coef, nd, zz, pv);
             float *rowp = (d == 0 ? wx : (d == 1 ? wy : wz)) + k * T;
 #pragma unroll
             for (int x = 0; x < T; ++x)
@@ -137,7 +127,7 @@ __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g9(P2G9Args a)
             for (int l = 0; l < PC; ++l) {
                 const int qq = o + l;
                 if ((unsigned)qq < (unsigned)T)
-                    rowp[qq] = (l & 1) ? pv2[l >> 1].y : pv2[l >> 1].x;
+                    rowp[qq] = pv[l];
             }
         }
         __syncthreads();

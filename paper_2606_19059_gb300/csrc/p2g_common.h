@@ -73,4 +73,47 @@ __device__ __forceinline__ int p2g_candidate(const int *seg_start, const int *se
     return seg_start[lo] + (q - seg_pref[lo]);
 }
 
+// The P bins of one (point, axis) from the first ceil(P/2) bins' polynomials:
+// the window is even, so bin P-1-l at z is bin l at -z (w_{P-1-l}(z) =
+// w_l(-z), and the Chebyshev fit inherits it), and both follow from the even
+// and odd parts of bin l's polynomial, E(z^2) +- z O(z^2): half the Horner
+// work of evaluating all P bins.  Packed FP32x2 over pairs of bins l.
+template <int PC, int PS>
+__device__ __forceinline__ void window_bins_sym(const float *coef, int nd, float zz, float (&pv)[PS])
+{
+    constexpr int NH = (PC + 1) / 2, NQ = (NH + 1) / 2;  // bins evaluated; their float2 pairs
+    const float zsq = zz * zz;
+    const float2 s2 = make_float2(zsq, zsq), z2 = make_float2(zz, zz), nz2 = make_float2(-zz, -zz);
+    const int je = (nd - 1) & ~1, jo = ((nd - 1) & 1) ? nd - 1 : nd - 2;  // top even and odd powers
+    float2 ev[NQ], od[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        ev[q] = *(const float2 *)(coef + je * PS + 2 * q);
+        od[q] = jo >= 1 ? *(const float2 *)(coef + jo * PS + 2 * q) : make_float2(0.f, 0.f);
+    }
+    for (int j = je - 2; j >= 0; j -= 2) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            ev[q] = __ffma2_rn(ev[q], s2, *(const float2 *)(coef + j * PS + 2 * q));
+    }
+    for (int j = jo - 2; j >= 1; j -= 2) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            od[q] = __ffma2_rn(od[q], s2, *(const float2 *)(coef + j * PS + 2 * q));
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float2 lo = __ffma2_rn(z2, od[q], ev[q]), hi = __ffma2_rn(nz2, od[q], ev[q]);
+        const int l0 = 2 * q, l1 = 2 * q + 1;
+        if (l0 < NH) {
+            pv[l0] = lo.x;
+            pv[PC - 1 - l0] = l0 < PC - 1 - l0 ? hi.x : pv[l0];
+        }
+        if (l1 < NH) {
+            pv[l1] = lo.y;
+            pv[PC - 1 - l1] = l1 < PC - 1 - l1 ? hi.y : pv[l1];
+        }
+    }
+}
+
 }  // namespace ewg

@@ -65,7 +65,9 @@ def test_near_field_small_box_explicit_images():
     assert errs(u, ref)[1] < 1e-11
 
 
-@pytest.mark.parametrize("dtype,P,M", [(F64, 8, 32), (F64, 7, 24), (F32, 12, 32)])
+# FP32 P2G evaluates bins l and P-1-l from bin l's even and odd parts: odd P
+# (a bin on the axis of symmetry) and even P both
+@pytest.mark.parametrize("dtype,P,M", [(F64, 8, 32), (F64, 7, 24), (F32, 12, 32), (F32, 11, 32), (F32, 7, 24)])
 def test_spread_matches_exact_window(dtype, P, M):
     x, f = workloads.make("uniform", 400, seed=103)
     p = plan(400, 1.0, 1e-8 if dtype == F64 else 1e-6, dtype, M=M, P=P)

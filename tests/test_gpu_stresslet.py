@@ -91,6 +91,22 @@ def test_double_layer_fp32_bulk_within_tolerance():
     assert l2 < 1e-6 and mx < 1e-6
 
 
+@pytest.mark.parametrize("tile,P", [(4, 12), (8, 11)])
+def test_combined_fp32_other_tile_and_odd_support(tile, P):
+    # 4^3 tiles take the per-triple P2G passes instead of the one-pass
+    # nine-component kernel; an odd support puts a bin on the window's axis of
+    # symmetry (the P2G rows of bins l and P-1-l come from one polynomial)
+    N = 1500
+    x, f, q, n = _case("uniform", N, 409)
+    p = ewald.Plan(N, 1.0, 1e-6, F32, M=32, P=P, tile=tile)
+    assert (p.params.tile, p.params.P) == (tile, P)
+    u = _combined(p, x, f, q, n)
+    tid = np.arange(0, N, 13)
+    ref = oracle.ewald(x, f, 1.0, targets=tid) + dl.ewald(x, dl.densities(q, n), 1.0, targets=tid)
+    l2, mx = errs(u[tid], ref)
+    assert l2 < 1e-6 and mx < 1e-6, (l2, mx)
+
+
 def test_double_layer_fp32_pairs_fp64_fft_two_cells_per_side():
     # FP32 bulk at 1e-7 < tol < 1e-6: FP32 densities spread onto FP64 grids,
     # FP64 CNV and FP64 near-field pairs; n_c = 2, so the 27 neighbour offsets

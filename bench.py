@@ -715,6 +715,9 @@ def main():
         except Exception as exc:  # pragma: no cover - reported, not fatal
             roof["peak_probe"] = {"error": str(exc)}
         roof["algorithmic"] = {"inrange_pairs": inr, "candidate_pairs": cand,
+                               "candidate_basis": "every target's 27 neighbour cells (the paper's P2P flop model, "
+                                                  "Sec. 4); the kernel's sub-cell culling tests about 86 % of them, "
+                                                  "which would give about 0.92 of this fraction",
                                "flops_per_inrange": FP32_FLOPS_PER_INRANGE,
                                "flops_per_candidate": FLOPS_PER_CANDIDATE, "flops_per_launch": p2p_flops}
         line = {

@@ -242,7 +242,9 @@ enum { EWALD_TUNE_MODEL = 0, EWALD_TUNE_MEASURE = 1 };
  * override), then cuFFT-friendly multiples of 8 for M between 0.6x and 1.7x
  * that choice (at most 6 of them, spread over the range) with grid tile T = 8,
  * and the model's M with the other tile (T = 4), each only where the kernels
- * accept it; P fixed at the planner's.  At most `cap` entries go to `cands`
+ * accept it -- and for double-single plans (EWALD_F32_BULK at tol <= 1e-7)
+ * only tiles their double-single grid kernels take (T = 8), as other tiles
+ * would fall back to FP64 P2G/G2P; P fixed at the planner's.  At most `cap` entries go to `cands`
  * (host array), their number to *n.
  * Errors: EINVAL for NULL pointers, cap < 1 or bad N, L, tol. */
 ewald_status ewald_autotune_candidates(int64_t N, double L, double tol, ewald_dtype dtype,

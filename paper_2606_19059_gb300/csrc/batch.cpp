@@ -83,6 +83,11 @@ ewald_status candidates(int64_t N, double L, double tol, ewald_dtype dtype, int 
             ewald_params q;
             if (choose_params(N, L, tol, dtype, &ov, &q) != EWALD_OK || q.tile != T)
                 continue;
+            // a double-single plan whose grid kernels would fall back to FP64
+            // (4^3 tiles): timed alone such a small box can win, but its FP64
+            // P2G/G2P, at 1/64 of the FP32 rate, dominates a batch of them
+            if (q.near_ds && !grid_ds_supported(q.P, q.tile, q.M))
+                continue;
             bool dup = false;
             for (const ewald_params &c : out)
                 dup |= c.M == q.M && c.tile == q.tile && c.P == q.P;

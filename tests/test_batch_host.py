@@ -44,6 +44,18 @@ def test_candidates_meet_the_planner_bound(N, tol):
     assert min(Ms) >= 0.6 * base.M - 8 and max(Ms) <= 1.7 * base.M + 8
 
 
+@pytest.mark.parametrize("N", [1000, 3000, 20000, 100000])
+def test_double_single_candidates_keep_the_double_single_grid(N):
+    # FP32 bulk at tol <= 1e-7 runs double-single grid kernels, which take 8^3
+    # tiles only; a 4^3-tile candidate would run FP64 P2G/G2P instead
+    c = ewald.ewald_autotune_candidates(N, 1.0, 1e-8, F32, cap=32)
+    assert all(q.near_ds == 1 for q in c)
+    assert all(q.tile == 8 for q in c), [(q.M, q.tile) for q in c]
+    # the FP32 plans still get the 4^3 candidate
+    c6 = ewald.ewald_autotune_candidates(N, 1.0, 1e-6, F32, cap=32)
+    assert any(q.tile == 4 for q in c6)
+
+
 def test_candidates_cap_and_model_mode():
     c = ewald.ewald_autotune_candidates(5000, 1.0, 1e-6, F32, cap=1)
     assert len(c) == 1

@@ -340,13 +340,16 @@ __device__ __forceinline__ void p2g_ds_body(const GridDsArgs &a, const int tile)
         }
         __syncthreads();
     }
-    // sum the slices (reusing the staging area) and store the tile in FP64
-    float2 *red = (float2 *)smem;  // [SL][3][T^3]
+    // sum the slices (reusing the staging area) and store the tile in FP64;
+    // [SL][3][T^2][T + 1]: rows padded by one value, so the 32 rows a warp
+    // writes at one x spread over the banks (unpadded: 16 rows a bank pair)
+    constexpr int RS = T + 1, T3P = T * T * RS;
+    float2 *red = (float2 *)smem;
 #pragma unroll
     for (int x = 0; x < T; ++x)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            red[(slice * 3 + c) * T3 + (z * T + y) * T + x] =
+            red[(slice * 3 + c) * T3P + (z * T + y) * RS + x] =
                 x & 1 ? make_float2(ah[x / 2][c].y, al[x / 2][c].y) : make_float2(ah[x / 2][c].x, al[x / 2][c].x);
     __syncthreads();
     const int M = a.M;
@@ -355,18 +358,19 @@ __device__ __forceinline__ void p2g_ds_body(const GridDsArgs &a, const int tile)
         const int c = o / T3, r = o - c * T3;
         float sh = 0.f, sl = 0.f;
 #pragma unroll
+        const int x = r % T, yy = (r / T) % T, zz = r / (T * T);
+#pragma unroll
         for (int qq = 0; qq < SL; ++qq) {
-            const float2 v = red[(qq * 3 + c) * T3 + r];
+            const float2 v = red[(qq * 3 + c) * T3P + (zz * T + yy) * RS + x];
             ds_acc(sh, sl, v.x, v.y);
         }
-        const int x = r % T, yy = (r / T) % T, zz = r / (T * T);
         const int64_t gx = tx * T + x, gy = ty * T + yy, gz = tz * T + zz;
         a.grid[c * M3 + (gz * M + gy) * M + gx] = ds_join(sh, sl);
     }
 }
 
 constexpr size_t kP2GDsStage = sizeof(float) * 6 * kP2GDsThreads * kT + sizeof(float4) * 2 * kP2GDsThreads;
-constexpr size_t kP2GDsRed = sizeof(float2) * kDsSlices * 3 * kT * kT * kT;
+constexpr size_t kP2GDsRed = sizeof(float2) * kDsSlices * 3 * kT * kT * (kT + 1);
 constexpr size_t kP2GDsSmem = kP2GDsStage > kP2GDsRed ? kP2GDsStage : kP2GDsRed;
 
 // ---- G2P --------------------------------------------------------------------

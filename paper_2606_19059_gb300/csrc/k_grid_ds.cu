@@ -123,17 +123,31 @@ __device__ __forceinline__ void window_ds_body(const dvec4 *__restrict__ tdat, c
     const double z = 2.0 * (d == 0 ? td.x : (d == 1 ? td.y : td.z)) - 1.0;
     float *w = wts + q * 2 * PW;
     const int nd = deg + 1;
-    for (int j = 0; j < PW; ++j) {
-        float h = 0.f, l = 0.f;
-        if (j < P) {
-            const double *c = coef + j * nd;
-            double v = c[deg];
-            for (int k = deg - 1; k >= 0; --k)
-                v = fma(v, z, c[k]);
-            ds_split(v, h, l);
-        }
+    // bins j and P-1-j from bin j's polynomial: the window is even, so bin
+    // P-1-j at z is bin j at -z, E(z^2) -+ z O(z^2) with E, O its even and
+    // odd parts (half the FP64 Horner work)
+    const double z2 = z * z;
+    const int ke = deg & ~1, ko = (deg & 1) ? deg : deg - 1;  // top even and odd powers
+    for (int j = 0; j < (P + 1) / 2; ++j) {
+        const double *c = coef + j * nd;
+        double e = c[ke], o = ko >= 1 ? c[ko] : 0.0;
+        for (int k = ke - 2; k >= 0; k -= 2)
+            e = fma(e, z2, c[k]);
+        for (int k = ko - 2; k >= 1; k -= 2)
+            o = fma(o, z2, c[k]);
+        float h, l;
+        ds_split(fma(z, o, e), h, l);
         w[j] = h;
         w[PW + j] = l;
+        if (P - 1 - j != j) {
+            ds_split(fma(-z, o, e), h, l);
+            w[P - 1 - j] = h;
+            w[PW + P - 1 - j] = l;
+        }
+    }
+    for (int j = P; j < PW; ++j) {
+        w[j] = 0.f;
+        w[PW + j] = 0.f;
     }
 }
 

@@ -262,6 +262,9 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_CUDA(dalloc(p, &p->err, sizeof(int)));
     EW_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->s2));
     EW_CUDA(cudaMemsetAsync(p->items, 0, 4 * ((size_t)g.ncells + 1), p->s2));
+    // binning counters start at zero (each binning's scatter re-zeroes them)
+    EW_CUDA(cudaMemsetAsync(p->cntn, 0, 4 * (size_t)g.nkeys, p->s2));
+    EW_CUDA(cudaMemsetAsync(p->cntt, 0, 4 * (size_t)g.ntiles, p->s2));
     EW_CUDA(cudaStreamSynchronize(p->s2));  // workspaces ready for any stream
 
     // window polynomial coefficients in the kernels' precision
@@ -338,11 +341,20 @@ ewald_status bin(ewald_plan_s *p, const double *x, const double *f, cudaStream_t
     a.nt = g.nt;
     a.f64 = p->near64;
     a.tf_ds = p->grid_ds;
-    EW_CUDA(cudaMemsetAsync(p->cntn, 0, 4 * (size_t)g.nkeys, s));
-    EW_CUDA(cudaMemsetAsync(p->cntt, 0, 4 * (size_t)g.ntiles, s));
-    EW_CUDA(launch_bin_keys(p, a, s));
-    EW_CUDA(launch_bin_scans(p, s));
-    EW_CUDA(launch_bin_scatter(p, a, s));
+    // the counters are zero on entry: set at plan creation, and re-zeroed by
+    // every binning's scatter once the scans have read them (or here, when a
+    // launch of this binning failed)
+    cudaError_t e = launch_bin_keys(p, a, s);
+    if (e == cudaSuccess)
+        e = launch_bin_scans(p, s);
+    if (e == cudaSuccess)
+        e = launch_bin_scatter(p, a, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaMemsetAsync(p->cntn, 0, 4 * (size_t)g.nkeys, s);
+        cudaMemsetAsync(p->cntt, 0, 4 * (size_t)g.ntiles, s);
+        return EWALD_ECUDA;
+    }
     if (p->grid_ds)
         EW_CUDA(launch_window_ds(p, s));
     p->positions_valid = true;

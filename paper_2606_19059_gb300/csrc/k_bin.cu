@@ -25,6 +25,7 @@ struct KeyArgs {
     double L, inv_L, inv_cell, cell, inv_h, half_odd;
     int nc, M, T, nt, ceilP2;
     int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
+    int ncntn, ncntt;  // lengths of cntn and cntt
     const int32_t *startn, *startt;
     void *npos, *nfrc, *nrec, *nflo, *tdat, *tfrc;
     bool tf_ds;
@@ -286,10 +287,18 @@ __global__ void k_bin_keys(KeyArgs k)
 {
     bin_keys_body(k, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
+// One plan's scatter, which also zeroes the per-key and per-tile counters
+// for the next binning: the scans have consumed them (the keys kernel of the
+// next binning counts into them again).
 template <typename R, typename R4>
 __global__ void k_bin_scatter(KeyArgs k)
 {
-    bin_scatter_body<R, R4>(k, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    bin_scatter_body<R, R4>(k, i);
+    for (int64_t q = i; q < k.ncntn; q += stride)
+        k.cntn[q] = 0;
+    for (int64_t q = i; q < k.ncntt; q += stride)
+        k.cntt[q] = 0;
 }
 __global__ void __launch_bounds__(1024) k_scan(ScanJob j0, ScanJob j1, ScanJob j2)
 {
@@ -404,6 +413,8 @@ KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
     k.slott = p->slott;
     k.cntn = p->cntn;
     k.cntt = p->cntt;
+    k.ncntn = p->g.nkeys;
+    k.ncntt = p->g.ntiles;
     k.permn = p->permn;
     k.permt = p->permt;
     k.startn = p->startn;

@@ -201,10 +201,10 @@ extern "C" ewald_status ewald_near_field_noalloc(int64_t N, const ewald_params *
         e = launch_scan(pl.cntn, pl.startn, g.nkeys, s);
     if (e == cudaSuccess)
         e = launch_scan(pl.cntt, pl.startt, g.ntiles, s);
+    if (e == cudaSuccess)  // the work items from the counts, before the scatter re-zeroes them
+        e = launch_cell_items(&pl, s);
     if (e == cudaSuccess)
         e = launch_bin_scatter(&pl, a, s);
-    if (e == cudaSuccess)
-        e = launch_cell_items(&pl, s);
     if (e == cudaSuccess)
         e = launch_p2p(&pl, s);
     if (e == cudaSuccess)

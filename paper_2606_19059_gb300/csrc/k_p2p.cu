@@ -1324,7 +1324,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p_ds(P2PArgs a, DSConst kc, i
     }
 }
 
-__global__ void __launch_bounds__(kWarps * 32) k_p2p_split(P2PArgs a, F32Const k32, DSConst kds, int items)
+// five blocks an SM (the shared ring allows five; registers fit without spills)
+__global__ void __launch_bounds__(kWarps * 32, 5) k_p2p_split(P2PArgs a, F32Const k32, DSConst kds, int items)
 {
     __shared__ WsSplit wsm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -576,12 +576,13 @@ struct GridDsBox {
 };
 
 template <int PC>
-__global__ void __launch_bounds__(kP2GDsThreads, 2) k_p2g_ds(GridDsArgs a)
+// three blocks an SM: 80 registers (a few bytes of spill) against 124 at two
+__global__ void __launch_bounds__(kP2GDsThreads, 3) k_p2g_ds(GridDsArgs a)
 {
     p2g_ds_body<PC>(a, blockIdx.x);
 }
 template <int PC>
-__global__ void __launch_bounds__(kP2GDsThreads, 2)
+__global__ void __launch_bounds__(kP2GDsThreads, 3)
     k_p2g_ds_boxes(const GridDsBox *__restrict__ boxes, const int *__restrict__ base, int nbox)
 {
     const int b = find_box(base, nbox, (int)blockIdx.x);

@@ -11,6 +11,7 @@
 // inputs cost no padding.
 #include <math.h>
 
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -22,8 +23,9 @@ namespace {
 struct KeyArgs {
     const double *x, *f;
     int64_t N;
-    double L, inv_L, inv_cell, cell, inv_h, half_odd;
-    int nc, M, T, nt, ceilP2;
+    double L, inv_L, cell, fix_scale;  // fix_scale = 2^62 / L
+    long long L_bits;                  // bit pattern of L
+    int nc, M, T, nt, ceilP2, odd_P;
     int32_t *keyn, *slotn, *keyt, *slott, *cntn, *cntt, *permn, *permt;
     int ncntn, ncntt;  // lengths of cntn and cntt
     const int32_t *startn, *startt;
@@ -40,11 +42,17 @@ __device__ __forceinline__ void store_force_ds(float4 *t, double fx, double fy, 
     t[1] = make_float4((float)(fx - (double)hx), (float)(fy - (double)hy), (float)(fz - (double)hz), 0.f);
 }
 
+// A point's bins, computed in fixed point: the wrapped coordinate as
+// X = floor(x 2^62 / L) (two FP64 operations a coordinate; everything after
+// them is integer arithmetic, GB300's FP64 rate being 1/64 of its FP32 rate).
+// With A = 4 X (the box as [0, 2^64)), the near cell is the high word of
+// A n_c and the position within it the low word (a fraction times 2^64); the
+// grid coordinate x/h + (P odd)/2 is A M (+ 2^63) likewise.
 struct Bin {
-    double xw[3];      // wrapped position in [0, L)
+    uint64_t fc[3];    // position within the near cell, times 2^64
+    uint64_t fg[3];    // fractional grid offset delta of the anchor, times 2^64
     int c[3], s[3];    // near cell and sub-cell
     int a[3], tl[3];   // window anchor (wrapped) and its tile
-    double delta[3];   // fractional grid offset of the anchor
     bool bad;
 };
 
@@ -59,21 +67,28 @@ __device__ __forceinline__ Bin compute_bin(const KeyArgs &k, int64_t i)
             b.bad = true;
             v = 0.0;
         }
-        // wrap into [0, L) (positions already inside skip it: FP64 runs at a
-        // small fraction of the FP32 rate here, and binning is FP64-bound)
-        v = wrap_coord(v, k.L, k.inv_L);
-        b.xw[d] = v;
-        double q = v * k.inv_cell;
-        int ci = min(max((int)q, 0), k.nc - 1);
-        int si = min(max((int)((q - ci) * kSub), 0), kSub - 1);
+        // wrap into [0, L) unless already inside (a test on the bit pattern:
+        // non-negative doubles order as their bits)
+        const long long vb = __double_as_longlong(v);
+        if (!(vb >= 0 && vb < k.L_bits))
+            v = wrap_coord(v, k.L, k.inv_L);
+        const uint64_t X = min(__double2ull_rz(v * k.fix_scale), (1ull << 62) - 1ull);
+        const uint64_t A = X << 2;
+        const int ci = (int)__umul64hi(A, (uint64_t)k.nc);  // <= nc - 1 as A < 2^64
+        const uint64_t fc = A * (uint64_t)k.nc;
         b.c[d] = ci;
-        b.s[d] = si;
+        b.s[d] = (int)__umul64hi(fc, (uint64_t)kSub);
+        b.fc[d] = fc;
         // window anchor (Sec. 2.2): a = floor(y/h + (P odd)/2) - ceil(P/2) + 1,
         // the P support points are a + l, l = 0..P-1
-        double sg = v * k.inv_h + k.half_odd;
-        double fl = floor(sg);
-        b.delta[d] = sg - fl;
-        int ai = ((int)fl - k.ceilP2 + 1) % k.M;
+        uint64_t gi = __umul64hi(A, (uint64_t)k.M), fg = A * (uint64_t)k.M;
+        if (k.odd_P) {
+            const uint64_t f2 = fg + (1ull << 63);
+            gi += f2 < fg ? 1ull : 0ull;
+            fg = f2;
+        }
+        b.fg[d] = fg;
+        int ai = ((int)gi - k.ceilP2 + 1) % k.M;
         if (ai < 0)
             ai += k.M;
         b.a[d] = ai;
@@ -98,6 +113,21 @@ __device__ __forceinline__ void bin_keys_body(const KeyArgs &k, int64_t i)
     k.slott[i] = atomicAdd(&k.cntt[kt], 1);
 }
 
+// a fraction held as a 64-bit word (times 2^64) in [0, 1]: its top 32 bits
+// (FP32), or 53 bits (FP64)
+template <typename R>
+__device__ __forceinline__ R frac64(uint64_t f);
+template <>
+__device__ __forceinline__ float frac64<float>(uint64_t f)
+{
+    return __uint2float_rn((unsigned)(f >> 32)) * 2.3283064365386963e-10f;
+}
+template <>
+__device__ __forceinline__ double frac64<double>(uint64_t f)
+{
+    return __ull2double_rn(f >> 11) * 1.1102230246251565e-16;
+}
+
 template <typename R, typename R4>
 __device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
 {
@@ -119,10 +149,13 @@ __device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
         uint64_t hq[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double q = b.xw[d] * k.inv_cell - b.c[d];
-            const double X = rint(q * 1048576.0);
-            hq[d] = (uint64_t)X;  // 0 .. 2^20
-            lo[d] = (float)(q - X * (1.0 / 1048576.0));
+            // hi = the fraction rounded to 20 bits (0 .. 2^20), lo = the rest
+            // (|lo| <= 2^43 units of 2^-64, exact as a signed word; the word
+            // wraps when hi = 2^20), converted from two exact halves
+            const uint64_t fc = b.fc[d];
+            hq[d] = (fc >> 44) + ((fc >> 43) & 1ull);
+            const long long lw = (long long)(fc - (hq[d] << 44));
+            lo[d] = fmaf((float)(int)(lw >> 21), 2097152.f, (float)(int)(lw & 0x1FFFFFll)) * 5.421010862427522e-20f;
         }
         const uint64_t packed = hq[0] | (hq[1] << 21) | (hq[2] << 42);
         float fx = 0.f, fy = 0.f, fz = 0.f;  // set_positions: forces come later
@@ -143,9 +176,9 @@ __device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
         }
     } else {
         R4 pos;
-        pos.x = (R)(b.xw[0] - b.c[0] * k.cell);
-        pos.y = (R)(b.xw[1] - b.c[1] * k.cell);
-        pos.z = (R)(b.xw[2] - b.c[2] * k.cell);
+        pos.x = (R)(__ull2double_rn(b.fc[0]) * 5.421010862427522e-20 * k.cell);
+        pos.y = (R)(__ull2double_rn(b.fc[1]) * 5.421010862427522e-20 * k.cell);
+        pos.z = (R)(__ull2double_rn(b.fc[2]) * 5.421010862427522e-20 * k.cell);
         pos.w = (R)0;
         ((R4 *)k.npos)[pn] = pos;
     }
@@ -153,9 +186,9 @@ __device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
     int packed = (b.a[0] - b.tl[0] * k.T) | ((b.a[1] - b.tl[1] * k.T) << 4) |
                  ((b.a[2] - b.tl[2] * k.T) << 8);
     R4 td;
-    td.x = (R)b.delta[0];
-    td.y = (R)b.delta[1];
-    td.z = (R)b.delta[2];
+    td.x = frac64<R>(b.fg[0]);
+    td.y = frac64<R>(b.fg[1]);
+    td.z = frac64<R>(b.fg[2]);
     td.w = (R)packed;  // small integer, exact in FP32 and FP64
     tdat[pt] = td;
     k.permt[pt] = (int32_t)i;
@@ -399,9 +432,9 @@ KeyArgs key_args(ewald_plan_s *p, const BinArgs &a)
     k.L = a.L;
     k.inv_L = 1.0 / a.L;
     k.cell = a.cell;
-    k.inv_cell = 1.0 / a.cell;
-    k.inv_h = 1.0 / a.h;
-    k.half_odd = (a.P % 2) ? 0.5 : 0.0;
+    k.fix_scale = 4611686018427387904.0 / a.L;  // 2^62 / L
+    std::memcpy(&k.L_bits, &a.L, sizeof(double));
+    k.odd_P = a.P % 2;
     k.nc = a.nc;
     k.M = a.M;
     k.T = a.T;

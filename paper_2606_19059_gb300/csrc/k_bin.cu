@@ -63,13 +63,14 @@ __device__ __forceinline__ Bin compute_bin(const KeyArgs &k, int64_t i)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         double v = k.x[3 * i + d];
-        if (!isfinite(v)) {
+        long long vb = __double_as_longlong(v);
+        if (((vb >> 52) & 0x7FF) == 0x7FF) {  // Inf or NaN
             b.bad = true;
             v = 0.0;
+            vb = 0;
         }
         // wrap into [0, L) unless already inside (a test on the bit pattern:
         // non-negative doubles order as their bits)
-        const long long vb = __double_as_longlong(v);
         if (!(vb >= 0 && vb < k.L_bits))
             v = wrap_coord(v, k.L, k.inv_L);
         const uint64_t X = min(__double2ull_rz(v * k.fix_scale), (1ull << 62) - 1ull);
@@ -137,6 +138,12 @@ __device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
     int pn = k.startn[k.keyn[i]] + k.slotn[i];
     int pt = k.startt[k.keyt[i]] + k.slott[i];
     R4 *tdat = (R4 *)k.tdat, *tfrc = (R4 *)k.tfrc;
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;  // set_positions: forces come later
+    if (k.f) {
+        f0 = k.f[3 * i];
+        f1 = k.f[3 * i + 1];
+        f2 = k.f[3 * i + 2];
+    }
     if (k.nrec) {
         // FP32 near record (32 bytes): cell-local position in cell units split
         // hi + lo, hi on a 2^-20 lattice stored as three 21-bit integers
@@ -158,20 +165,14 @@ __device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
             lo[d] = fmaf((float)(int)(lw >> 21), 2097152.f, (float)(int)(lw & 0x1FFFFFll)) * 5.421010862427522e-20f;
         }
         const uint64_t packed = hq[0] | (hq[1] << 21) | (hq[2] << 42);
-        float fx = 0.f, fy = 0.f, fz = 0.f;  // set_positions: forces come later
-        if (k.f) {
-            fx = (float)k.f[3 * i];
-            fy = (float)k.f[3 * i + 1];
-            fz = (float)k.f[3 * i + 2];
-        }
+        const float fx = (float)f0, fy = (float)f1, fz = (float)f2;
         float4 *rec = (float4 *)k.nrec + 2 * (int64_t)pn;
         rec[0] = make_float4(lo[0], lo[1], lo[2], fx);
         rec[1] = make_float4(fy, fz, __uint_as_float((unsigned)packed), __uint_as_float((unsigned)(packed >> 32)));
         if (k.nflo) {  // double-single P2P: the forces' FP32 rounding errors
             float4 fl = make_float4(0.f, 0.f, 0.f, 0.f);
             if (k.f)
-                fl = make_float4((float)(k.f[3 * i] - (double)fx), (float)(k.f[3 * i + 1] - (double)fy),
-                                 (float)(k.f[3 * i + 2] - (double)fz), 0.f);
+                fl = make_float4((float)(f0 - (double)fx), (float)(f1 - (double)fy), (float)(f2 - (double)fz), 0.f);
             ((float4 *)k.nflo)[pn] = fl;
         }
     } else {
@@ -194,14 +195,14 @@ __device__ __forceinline__ void bin_scatter_body(const KeyArgs &k, int64_t i)
     k.permt[pt] = (int32_t)i;
     if (k.f) {
         R4 fv;
-        fv.x = (R)k.f[3 * i];
-        fv.y = (R)k.f[3 * i + 1];
-        fv.z = (R)k.f[3 * i + 2];
+        fv.x = (R)f0;
+        fv.y = (R)f1;
+        fv.z = (R)f2;
         fv.w = (R)0;
         if (!k.nrec)
             ((R4 *)k.nfrc)[pn] = fv;
         if (k.tf_ds)
-            store_force_ds((float4 *)k.tfrc + 2 * (int64_t)pt, k.f[3 * i], k.f[3 * i + 1], k.f[3 * i + 2]);
+            store_force_ds((float4 *)k.tfrc + 2 * (int64_t)pt, f0, f1, f2);
         else
             tfrc[pt] = fv;
     }

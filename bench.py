@@ -682,6 +682,16 @@ def main():
         }
         for k in ("scale", "fft", "ifft"):
             stage_roof[k]["frac"] = stage_roof[k]["achieved"] / hbm
+        if not prm["fft_f64"] and M in (64, 128, 256):
+            # FP32 spectra at these M: 2-D (y, x) transforms of the 3 M planes
+            # around one kernel for the z transforms and the CNV
+            stage_roof["fft"]["kernel"] = "cuFFT 2-D R2C of the 3 M (y, x) planes"
+            stage_roof["scale"]["kernel"] = "k_fgc_z: z FFT, CNV (eq. (sca)) and z IFFT, spectrum read and written once"
+            stage_roof["ifft"]["kernel"] = "cuFFT 2-D C2R of the 3 M (y, x) planes"
+        else:
+            stage_roof["fft"]["kernel"] = "cuFFT 3-D R2C"
+            stage_roof["scale"]["kernel"] = "k_scale: CNV (eq. (sca))"
+            stage_roof["ifft"]["kernel"] = "cuFFT 3-D C2R"
         # P2G / G2P: intensity far above the HBM ridge, so the binding fraction
         # is the FP32 pipe; the algorithmic HBM rate is reported beside it.
         # P2G per source: 3 P nu Horner FMAs, P^2 + P^3 weight products,

@@ -97,7 +97,11 @@ typedef struct {
  * field, so the stages do not add up to total_ms.  In a combined apply
  * (ewald_apply_combined) p2p_ms includes the double layer's FP32 near field
  * (FP32 plans) and sum_ms its FP64 near field (the other plans); p2g_ms
- * covers the spreading of all nine components. */
+ * covers the spreading of all nine components.  Plans with FP32 spectra and
+ * M in {64, 128, 256} run the FFT as a 2-D (y, x) transform of each z plane
+ * (fft_ms), the z transforms and the CNV in one kernel (scale_ms) and the
+ * inverse 2-D transforms (ifft_ms); a combined apply keeps the 3-D
+ * transforms and the separate CNV. */
 typedef struct {
     float bin_ms, p2p_ms, p2g_ms, fft_ms, scale_ms, ifft_ms, g2p_ms, sum_ms, total_ms;
 } ewald_stage_timing;

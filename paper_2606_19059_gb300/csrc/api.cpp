@@ -147,10 +147,14 @@ void free_plan(ewald_plan_s *p)
         cufftDestroy(p->fwd);
     if (p->have_inv)
         cufftDestroy(p->inv);
+    if (p->have_fwd2)
+        cufftDestroy(p->fwd2);
+    if (p->have_inv2)
+        cufftDestroy(p->inv2);
     void *bufs[] = {p->keyn, p->slotn, p->keyt,  p->slott, p->cntn, p->startn, p->cntt,
                     p->startt, p->items, p->item_off, p->permn, p->permt, p->npos, p->nlo, p->nfrc, p->nrec, p->nflo,
                     p->tdat, p->tfrc, p->un, p->uf, p->tab, p->wcoef_dev,
-                    p->err, p->hx, p->hf, p->hu, p->fftwork, p->wts, p->dl_tf, p->dl_grid, p->dl_spec, p->dl_near};
+                    p->err, p->hx, p->hf, p->hu, p->fftwork, p->twz, p->wts, p->dl_tf, p->dl_grid, p->dl_spec, p->dl_near};
     for (void *b : bufs)
         dfree(p, b);
     if (!p->ext_grid) {  // a batch's grouped FFT buffers belong to the batch
@@ -309,10 +313,38 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_FFT(cufftSetAutoAllocation(p->inv, 0));
     EW_FFT(cufftMakePlanMany(p->inv, 3, n3, inembed_c, 1, (int)g.ncplx, inembed_r, 1,
                              (int)g.nreal, p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3, &wsi));
-    EW_CUDA(dalloc(p, &p->fftwork, std::max(wsf, wsi)));
+    size_t ws = std::max(wsf, wsi);
+    if (!p->fft64 && fgc_z_supported(g.M)) {
+        // 2-D (y, x) transforms of the 3 M planes, z left to the fused kernel
+        int n2[2] = {g.M, g.M}, er2[2] = {g.M, g.M}, ec2[2] = {g.M, g.Mh};
+        size_t w2f = 0, w2i = 0;
+        EW_FFT(cufftCreate(&p->fwd2));
+        p->have_fwd2 = true;
+        EW_FFT(cufftSetAutoAllocation(p->fwd2, 0));
+        EW_FFT(cufftMakePlanMany(p->fwd2, 2, n2, er2, 1, g.M * g.M, ec2, 1, g.M * g.Mh, CUFFT_R2C, 3 * g.M, &w2f));
+        EW_FFT(cufftCreate(&p->inv2));
+        p->have_inv2 = true;
+        EW_FFT(cufftSetAutoAllocation(p->inv2, 0));
+        EW_FFT(cufftMakePlanMany(p->inv2, 2, n2, ec2, 1, g.M * g.Mh, er2, 1, g.M * g.M, CUFFT_C2R, 3 * g.M, &w2i));
+        ws = std::max(ws, std::max(w2f, w2i));
+        std::vector<float> tw(2 * (size_t)g.M);
+        for (int j = 0; j < g.M; ++j) {  // w_M^j = e^{-2 pi i j / M}
+            tw[2 * j] = (float)cos(2.0 * kPi * j / g.M);
+            tw[2 * j + 1] = (float)-sin(2.0 * kPi * j / g.M);
+        }
+        EW_CUDA(dalloc(p, &p->twz, sizeof(float) * tw.size()));
+        EW_CUDA(cudaStreamSynchronize(p->s2));
+        EW_CUDA(cudaMemcpy(p->twz, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice));
+        p->fgc_fused = true;
+    }
+    EW_CUDA(dalloc(p, &p->fftwork, ws));
     EW_CUDA(cudaStreamSynchronize(p->s2));
     EW_FFT(cufftSetWorkArea(p->fwd, p->fftwork));
     EW_FFT(cufftSetWorkArea(p->inv, p->fftwork));
+    if (p->fgc_fused) {
+        EW_FFT(cufftSetWorkArea(p->fwd2, p->fftwork));
+        EW_FFT(cufftSetWorkArea(p->inv2, p->fftwork));
+    }
 
     EW_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     EW_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
@@ -372,6 +404,18 @@ void rec(ewald_plan_s *p, int i, cudaStream_t s)
 // their v-hat added in the CNV (Sec. 2.3).
 ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s, bool dl = false)
 {
+    if (p->fgc_fused && !dl) {
+        // 2-D R2C of the 3 M planes, z-FFT + CNV + z-IFFT in one kernel, 2-D C2R
+        EW_FFT(cufftSetStream(p->fwd2, s));
+        EW_FFT(cufftSetStream(p->inv2, s));
+        EW_FFT(cufftExecR2C(p->fwd2, (cufftReal *)p->grid, (cufftComplex *)p->spec));
+        rec(p, 3, s);
+        EW_CUDA(launch_fgc_z(p, C, s));
+        rec(p, 4, s);
+        EW_FFT(cufftExecC2R(p->inv2, (cufftComplex *)p->spec, (cufftReal *)p->grid));
+        rec(p, 5, s);
+        return EWALD_OK;
+    }
     EW_FFT(cufftSetStream(p->fwd, s));
     EW_FFT(cufftSetStream(p->inv, s));
     const int ntr = dl ? 3 : 1;

@@ -178,7 +178,13 @@ struct ewald_plan_s {
 
     cufftHandle fwd = 0, inv = 0;
     bool have_fwd = false, have_inv = false;
-    void *fftwork = nullptr;                      // shared cuFFT work area (both plans)
+    // FP32 spectra, M in {64, 128, 256}: 2-D (y, x) transforms of the 3 M
+    // planes around the fused z-FFT / CNV / z-IFFT kernel (k_fgc_z.cu); the
+    // 3-D plans stay for the double layer's transforms
+    cufftHandle fwd2 = 0, inv2 = 0;
+    bool have_fwd2 = false, have_inv2 = false, fgc_fused = false;
+    void *twz = nullptr;                          // w_M^j, j < M (FP32 complex)
+    void *fftwork = nullptr;                      // shared cuFFT work area (every plan)
     bool pooled = false;                          // workspaces from the stream-ordered pool
     cudaStream_t s2 = nullptr;                    // second stream: P2P alongside the far field
     cudaStream_t s3 = nullptr;                    // origin stream of the applies' graph captures
@@ -253,6 +259,8 @@ cudaError_t launch_p2p_dl32(ewald_plan_s *p, const void *drec, cudaStream_t s);
 cudaError_t launch_p2p_dl(ewald_plan_s *p, const double *x, const double *q, const double *n, double *u,
                           cudaStream_t s);
 cudaError_t launch_scale(ewald_plan_s *p, double C, cudaStream_t s);
+bool fgc_z_supported(int M);
+cudaError_t launch_fgc_z(ewald_plan_s *p, double C, cudaStream_t s);
 // G2P from a grid in the kernels' precision (FP64 when near64, else FP32; the
 // double-single planes for grid_ds plans); the sum is multiplied by `scale`.
 cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s);

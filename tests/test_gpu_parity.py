@@ -107,7 +107,10 @@ def test_spread_interp_adjoint_on_gpu():
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-@pytest.mark.parametrize("dtype,M,bound", [(F64, 32, 1e-12), (F64, 36, 1e-12), (F32, 32, 2e-6)])
+# FP32 at M = 64, 128 and 256: 2-D (y, x) transforms around one kernel for
+# the z transforms and the CNV; M = 32: the 3-D transforms and the CNV pass
+@pytest.mark.parametrize("dtype,M,bound", [(F64, 32, 1e-12), (F64, 36, 1e-12), (F32, 32, 2e-6), (F32, 64, 2e-6),
+                                           (F32, 128, 3e-6), (F32, 256, 4e-6)])
 def test_fourier_convolve_matches_numpy(dtype, M, bound):
     rng = np.random.default_rng(106)
     P = 8

@@ -100,8 +100,8 @@ typedef struct {
  * covers the spreading of all nine components.  Plans with FP32 spectra and
  * M in {64, 128, 256} run the FFT as a 2-D (y, x) transform of each z plane
  * (fft_ms), the z transforms and the CNV in one kernel (scale_ms) and the
- * inverse 2-D transforms (ifft_ms); a combined apply keeps the 3-D
- * transforms and the separate CNV. */
+ * inverse 2-D transforms (ifft_ms), in a combined apply with the double
+ * layer's six density components transformed and scaled alongside. */
 typedef struct {
     float bin_ms, p2p_ms, p2g_ms, fft_ms, scale_ms, ifft_ms, g2p_ms, sum_ms, total_ms;
 } ewald_stage_timing;

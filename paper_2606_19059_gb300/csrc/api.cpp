@@ -404,13 +404,17 @@ void rec(ewald_plan_s *p, int i, cudaStream_t s)
 // their v-hat added in the CNV (Sec. 2.3).
 ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s, bool dl = false)
 {
-    if (p->fgc_fused && !dl) {
-        // 2-D R2C of the 3 M planes, z-FFT + CNV + z-IFFT in one kernel, 2-D C2R
+    if (p->fgc_fused) {
+        // 2-D R2C of the 3 M planes (and of the double layer's two density
+        // triples), z-FFT + CNV + z-IFFT in one kernel, 2-D C2R
         EW_FFT(cufftSetStream(p->fwd2, s));
         EW_FFT(cufftSetStream(p->inv2, s));
         EW_FFT(cufftExecR2C(p->fwd2, (cufftReal *)p->grid, (cufftComplex *)p->spec));
+        for (int t = 0; dl && t < 2; ++t)
+            EW_FFT(cufftExecR2C(p->fwd2, (cufftReal *)p->dl_grid + 3 * p->g.nreal * t,
+                                (cufftComplex *)p->dl_spec + 3 * p->g.ncplx * t));
         rec(p, 3, s);
-        EW_CUDA(launch_fgc_z(p, C, s));
+        EW_CUDA(dl ? launch_fgc_z_dl(p, C, s) : launch_fgc_z(p, C, s));
         rec(p, 4, s);
         EW_FFT(cufftExecC2R(p->inv2, (cufftComplex *)p->spec, (cufftReal *)p->grid));
         rec(p, 5, s);

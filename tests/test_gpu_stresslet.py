@@ -107,6 +107,26 @@ def test_combined_fp32_other_tile_and_odd_support(tile, P):
     assert l2 < 1e-6 and mx < 1e-6, (l2, mx)
 
 
+@pytest.mark.parametrize("M", [64, 256])
+def test_combined_fp32_z_kernels_at_other_grid_sizes(M):
+    # FP32 spectra at M = 64 and 256 take the 2-D transforms around the z
+    # kernels (Stokeslet alone, and with the double layer's nine components),
+    # whose splits M = R1 R2 and block shapes differ from M = 128's
+    N = 1500
+    x, f, q, n = _case("uniform", N, 410)
+    p = ewald.Plan(N, 1.0, 1e-6, F32, M=M, P=12)
+    assert p.params.fft_f64 == 0 and p.params.M == M and p.params.tile == 8
+    tid = np.arange(0, N, 13)
+    ref_s = oracle.ewald(x, f, 1.0, targets=tid)
+    us = host(p.apply(dev(x), dev(f)))
+    l2, mx = errs(us[tid], ref_s)
+    assert l2 < 1e-6 and mx < 1e-6, (l2, mx)
+    u = _combined(p, x, f, q, n)
+    ref = ref_s + dl.ewald(x, dl.densities(q, n), 1.0, targets=tid)
+    l2, mx = errs(u[tid], ref)
+    assert l2 < 1e-6 and mx < 1e-6, (l2, mx)
+
+
 def test_double_layer_fp32_pairs_fp64_fft_two_cells_per_side():
     # FP32 bulk at 1e-7 < tol < 1e-6: FP32 densities spread onto FP64 grids,
     # FP64 CNV and FP64 near-field pairs; n_c = 2, so the 27 neighbour offsets

@@ -65,17 +65,45 @@ def test_near_field_small_box_explicit_images():
     assert errs(u, ref)[1] < 1e-11
 
 
+def _support_sums(x, f, L, M, P):
+    """Per grid point g and component c: n(g), the number of points whose
+    window support (|g_d - x_d| < P h / 2 on every axis, periodic) holds g, and
+    A_c(g), the sum of |f_c| over them."""
+    h = L / M
+    grid = np.arange(M) * h
+    ins = []
+    for d in range(3):
+        r = np.abs(grid[None, :] - np.mod(x[:, d], L)[:, None])
+        ins.append((np.minimum(r, L - r) < P * h / 2).astype(np.float64))
+    n = np.einsum("pi,pj,pk->ijk", ins[2], ins[1], ins[0])
+    A = np.stack([np.einsum("p,pi,pj,pk->ijk", np.abs(f[:, c]), ins[2], ins[1], ins[0]) for c in range(3)])
+    return n, A
+
+
 # FP32 P2G evaluates bins l and P-1-l from bin l's even and odd parts: odd P
-# (a bin on the axis of symmetry) and even P both
+# (a bin on the axis of symmetry) and even P both.
+# Bound, per grid point and component: each term w_x w_y w_z f_c carries three
+# window values off by at most werr (the polynomial against the exact window)
+# and, in the kernels' precision u, the rounding of a degree-nu polynomial in
+# its even/odd form (2 nu + 2 roundings) and of the products (2 more); the n(g)
+# terms are then summed in an order the kernel does not fix (first-order
+# forward error of a sum: (n - 1) u times the sum of the terms' sizes).  So
+# |g - ref| <= 3 werr A(g) + (2 nu + 4 + n(g)) u B(g), B = spread of |f|
+# (the window is nonnegative).
 @pytest.mark.parametrize("dtype,P,M", [(F64, 8, 32), (F64, 7, 24), (F32, 12, 32), (F32, 11, 32), (F32, 7, 24)])
 def test_spread_matches_exact_window(dtype, P, M):
     x, f = workloads.make("uniform", 400, seed=103)
     p = plan(400, 1.0, 1e-8 if dtype == F64 else 1e-6, dtype, M=M, P=P)
     g = host(p.spread(dev(x), dev(f)))
     ref = spectral.spread(x, f, 1.0, M, P)
+    B = spectral.spread(x, np.abs(f), 1.0, M, P)
+    n, A = _support_sums(x, f, 1.0, M, P)
     _, werr = ewald.ewald_window_eval(P, p.params.poly_deg, np.zeros(1))
-    bound = 3 * werr * np.abs(f).max() + (2e-7 if dtype == F32 else 1e-14) * np.abs(ref).max()
-    assert np.abs(g - ref).max() <= bound, (np.abs(g - ref).max(), bound)
+    u = 2.0 ** -24 if dtype == F32 else 2.0 ** -53
+    bound = 3 * werr * A + (2 * p.params.poly_deg + 4 + n[None]) * u * B + 1e-300
+    err = np.abs(g - ref)
+    assert np.all(err <= bound), (err.max(), (err / bound).max())
+    assert n.max() > 0 and err.max() < 1e-3 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("dtype", [F64, F32])

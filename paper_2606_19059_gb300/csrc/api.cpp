@@ -314,24 +314,43 @@ ewald_status make_plan(ewald_plan_s *p)
     EW_FFT(cufftMakePlanMany(p->inv, 3, n3, inembed_c, 1, (int)g.ncplx, inembed_r, 1,
                              (int)g.nreal, p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3, &wsi));
     size_t ws = std::max(wsf, wsi);
-    if (!p->fft64 && fgc_z_supported(g.M)) {
+    if (fgc_z_supported(g.M)) {
         // 2-D (y, x) transforms of the 3 M planes, z left to the fused kernel
         int n2[2] = {g.M, g.M}, er2[2] = {g.M, g.M}, ec2[2] = {g.M, g.Mh};
         size_t w2f = 0, w2i = 0;
         EW_FFT(cufftCreate(&p->fwd2));
         p->have_fwd2 = true;
         EW_FFT(cufftSetAutoAllocation(p->fwd2, 0));
-        EW_FFT(cufftMakePlanMany(p->fwd2, 2, n2, er2, 1, g.M * g.M, ec2, 1, g.M * g.Mh, CUFFT_R2C, 3 * g.M, &w2f));
+        EW_FFT(cufftMakePlanMany(p->fwd2, 2, n2, er2, 1, g.M * g.M, ec2, 1, g.M * g.Mh,
+                                 p->fft64 ? CUFFT_D2Z : CUFFT_R2C, 3 * g.M, &w2f));
         EW_FFT(cufftCreate(&p->inv2));
         p->have_inv2 = true;
         EW_FFT(cufftSetAutoAllocation(p->inv2, 0));
-        EW_FFT(cufftMakePlanMany(p->inv2, 2, n2, ec2, 1, g.M * g.Mh, er2, 1, g.M * g.M, CUFFT_C2R, 3 * g.M, &w2i));
+        EW_FFT(cufftMakePlanMany(p->inv2, 2, n2, ec2, 1, g.M * g.Mh, er2, 1, g.M * g.M,
+                                 p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3 * g.M, &w2i));
         ws = std::max(ws, std::max(w2f, w2i));
-        std::vector<float> tw(2 * (size_t)g.M);
-        for (int j = 0; j < g.M; ++j) {  // w_M^j = e^{-2 pi i j / M}
-            tw[2 * j] = (float)cos(2.0 * kPi * j / g.M);
-            tw[2 * j + 1] = (float)-sin(2.0 * kPi * j / g.M);
+        // w_M^j = e^{-2 pi i j / M}: FP32 (re, im) for k_fgc_z; for the
+        // double-single k_fgc_z64 (re h, re l, im h, im l), then the CNV
+        // table as (h, l) pairs
+        std::vector<float> tw;
+        auto hl = [&tw](double v) {
+            const float h = (float)v;
+            tw.push_back(h);
+            tw.push_back((float)(v - (double)h));
+        };
+        for (int j = 0; j < g.M; ++j) {
+            const double c = cos(2.0 * kPi * j / g.M), sn = -sin(2.0 * kPi * j / g.M);
+            if (p->fft64) {
+                hl(c);
+                hl(sn);
+            } else {
+                tw.push_back((float)c);
+                tw.push_back((float)sn);
+            }
         }
+        if (p->fft64)
+            for (int i = 0; i < g.M; ++i)
+                hl(tab[i]);
         EW_CUDA(dalloc(p, &p->twz, sizeof(float) * tw.size()));
         EW_CUDA(cudaStreamSynchronize(p->s2));
         EW_CUDA(cudaMemcpy(p->twz, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice));
@@ -404,7 +423,20 @@ void rec(ewald_plan_s *p, int i, cudaStream_t s)
 // their v-hat added in the CNV (Sec. 2.3).
 ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s, bool dl = false)
 {
-    if (p->fgc_fused) {
+    if (p->fgc_fused && p->fft64 && !dl) {
+        // FP64 spectra: 2-D D2Z of the 3 M planes, the z transforms and the
+        // CNV in double-single arithmetic, 2-D Z2D
+        EW_FFT(cufftSetStream(p->fwd2, s));
+        EW_FFT(cufftSetStream(p->inv2, s));
+        EW_FFT(cufftExecD2Z(p->fwd2, (cufftDoubleReal *)p->grid, (cufftDoubleComplex *)p->spec));
+        rec(p, 3, s);
+        EW_CUDA(launch_fgc_z64(p, C, s));
+        rec(p, 4, s);
+        EW_FFT(cufftExecZ2D(p->inv2, (cufftDoubleComplex *)p->spec, (cufftDoubleReal *)p->grid));
+        rec(p, 5, s);
+        return EWALD_OK;
+    }
+    if (p->fgc_fused && !p->fft64) {
         // 2-D R2C of the 3 M planes (and of the double layer's two density
         // triples), z-FFT + CNV + z-IFFT in one kernel, 2-D C2R
         EW_FFT(cufftSetStream(p->fwd2, s));

@@ -370,6 +370,13 @@ def clustered_entry(c, peaks):
         gbs = by / (st[k + "_ms"] * 1e-3) / 1e9
         roof[k] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                    "bytes_per_launch": by}
+    if M in (64, 128, 256):
+        # 2-D (y, x) transforms of the 3 M planes around one kernel for the z
+        # transforms and the CNV (double-single arithmetic for FP64 spectra)
+        zk = "k_fgc_z64 (double-single)" if prm["fft_f64"] else "k_fgc_z"
+        roof["fft"]["kernel"] = "cuFFT 2-D " + ("D2Z" if prm["fft_f64"] else "R2C") + " of the 3 M (y, x) planes"
+        roof["scale"]["kernel"] = zk + ": z FFT, CNV (eq. (sca)) and z IFFT, spectrum read and written once"
+        roof["ifft"]["kernel"] = "cuFFT 2-D " + ("Z2D" if prm["fft_f64"] else "C2R") + " of the 3 M (y, x) planes"
     near = ("double-single" if prm["near_ds"] else ("FP64" if prm["near_f64"] else "FP32"))
     roof["p2p"] = {"inrange_pairs_est": inr, "pairs_per_s": inr / (st["p2p_ms"] * 1e-3),
                    "arithmetic": near + " pairs"}

@@ -315,19 +315,24 @@ ewald_status make_plan(ewald_plan_s *p)
                              (int)g.nreal, p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3, &wsi));
     size_t ws = std::max(wsf, wsi);
     if (fgc_z_supported(g.M)) {
-        // 2-D (y, x) transforms of the 3 M planes, z left to the fused kernel
+        // FP32: 2-D (y, x) transforms of the 3 M planes, z left to the fused
+        // kernel; FP64: 1-D transforms along x of the 3 M^2 rows, y and z
+        // left to the double-single kernels
         int n2[2] = {g.M, g.M}, er2[2] = {g.M, g.M}, ec2[2] = {g.M, g.Mh};
+        const int rank = p->fft64 ? 1 : 2, batch = p->fft64 ? 3 * g.M * g.M : 3 * g.M;
+        const int dr = p->fft64 ? g.M : g.M * g.M, dc = p->fft64 ? g.Mh : g.M * g.Mh;
+        int *nn = p->fft64 ? n2 + 1 : n2, *er = p->fft64 ? er2 + 1 : er2, *ec = p->fft64 ? ec2 + 1 : ec2;
         size_t w2f = 0, w2i = 0;
         EW_FFT(cufftCreate(&p->fwd2));
         p->have_fwd2 = true;
         EW_FFT(cufftSetAutoAllocation(p->fwd2, 0));
-        EW_FFT(cufftMakePlanMany(p->fwd2, 2, n2, er2, 1, g.M * g.M, ec2, 1, g.M * g.Mh,
-                                 p->fft64 ? CUFFT_D2Z : CUFFT_R2C, 3 * g.M, &w2f));
+        EW_FFT(cufftMakePlanMany(p->fwd2, rank, nn, er, 1, dr, ec, 1, dc, p->fft64 ? CUFFT_D2Z : CUFFT_R2C, batch,
+                                 &w2f));
         EW_FFT(cufftCreate(&p->inv2));
         p->have_inv2 = true;
         EW_FFT(cufftSetAutoAllocation(p->inv2, 0));
-        EW_FFT(cufftMakePlanMany(p->inv2, 2, n2, ec2, 1, g.M * g.Mh, er2, 1, g.M * g.M,
-                                 p->fft64 ? CUFFT_Z2D : CUFFT_C2R, 3 * g.M, &w2i));
+        EW_FFT(cufftMakePlanMany(p->inv2, rank, nn, ec, 1, dc, er, 1, dr, p->fft64 ? CUFFT_Z2D : CUFFT_C2R, batch,
+                                 &w2i));
         ws = std::max(ws, std::max(w2f, w2i));
         // w_M^j = e^{-2 pi i j / M}: FP32 (re, im) for k_fgc_z; for the
         // double-single k_fgc_z64 (re h, re l, im h, im l), then the CNV
@@ -424,14 +429,17 @@ void rec(ewald_plan_s *p, int i, cudaStream_t s)
 ewald_status fgc(ewald_plan_s *p, double C, cudaStream_t s, bool dl = false)
 {
     if (p->fgc_fused && p->fft64 && !dl) {
-        // FP64 spectra: 2-D D2Z of the 3 M planes, the z transforms and the
-        // CNV in double-single arithmetic, 2-D Z2D
+        // FP64 spectra: 1-D D2Z along x of the 3 M^2 rows, the y transforms,
+        // the z transforms with the CNV and the inverse y transforms in
+        // double-single arithmetic, 1-D Z2D along x
         EW_FFT(cufftSetStream(p->fwd2, s));
         EW_FFT(cufftSetStream(p->inv2, s));
         EW_FFT(cufftExecD2Z(p->fwd2, (cufftDoubleReal *)p->grid, (cufftDoubleComplex *)p->spec));
+        EW_CUDA(launch_fft_y64(p, false, s));
         rec(p, 3, s);
         EW_CUDA(launch_fgc_z64(p, C, s));
         rec(p, 4, s);
+        EW_CUDA(launch_fft_y64(p, true, s));
         EW_FFT(cufftExecZ2D(p->inv2, (cufftDoubleComplex *)p->spec, (cufftDoubleReal *)p->grid));
         rec(p, 5, s);
         return EWALD_OK;

@@ -178,10 +178,11 @@ struct ewald_plan_s {
 
     cufftHandle fwd = 0, inv = 0;
     bool have_fwd = false, have_inv = false;
-    // M in {64, 128, 256}: 2-D (y, x) transforms of the 3 M planes around the
-    // fused z-FFT / CNV / z-IFFT kernels (k_fgc_z.cu for FP32 spectra, the
-    // double layer's two density triples through the same 2-D plan;
-    // k_fgc_z64.cu for FP64 spectra, the Stokeslet alone)
+    // M in {64, 128, 256}: FP32 spectra, 2-D (y, x) transforms of the 3 M
+    // planes around the fused z-FFT / CNV / z-IFFT kernels (k_fgc_z.cu; the
+    // double layer's two density triples through the same 2-D plan); FP64
+    // spectra, the Stokeslet alone, 1-D transforms along x of the 3 M^2 rows
+    // around the double-single y and z kernels (k_fgc_z64.cu)
     cufftHandle fwd2 = 0, inv2 = 0;
     bool have_fwd2 = false, have_inv2 = false, fgc_fused = false;
     void *twz = nullptr;                          // w_M^j, j < M (FP32 complex; FP64 spectra:
@@ -267,6 +268,9 @@ cudaError_t launch_fgc_z(ewald_plan_s *p, double C, cudaStream_t s);
 cudaError_t launch_fgc_z_dl(ewald_plan_s *p, double C, cudaStream_t s);
 // FP64 spectra: the z transforms and the CNV in double-single arithmetic (k_fgc_z64.cu)
 cudaError_t launch_fgc_z64(ewald_plan_s *p, double C, cudaStream_t s);
+// FP64 spectra: the y transforms (forward or inverse) in double-single
+// arithmetic, between cuFFT's 1-D transforms along x and the z kernel
+cudaError_t launch_fft_y64(ewald_plan_s *p, bool inv, cudaStream_t s);
 // G2P from a grid in the kernels' precision (FP64 when near64, else FP32; the
 // double-single planes for grid_ds plans); the sum is multiplied by `scale`.
 cudaError_t launch_g2p(ewald_plan_s *p, const void *grid, double scale, cudaStream_t s);

@@ -1,7 +1,8 @@
 // k_fgc_z64.cu -- steps a3-a5 around the k-space scaling (CNV, eq. (sca)) for
-// FP64 spectra (the plans of tol < 1e-6) with M in {64, 128, 256}: the z
-// transforms and the CNV of k_fgc_z.cu, in double-single arithmetic, between
-// a 2-D (y, x) D2Z and a 2-D Z2D of cuFFT over the 3 M planes.
+// FP64 spectra (the plans of tol < 1e-6) with M in {64, 128, 256}: the y
+// transforms (k_fft_y64), and the z transforms with the CNV of k_fgc_z.cu
+// (k_fgc_z64), in double-single arithmetic, between cuFFT's 1-D D2Z and Z2D
+// along x of the 3 M^2 rows.
 //
 // GB300's FP64 pipe runs at 1/64 of its FP32 rate, and cuFFT's FP64
 // transforms are bound by it.  Values here are unevaluated sums h + l of two
@@ -285,6 +286,111 @@ __global__ void __launch_bounds__(kZ64Threads) k_fgc_z64(double2 *__restrict__ s
     }
 }
 
+// The y transforms of FP64 spectra in the same arithmetic: after cuFFT's 1-D
+// D2Z along x, every (component, z, k_x) column along y goes through the
+// length-M DFT (forward) or, after the z kernel, its inverse, so that of the
+// three transform directions only the real-to-complex one along x stays on
+// the FP64 pipe.  spec: [3 M][M][Mh] (plane, y, k_x); a block takes WY
+// consecutive columns (k_x fastest, a block may span two planes).  Forward,
+// with y = R2 n1 + n2 and k = k1 + R1 k2: a thread per (n2, column) runs the
+// length-R1 DFT and the twiddles into shared memory, a thread per (k1,
+// column) the length-R2 DFT and stores X[k1 + R1 k2].  Inverse, with
+// y = R2 a + b: a thread per (k1, column) loads X[k1 + R1 k2], runs the
+// inverse length-R2 DFT and the twiddles w_M^{-b k1}, a thread per (b,
+// column) the inverse length-R1 DFT and stores x[R2 a + b].
+template <int M, bool INV>
+__global__ void __launch_bounds__(kZ64Threads) k_fft_y64(double2 *__restrict__ spec, const float4 *__restrict__ tw)
+{
+    constexpr int R1 = ZSplit64<M>::R1, R2 = ZSplit64<M>::R2, WY = 3 * ZSplit64<M>::W, Mh = M / 2 + 1;
+    constexpr int S = R1 * WY + WY, NT = kZ64Threads;
+    static_assert((3 * M * Mh) % WY == 0, "the blocks tile the columns");
+    __shared__ float4 buf[R2 * S];  // slot (n2 or b, k1, w)
+    const int colb = blockIdx.x * WY;
+    auto column = [&](int w) {  // first element of column colb + w
+        const int col = colb + w, pz = col / Mh, kx = col - pz * Mh;
+        return spec + (int64_t)pz * M * Mh + kx;
+    };
+    if (!INV) {
+        for (int t = threadIdx.x; t < WY * R2; t += NT) {
+            const int w = t % WY, n2 = t / WY;
+            const double2 *src = column(w);
+            cds v[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) {
+                const double2 x = src[(R2 * n1 + n2) * Mh];
+                v[n1] = {split(x.x), split(x.y)};
+            }
+            dft_ds<R1, false>(v);
+            float4 *dst = buf + n2 * S + w;
+            dst[0] = pack(v[0]);
+#pragma unroll
+            for (int k1 = 1; k1 < R1; ++k1) {
+                const float4 q = tw[n2 * k1];
+                dst[k1 * WY] = pack(cmul(v[k1], {q.x, q.y}, {q.z, q.w}));
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < WY * R1; t += NT) {
+            const int w = t % WY, k1 = t / WY;
+            const float4 *col = buf + k1 * WY + w;
+            cds v[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2)
+                v[n2] = unpack(col[n2 * S]);
+            dft_ds<R2, false>(v);
+            double2 *dst = column(w);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2)
+                dst[(k1 + R1 * k2) * Mh] = make_double2(join(v[k2].re), join(v[k2].im));
+        }
+    } else {
+        for (int t = threadIdx.x; t < WY * R1; t += NT) {
+            const int w = t % WY, k1 = t / WY;
+            const double2 *src = column(w);
+            cds v[R2];
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                const double2 x = src[(k1 + R1 * k2) * Mh];
+                v[k2] = {split(x.x), split(x.y)};
+            }
+            dft_ds<R2, true>(v);
+            float4 *col = buf + k1 * WY + w;
+            col[0] = pack(v[0]);
+#pragma unroll
+            for (int b = 1; b < R2; ++b) {
+                const float4 q = tw[b * k1];
+                col[b * S] = pack(cmul(v[b], {q.x, q.y}, {-q.z, -q.w}));
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < WY * R2; t += NT) {
+            const int w = t % WY, b = t / WY;
+            const float4 *src = buf + b * S + w;
+            cds v[R1];
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1)
+                v[k1] = unpack(src[k1 * WY]);
+            dft_ds<R1, true>(v);
+            double2 *dst = column(w);
+#pragma unroll
+            for (int a = 0; a < R1; ++a)
+                dst[(R2 * a + b) * Mh] = make_double2(join(v[a].re), join(v[a].im));
+        }
+    }
+}
+
+template <int M>
+cudaError_t run_fft_y64(ewald_plan_s *p, bool inv, cudaStream_t s)
+{
+    constexpr int WY = 3 * ZSplit64<M>::W;
+    const int nb = 3 * M * (M / 2 + 1) / WY;
+    if (inv)
+        k_fft_y64<M, true><<<nb, kZ64Threads, 0, s>>>((double2 *)p->spec, (const float4 *)p->twz);
+    else
+        k_fft_y64<M, false><<<nb, kZ64Threads, 0, s>>>((double2 *)p->spec, (const float4 *)p->twz);
+    return cudaGetLastError();
+}
+
 float2 split_host(double v)
 {
     const float h = (float)v;
@@ -304,6 +410,20 @@ cudaError_t run_fgc_z64(ewald_plan_s *p, double C, cudaStream_t s)
 }
 
 }  // namespace
+
+cudaError_t launch_fft_y64(ewald_plan_s *p, bool inv, cudaStream_t s)
+{
+    switch (p->g.M) {
+    case 64:
+        return run_fft_y64<64>(p, inv, s);
+    case 128:
+        return run_fft_y64<128>(p, inv, s);
+    case 256:
+        return run_fft_y64<256>(p, inv, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_fgc_z64(ewald_plan_s *p, double C, cudaStream_t s)
 {

@@ -371,12 +371,17 @@ def clustered_entry(c, peaks):
         roof[k] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                    "bytes_per_launch": by}
     if M in (64, 128, 256):
-        # 2-D (y, x) transforms of the 3 M planes around one kernel for the z
-        # transforms and the CNV (double-single arithmetic for FP64 spectra)
-        zk = "k_fgc_z64 (double-single)" if prm["fft_f64"] else "k_fgc_z"
-        roof["fft"]["kernel"] = "cuFFT 2-D " + ("D2Z" if prm["fft_f64"] else "R2C") + " of the 3 M (y, x) planes"
-        roof["scale"]["kernel"] = zk + ": z FFT, CNV (eq. (sca)) and z IFFT, spectrum read and written once"
-        roof["ifft"]["kernel"] = "cuFFT 2-D " + ("Z2D" if prm["fft_f64"] else "C2R") + " of the 3 M (y, x) planes"
+        # FP32 spectra: 2-D (y, x) transforms of the 3 M planes around one
+        # kernel for the z transforms and the CNV; FP64 spectra: 1-D
+        # transforms along x, the y and z transforms in double-single kernels
+        if prm["fft_f64"]:
+            roof["fft"]["kernel"] = "cuFFT 1-D D2Z along x, then k_fft_y64 (double-single y FFT)"
+            roof["scale"]["kernel"] = "k_fgc_z64 (double-single): z FFT, CNV (eq. (sca)) and z IFFT"
+            roof["ifft"]["kernel"] = "k_fft_y64 inverse (double-single), then cuFFT 1-D Z2D along x"
+        else:
+            roof["fft"]["kernel"] = "cuFFT 2-D R2C of the 3 M (y, x) planes"
+            roof["scale"]["kernel"] = "k_fgc_z: z FFT, CNV (eq. (sca)) and z IFFT, spectrum read and written once"
+            roof["ifft"]["kernel"] = "cuFFT 2-D C2R of the 3 M (y, x) planes"
     near = ("double-single" if prm["near_ds"] else ("FP64" if prm["near_f64"] else "FP32"))
     roof["p2p"] = {"inrange_pairs_est": inr, "pairs_per_s": inr / (st["p2p_ms"] * 1e-3),
                    "arithmetic": near + " pairs"}

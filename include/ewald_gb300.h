@@ -97,11 +97,13 @@ typedef struct {
  * field, so the stages do not add up to total_ms.  In a combined apply
  * (ewald_apply_combined) p2p_ms includes the double layer's FP32 near field
  * (FP32 plans) and sum_ms its FP64 near field (the other plans); p2g_ms
- * covers the spreading of all nine components.  Plans with FP32 spectra and
- * M in {64, 128, 256} run the FFT as a 2-D (y, x) transform of each z plane
- * (fft_ms), the z transforms and the CNV in one kernel (scale_ms) and the
- * inverse 2-D transforms (ifft_ms), in a combined apply with the double
- * layer's six density components transformed and scaled alongside. */
+ * covers the spreading of all nine components.  Plans with M in {64, 128,
+ * 256} run the z transforms and the CNV in one kernel (scale_ms): with FP32
+ * spectra between 2-D (y, x) transforms of each z plane (fft_ms, ifft_ms),
+ * in a combined apply with the double layer's six density components
+ * transformed and scaled alongside; with FP64 spectra (Stokeslet applies) in
+ * double-single arithmetic, fft_ms and ifft_ms then covering the 1-D
+ * transforms along x and the double-single y transforms. */
 typedef struct {
     float bin_ms, p2p_ms, p2g_ms, fft_ms, scale_ms, ifft_ms, g2p_ms, sum_ms, total_ms;
 } ewald_stage_timing;

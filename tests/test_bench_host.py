@@ -92,3 +92,7 @@ def test_clustered_entry(monkeypatch, capsys, fake_result):
     assert r["fft"]["bytes_per_launch"] == 3 * M ** 3 * 8 + 3 * ncplx * 16
     assert r["fft"]["frac"] == pytest.approx(r["fft"]["achieved"] / r["fft"]["peak"])
     assert r["p2p"]["inrange_pairs_est"] > 0
+    # M = 256 with FP64 spectra: the double-single y and z transform kernels
+    assert M == 256 and "k_fgc_z64" in r["scale"]["kernel"] and "k_fft_y64" in r["fft"]["kernel"]
+    # and the main line's FP32 spectra at M = 128: the FP32 z-transform kernel
+    assert d["stage_roofline"]["scale"]["kernel"].startswith("k_fgc_z:")
